@@ -1,0 +1,366 @@
+"""Benchmark of the k x k median filter on synthetic inputs (one JSON line).
+
+Default workload: the 30-megapixel RGB photograph case of the paper's teaser
+(Fig. 1): 3 planar u8 channels of 4480 x 6720, 17 x 17 median, synthetic
+photo-like content (smooth field + Gaussian noise + 5% impulses).  A step is
+one full filter of that image; inputs are resident in HBM; L2 is flushed
+(256 MB write) between timed steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): every rank filters its own copy (independent
+replicas, no collective on the data path); value = all ranks' pixels / the
+slowest rank's time.  --impl reference times the CPU oracle on a bounded
+sample of the same workload (the reference arm of this tier).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PAPER_MPIX_S = 6720 * 4480 * 3 / 2.2e-3 / 1e6  # teaser: 17x17, 30 MP RGB u8 in 2.2 ms (L40S)
+
+WORKLOADS = {
+    # name: (channels, H, W, dtype, k, generator)
+    "photo_rgb_30mp_u8_k17": (3, 4480, 6720, "u8", 17, "photo"),
+    "gray_640x480_u8_k5": (1, 480, 640, "u8", 5, "uniform"),
+}
+for _dt in ("u8", "u16", "u32", "f32"):
+    for _k in (3, 5, 7, 9, 11, 15, 21, 31, 45, 61, 75):
+        WORKLOADS["sweep_4096_%s_k%d" % (_dt, _k)] = (1, 4096, 4096, _dt, _k, "uniform")
+
+
+def make_input(name):
+    from paper_2507_19926_gb300 import synth
+    C, H, W, dt, k, gen = WORKLOADS[name]
+    if gen == "photo":
+        return synth.photo_rgb(H, W)
+    return synth.uniform((C, H, W), dt, synth.SEED_BASE + 2)
+
+
+def to_device(a, dev):
+    """numpy u8/u16/u32/f32 array -> CUDA tensor holding the same bits."""
+    import numpy as np
+    import torch
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint16:
+        return torch.from_numpy(a.view(np.int16)).to(dev).view(torch.uint16)
+    if a.dtype == np.uint32:
+        return torch.from_numpy(a.view(np.int32)).to(dev).view(torch.uint32)
+    return torch.from_numpy(a).to(dev)
+
+
+def gpu_uuid(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev.index or 0)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [s.strip() for s in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_ops_per_px(k):
+    """Min/max element operations per output pixel of the cheapest
+    hierarchy the network generator can emit for k (root tiles 1..16,
+    with the block-wide column sort amortised over the tile width)."""
+    from paper_2507_19926_gb300 import netgen
+    best = None
+    t = 1
+    while t <= min(k, 16):
+        if t * 2 <= k + 1 or t == 1:
+            net = netgen.build(k, t)
+            cs = netgen.column_sort_network(k - t + 1)
+            v = len(net.ops) / (t * t) + len(cs.ops) / t
+            best = v if best is None else min(best, v)
+        t *= 2
+    return best
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_sample(x, k, seconds=8.0):
+    """Times the oracle on sampled rows of x until about `seconds` have passed."""
+    import numpy as np
+    import oracle
+    from paper_2507_19926_gb300 import synth
+    C, H, W = x.shape
+    g = synth.rng(12345)
+    nrows, total_px, total_s = 2, 0, 0.0
+    while total_s < seconds:
+        rows = np.sort(g.choice(H, size=min(nrows, H), replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.median_filter_rows(x, k, rows)
+        dt = time.perf_counter() - t0
+        total_px += C * len(rows) * W
+        total_s += dt
+        nrows = max(2, min(H, int(nrows * max(1.5, min(8.0, (seconds - total_s) / max(dt, 1e-3))))))
+    return total_px / total_s / 1e6, total_px, total_s
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    C, H, W, dt, k, _ = WORKLOADS[args.workload]
+    x = make_input(args.workload)
+    cores = oracle.max_threads()
+    g = __import__("paper_2507_19926_gb300.synth", fromlist=["rng"]).rng(777)
+    rows_per_step = max(1, min(H, int(args.ref_rows)))
+    times, px = [], 0
+    for step in range(args.warmup + args.steps):
+        rows = np.sort(g.choice(H, size=rows_per_step, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.median_filter_rows(x, k, rows)
+        el = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(el)
+            px += C * rows_per_step * W
+    total = sum(times)
+    value = px / total / 1e6
+    sample = "%d random rows x %d channels x %d columns per step of %s" % (rows_per_step, C, W, args.workload)
+    print(json.dumps({
+        "impl": "reference", "metric": "median filter throughput (%s)" % args.workload,
+        "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dt, "data": "synthetic",
+        "config": {"workload": args.workload, "channels": C, "H": H, "W": W, "k": k},
+        "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2507_19926_gb300 as mf
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    mf.load_library()
+    C, H, W, dt, k, _ = WORKLOADS[args.workload]
+    code = {"u8": mf.MF_U8, "u16": mf.MF_U16, "u32": mf.MF_U32, "f32": mf.MF_F32}[dt]
+    variant = mf.VARIANTS[args.variant]
+    x_np = make_input(args.workload)
+    x = to_device(x_np, dev)
+    y = torch.empty_like(x)
+    es = x.element_size()
+    pitch = W * es
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        mf.mf_median_filter_ex(x.data_ptr(), y.data_ptr(), H, W, pitch, C, code, k,
+                               mf.MF_BORDER_CLAMP, variant, None, 0, sptr)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(gpu_uuid(dev))
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = mf.mf_kernel_launch_count()
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)  # evict the image from L2 (outside the events)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    t_wall = time.perf_counter() - t_wall0
+    launches = mf.mf_kernel_launch_count() - launches0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    px_per_step = C * H * W
+    value = ws * px_per_step * args.steps / (total_ms * 1e-3) / 1e6
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    h_in = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+    h_in.copy_(x)
+    h_out = torch.empty_like(h_in, pin_memory=True)
+    mf.mf_median_filter_host(h_in.data_ptr(), h_out.data_ptr(), H, W, pitch, C, code, k,
+                             mf.MF_BORDER_CLAMP, variant, sptr)
+    e2e_times = []
+    for i in range(max(3, min(args.steps, 10))):
+        t0 = time.perf_counter()
+        mf.mf_median_filter_host(h_in.data_ptr(), h_out.data_ptr(), H, W, pitch, C, code, k,
+                                 mf.MF_BORDER_CLAMP, variant, sptr)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_times)
+    e2e_val = ws * px_per_step / e2e_s / 1e6
+    if not torch.equal(h_out.to(dev), y):
+        raise SystemExit("host entry point disagrees with the device entry point")
+
+    if rank != 0:
+        return
+    plan = mf.mf_describe(H, W, C, code, k, variant)
+    peaks = read_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = None
+    extra = {}
+    if "oblivious" in plan:
+        lanes = 2 if dt in ("u8", "u16") else 1
+        ops_px = algorithmic_ops_per_px(k)
+        kind = 1 if lanes == 2 else 0
+        rate, _ = mf.mf_probe_minmax(kind)
+        max_mhz = peaks.get("sm_max_mhz", 2070.0)
+        # min/max instructions per clock per SM from the probe, at the clock it ran
+        probe_mhz = clocks["sm_mhz"] if clocks else max_mhz
+        ipc = rate / (sms * probe_mhz * 1e6)
+        ipc_nominal = 64.0 if ipc < 96 else 128.0
+        peak = sms * ipc_nominal * max_mhz * 1e6 * lanes / 1e9  # G element-ops/s
+        achieved = ops_px * px_per_step / (ms_per_step * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gminmax/s",
+                "frac": achieved / peak, "traffic": None,
+                "basis": "%.1f min/max element-ops per pixel (cheapest generated hierarchy) x %d px; "
+                         "peak = %d SMs x %d min/max instr/clk/SM x %.0f MHz x %d lanes "
+                         "(probe: %.1f instr/clk/SM at %.0f MHz)" % (
+                             ops_px, px_per_step, sms, ipc_nominal, max_mhz, lanes, ipc, probe_mhz)}
+    bytes_per_step = 2 * px_per_step * x.element_size()
+    extra["hbm"] = {"achieved_gbs": bytes_per_step / (ms_per_step * 1e-3) / 1e9,
+                    "peak_gbs": peaks.get("hbm_gbs"),
+                    "frac": (bytes_per_step / (ms_per_step * 1e-3) / 1e9) / peaks["hbm_gbs"]
+                    if peaks.get("hbm_gbs") else None}
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        import oracle
+        v, npx, secs = cpu_sample(x_np, k, args.cpu_seconds)
+        cpu = {"value": v, "unit": "Mpix/s", "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": "%d output channel-pixels on random full rows of the same image (%.1f s)" % (npx, secs)}
+    out = {
+        "metric": "median filter throughput (output channel-pixels per second)",
+        "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_MPIX_S if args.workload == "photo_rgb_30mp_u8_k17" else None,
+        "dtype": dt, "data": "synthetic",
+        "config": {"workload": args.workload, "channels": C, "H": H, "W": W, "k": k, "variant": args.variant,
+                   "plan": plan, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "Mpix/s", "h2d_bytes_per_step": int(x.numel() * x.element_size()),
+                "d2h_bytes_per_step": int(y.numel() * y.element_size())},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "wall_s_timed_region": t_wall,
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+        "extra": extra,
+    }
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="photo_rgb_30mp_u8_k17", choices=sorted(WORKLOADS))
+    ap.add_argument("--variant", default="auto", choices=["auto", "oblivious", "data_aware"])
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-rows", type=int, default=8)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * medianfilter.h -- C ABI of the GB300 (sm_103a) k x k median filter.
+ *
+ * The filter replaces every pixel by the median of the k x k neighbourhood
+ * centred on it (paper: "A Fast Parallel Median Filtering Algorithm Using
+ * Hierarchical Tiling", Sec. 1).  It is computed by hierarchical tiling
+ * (Sec. 3) with either the data-oblivious selection network held in
+ * registers (Sec. 4) or the data-aware merge variant (Sec. 5).  Both give
+ * exactly the same result: selection does no arithmetic, so outputs are
+ * bit-copies of input elements.
+ *
+ * Conventions fixed by this library where the paper is silent:
+ *   - borders clamp to the edge (window reads src[clamp(y+dy)][clamp(x+dx)]);
+ *   - k is odd, 1 <= k <= 75 (k = 1 is the identity); the median is the
+ *     element of 0-based rank (k*k-1)/2 of the window;
+ *   - f32 values are ordered by their sign-flipped bit pattern:
+ *     -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN;
+ *   - the argmedian of a pixel is the source pixel of the rank-(k*k-1)/2
+ *     window element under (value, row-major window slot) order, stored as
+ *     ys * W + xs within the channel plane.
+ *
+ * Memory: every image pointer below is device memory owned by the caller,
+ * except where an entry point says "host".  Channels are planar: plane c of
+ * an image starts at base + c * H * pitch, for src and dst alike.  pitch
+ * is in bytes, a multiple of the element size and >= W * element size.
+ *
+ * Streams: device entry points enqueue work on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream) and return without synchronising.
+ * Errors: every entry point returns MF_OK (0) or a negative mf_status;
+ * arguments are checked before anything is launched, no error terminates
+ * the process, and mf_last_error() gives a one-line description of the
+ * calling thread's last failure.
+ */
+#ifndef MEDIANFILTER_H
+#define MEDIANFILTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *mf_stream_t; /* identical to cudaStream_t */
+
+typedef enum { MF_U8 = 0, MF_U16 = 1, MF_U32 = 2, MF_F32 = 3 } mf_dtype;
+typedef enum { MF_BORDER_CLAMP = 0 } mf_border;
+typedef enum { MF_AUTO = 0, MF_OBLIVIOUS = 1, MF_DATA_AWARE = 2 } mf_variant;
+typedef enum { MF_GRAD_ATOMIC = 0, MF_GRAD_DETERMINISTIC = 1 } mf_grad_mode;
+
+typedef enum {
+    MF_OK = 0,
+    MF_ERR_ARG = -1,      /* bad k, H, W, channels, or a NULL pointer */
+    MF_ERR_DTYPE = -2,    /* dtype not supported by this entry point */
+    MF_ERR_PITCH = -3,    /* pitch too small or not a multiple of the element size */
+    MF_ERR_ALIAS = -4,    /* src and dst overlap */
+    MF_ERR_ALLOC = -5,    /* device or host allocation failed */
+    MF_ERR_CUDA = -6,     /* a CUDA call failed; see mf_last_error() */
+    MF_ERR_TIMEOUT = -7,  /* a bounded device-side wait gave up */
+    MF_ERR_INTERNAL = -8, /* an internal consistency check failed */
+    MF_ERR_UNSUPPORTED = -9 /* no kernel instantiated for this request */
+} mf_status;
+
+/* Median filter of `channels` planar planes of H x W elements of `dtype`
+ * (paper Sec. 1 definition; computed by hierarchical tiling, Sec. 3).
+ * src, dst: device pointers, caller-owned, must not overlap.  The variant
+ * and tile shape are chosen automatically (autotuner cache, else the paper's
+ * root-tile heuristic t(k) = 2^(floor(log2 k) - 1), Sec. 4.2). */
+int mf_median_filter(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                     mf_dtype dtype, int k, mf_border border, mf_stream_t stream);
+
+/* As mf_median_filter, with an explicit variant (Sec. 4 oblivious network,
+ * Sec. 5 data-aware merges) and an optional argmedian output.
+ * argidx: NULL, or a caller-owned device buffer of int32 with `idx_pitch`
+ * bytes per row (>= 4 * W, multiple of 4); plane c starts at
+ * argidx + c * H * idx_pitch.  Entry (y, x) receives ys * W + xs of the
+ * source pixel of the median (tie rule: lowest value, then lowest row-major
+ * window slot).  dst may be NULL when argidx is given. */
+int mf_median_filter_ex(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                        mf_dtype dtype, int k, mf_border border, mf_variant variant,
+                        int32_t *argidx, size_t idx_pitch, mf_stream_t stream);
+
+/* Gradient of the filter with respect to its f32 input: grad_in[p] = sum
+ * of grad_out[q] over the outputs q whose argmedian is p (the median is the
+ * identity on its selected input).  All pointers are caller-owned device
+ * memory; grad_out and grad_in use `pitch` (bytes, >= 4 * W), argidx uses
+ * idx_pitch.  MF_GRAD_ATOMIC zeroes grad_in and scatter-adds with atomics
+ * (summation order unspecified); MF_GRAD_DETERMINISTIC gathers, for each p,
+ * the contributions in increasing row-major q (bit-identical run to run and
+ * to a sequential scatter).  grad_in must not overlap grad_out or argidx. */
+int mf_median_filter_bwd(const float *grad_out, const int32_t *argidx, float *grad_in,
+                         int H, int W, size_t pitch, size_t idx_pitch, int channels, int k,
+                         mf_grad_mode mode, mf_stream_t stream);
+
+/* The same filter on HOST buffers: copies src (pitch bytes per row) to the
+ * device, filters, copies the result back into dst (host) and waits for
+ * completion.  Host buffers are caller-owned; page-locked memory makes the
+ * copies asynchronous DMA.  Device staging memory is owned by the library:
+ * one pair of buffers per process, grown on demand, shared by calls under a
+ * lock and released by mf_shutdown(). */
+int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, size_t pitch,
+                          int channels, mf_dtype dtype, int k, mf_border border,
+                          mf_variant variant, mf_stream_t stream);
+
+/* ---- batched persistent launch --------------------------------------- */
+
+typedef struct {
+    const void *src;  /* device, caller-owned */
+    void *dst;        /* device, caller-owned */
+    int H, W;
+    size_t pitch;     /* bytes, src and dst */
+    int channels;
+    mf_dtype dtype;
+    int k;            /* odd, 1..31 */
+} mf_image_desc;
+
+typedef struct mf_batch_plan mf_batch_plan;
+
+/* Plans many images of uneven sizes, dtypes and k for one persistent launch
+ * with a device-side work queue, ordered by predicted cost.  The plan owns
+ * its device memory (work list and queue counter) until destroyed.  The
+ * descriptors are copied; the image buffers they point to must stay valid
+ * while the plan is run. */
+int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_plan **out);
+/* Runs a plan on `stream` (one CUDA graph launch: queue reset + kernel). */
+int mf_batch_run(mf_batch_plan *plan, mf_stream_t stream);
+int mf_batch_plan_destroy(mf_batch_plan *plan);
+
+/* ---- tuning and introspection ------------------------------------------ */
+
+/* Times the instantiated candidates for one (k, dtype, H, W) on the current
+ * device and records the fastest in the in-memory tuning table (and in the
+ * JSON file named by MF_TUNE_CACHE, if set).  Uses caller-owned scratch:
+ * src and dst must be device buffers of channels * H * pitch bytes. */
+int mf_autotune(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                mf_dtype dtype, int k, mf_stream_t stream);
+
+/* Describes the plan mf_median_filter would launch: writes a one-line
+ * description (variant, tile, block) into buf.  Returns MF_OK or an error. */
+int mf_describe(int H, int W, int channels, mf_dtype dtype, int k, mf_variant variant,
+                char *buf, size_t buflen);
+
+/* Min/max throughput microbenchmark (the denominator of the data-oblivious
+ * kernels' ALU roofline; no counterpart in the paper).  kind: 0 = u32,
+ * 1 = packed u16x2, 2 = f32, 3 = packed f16x2 min/max.  Runs `iters`
+ * iterations of 16 min/max per thread on 4 blocks of 256 threads per SM of
+ * the current device (the library allocates and frees its own 8 KB-scale
+ * buffers) and writes instructions per second (one per thread-instruction)
+ * and the best of three elapsed times in milliseconds (ms may be NULL). */
+int mf_probe_minmax(int kind, int iters, double *instr_per_s, double *ms);
+
+/* Number of CUDA kernels this library launched since load (all threads). */
+uint64_t mf_kernel_launch_count(void);
+
+const char *mf_status_string(int status);
+const char *mf_last_error(void);
+const char *mf_version(void);
+
+/* Releases cached device memory of the calling process. */
+int mf_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MEDIANFILTER_H */

@@ -1,0 +1,163 @@
+"""Builds libmedianfilter.so for sm_103a.
+
+Steps: (1) emit the data-oblivious networks and their kernel
+instantiations (codegen.py) into _build/gen; (2) compile every translation
+unit with nvcc in parallel; (3) link the shared library next to this file.
+Outputs are git-ignored build artefacts.  Nothing here needs a GPU.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import hashlib
+import os
+import shutil
+import subprocess
+import sys
+
+from . import codegen, netgen
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+GEN = os.path.join(BUILD, "gen")
+LIB = os.path.join(HERE, "libmedianfilter.so")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+              "-I" + INCLUDE, "-I" + CSRC, "-I" + GEN]
+
+# Data-oblivious instantiations: k -> (tile w, tile h, block x, block y).
+# Root tiles follow t(k) = 2^(floor(log2 k) - 1) (paper Sec. 4.2) up to
+# k = 7 and stay at 4x4 above: an 8x8 root tile's network no longer fits
+# the 255 registers of one thread (the paper's own limit, Sec. 4.3).
+O1_VALUE = {3: (2, 2, 32, 4), 5: (2, 2, 32, 4), 7: (4, 4, 32, 4), 9: (4, 4, 32, 4),
+            11: (4, 4, 32, 4), 13: (4, 4, 32, 4), 15: (4, 4, 32, 4), 17: (4, 4, 32, 4)}
+# argmedian with 32-bit records (8/16-bit data) and 64-bit records (32-bit data)
+O1_ARG32 = {k: v for k, v in O1_VALUE.items()}
+O1_ARG64 = {k: v for k, v in O1_VALUE.items() if k <= 9}
+
+DT_NAMES = {0: "MF_U8", 1: "MF_U16", 2: "MF_U32", 3: "MF_F32"}
+
+
+def _o1_instances():
+    """(k, tw, th, bx, by, dtype, ko, arg, ib) for every O1 kernel built."""
+    out = []
+    for k, (tw, th, bx, by) in sorted(O1_VALUE.items()):
+        for dt in (0, 1):
+            out.append((k, tw, th, bx, by, dt, "KoU16x2", False, 0))
+        for dt in (2, 3):
+            out.append((k, tw, th, bx, by, dt, "KoU32", False, 0))
+    for k, (tw, th, bx, by) in sorted(O1_ARG32.items()):
+        out.append((k, tw, th, bx, by, 0, "KoU32", True, 24))
+        out.append((k, tw, th, bx, by, 1, "KoU32", True, 16))
+    for k, (tw, th, bx, by) in sorted(O1_ARG64.items()):
+        for dt in (2, 3):
+            out.append((k, tw, th, bx, by, dt, "KoU64", True, 32))
+    return out
+
+
+def generate():
+    os.makedirs(GEN, exist_ok=True)
+    insts = _o1_instances()
+    by_k = {}
+    for inst in insts:
+        by_k.setdefault(inst[0], []).append(inst)
+    tus = []
+    decls = []
+    entries = []
+    for k, lst in sorted(by_k.items()):
+        parts = ['// generated by codegen/build.py -- do not edit', '#include "mf_oblivious.cuh"',
+                 "namespace mf {"]
+        nets = sorted({(i[1], i[2]) for i in lst})
+        sorts = sorted({k - th + 1 for (_, th) in nets})
+        for tw, th in nets:
+            parts.append(codegen.emit_network(netgen.build(k, tw, th), codegen.net_name(k, tw, th)))
+        for n in sorts:
+            parts.append(codegen.emit_colsort(n))
+        for (k_, tw, th, bx, by, dt, ko, arg, ib) in lst:
+            fn = "o1_launch_k%d_%dx%d_%s_%s%s" % (k, tw, th, DT_NAMES[dt], ko, "_arg" if arg else "")
+            parts.append(
+                "int %s(const ImgArgs &a, int c, cudaStream_t s) {\n"
+                "  return launch_o1<%d, %d, %d, %d, %d, %s, %s, %s, %d, %s, %s>(a, c, s);\n}"
+                % (fn, k, tw, th, bx, by, DT_NAMES[dt], ko, "true" if arg else "false", ib,
+                   codegen.net_name(k, tw, th), codegen.sort_name(k - th + 1)))
+            decls.append("int %s(const ImgArgs &a, int c, cudaStream_t s);" % fn)
+            entries.append("  {%d, %s, %d, %d, %d, %d, %d, %d, %s, \"%s\"}," %
+                           (k, DT_NAMES[dt], 1 if arg else 0, tw, th, bx, by,
+                            netgen.build(k, tw, th).ops.__len__(), fn, fn))
+        parts.append("}  // namespace mf")
+        path = os.path.join(GEN, "o1_k%d.cu" % k)
+        codegen.write_if_changed(path, "\n".join(parts) + "\n")
+        tus.append(path)
+    reg = ['// generated -- do not edit', '#include "mf_registry.h"', "namespace mf {"]
+    reg += decls
+    reg.append("const O1Entry kO1Entries[] = {")
+    reg += entries
+    reg.append("};")
+    reg.append("const int kO1Count = %d;" % len(entries))
+    reg.append("}  // namespace mf")
+    path = os.path.join(GEN, "o1_registry.cu")
+    codegen.write_if_changed(path, "\n".join(reg) + "\n")
+    tus.append(path)
+    return tus
+
+
+def _flags_hash(src, flags):
+    h = hashlib.sha1()
+    h.update(" ".join(flags).encode())
+    with open(src, "rb") as f:
+        h.update(f.read())
+    # headers of csrc affect every TU
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cuh", ".h")):
+            with open(os.path.join(CSRC, name), "rb") as f:
+                h.update(f.read())
+    with open(os.path.join(INCLUDE, "medianfilter.h"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _compile(src, verbose=False):
+    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+    stamp = obj + ".hash"
+    hsh = _flags_hash(src, NVCC_FLAGS + ARCH)
+    if os.path.exists(obj) and os.path.exists(stamp) and open(stamp).read() == hsh:
+        return obj, ""
+    cmd = ["nvcc"] + ARCH + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr[-8000:]))
+    with open(stamp, "w") as f:
+        f.write(hsh)
+    return obj, r.stderr
+
+
+def build(jobs=None, verbose=False):
+    """Generate, compile and link; returns the path of the shared library."""
+    if shutil.which("nvcc") is None:
+        raise RuntimeError("nvcc not found on PATH")
+    os.makedirs(BUILD, exist_ok=True)
+    tus = generate()
+    tus += [os.path.join(CSRC, n) for n in sorted(os.listdir(CSRC)) if n.endswith(".cu")]
+    jobs = jobs or max(1, min(len(tus), os.cpu_count() or 4))
+    # biggest TUs first
+    tus.sort(key=lambda p: -os.path.getsize(p))
+    objs, logs = [], []
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        for obj, log in ex.map(lambda s: _compile(s, verbose), tus):
+            objs.append(obj)
+            logs.append(log)
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = ["nvcc"] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + sorted(objs)
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
+    os.replace(tmp, LIB)
+    if verbose:
+        sys.stderr.write("".join(logs))
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose="-v" in sys.argv))

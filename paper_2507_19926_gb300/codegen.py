@@ -1,0 +1,93 @@
+"""Emits CUDA source for the data-oblivious networks built by ``netgen``.
+
+Each (k, t_w, t_h) network becomes a struct with one templated device
+function: straight-line SSA code of ``KO::mn`` / ``KO::mx`` calls, each
+shared-memory input loaded just before its first use at an offset that the
+layout class ``L`` folds into a constant.  The kernel template in
+``csrc/mf_oblivious.cuh`` supplies ``KO`` (packed u16x2 keys, u32 keys,
+32/64-bit argmedian records) and ``L``.
+
+The generated files go to a build directory; nothing here runs on the GPU.
+"""
+from __future__ import annotations
+
+import os
+
+from . import netgen
+
+
+def net_name(k, tw, th):
+    return "Net_k%d_%dx%d" % (k, tw, th)
+
+
+def sort_name(n):
+    return "ColSort_%d" % n
+
+
+def emit_network(net, name):
+    lines = []
+    w = lines.append
+    w("struct %s {" % name)
+    w("  static constexpr int n_ops = %d;" % len(net.ops))
+    w("  template <class KO, class L>")
+    w("  static __device__ __forceinline__ void run(const typename KO::T *__restrict__ cs,")
+    w("                                            const typename KO::T *__restrict__ rw,")
+    w("                                            typename KO::T *o) {")
+    w("    typedef typename KO::T T;")
+    n_in = len(net.inputs)
+    loaded = [False] * n_in
+
+    def ref(v):
+        if v < n_in and not loaded[v]:
+            desc = net.inputs[v]
+            if desc[0] == "col":
+                w("    const T v%d = cs[L::col(%d, %d)];" % (v, desc[1], desc[2]))
+            else:
+                w("    const T v%d = rw[L::px(%d, %d)];" % (v, desc[1], desc[2]))
+            loaded[v] = True
+        return "v%d" % v
+
+    for kind, a, b, v in net.ops:
+        ra, rb = ref(a), ref(b)
+        w("    const T v%d = KO::%s(%s, %s);" % (v, "mn" if kind == "min" else "mx", ra, rb))
+    for i, v in enumerate(net.outputs):
+        w("    o[%d] = %s;" % (i, ref(v)))
+    w("  }")
+    w("};")
+    return "\n".join(lines) + "\n"
+
+
+def emit_colsort(n):
+    net = netgen.column_sort_network(n)
+    lines = []
+    w = lines.append
+    w("struct %s {" % sort_name(n))
+    w("  static constexpr int n_ops = %d;" % len(net.ops))
+    w("  template <class KO>")
+    w("  static __device__ __forceinline__ void run(typename KO::T *v) {")
+    w("    typedef typename KO::T T;")
+    # inputs are ("in", i) in first-use order
+    for j, desc in enumerate(net.inputs):
+        w("    const T v%d = v[%d];" % (j, desc[1]))
+    n_in = len(net.inputs)
+    for kind, a, b, v in net.ops:
+        w("    const T v%d = KO::%s(v%d, v%d);" % (v, "mn" if kind == "min" else "mx", a, b))
+    for i, v in enumerate(net.outputs):
+        w("    v[%d] = v%d;" % (i, v))
+    if n_in == 0 and n == 1:
+        pass
+    w("  }")
+    w("};")
+    return "\n".join(lines) + "\n"
+
+
+def write_if_changed(path, text):
+    if os.path.exists(path):
+        with open(path) as f:
+            if f.read() == text:
+                return False
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        f.write(text)
+    os.replace(tmp, path)
+    return True

@@ -1,0 +1,300 @@
+// C ABI of the median filter: argument checks, variant/tile dispatch, the
+// host-buffer entry point, error reporting.  The filter itself is defined in
+// the paper's introduction (Sec. 1); the kernels live in mf_oblivious.cuh
+// (Sec. 4) and mf_data_aware.cu (Sec. 5).
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mf_registry.h"
+#include "mf_tune.h"
+
+namespace mf {
+
+static thread_local char g_err[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+const O1Entry *find_o1(int k, int dtype, bool arg) {
+    for (int i = 0; i < kO1Count; i++)
+        if (kO1Entries[i].k == k && kO1Entries[i].dtype == dtype && kO1Entries[i].arg == (arg ? 1 : 0))
+            return &kO1Entries[i];
+    return nullptr;
+}
+
+static int esize(int dtype) {
+    switch (dtype) {
+        case MF_U8: return 1;
+        case MF_U16: return 2;
+        case MF_U32: return 4;
+        case MF_F32: return 4;
+        default: return 0;
+    }
+}
+
+static int cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return MF_ERR_CUDA;
+}
+
+static bool overlap(const void *a, size_t na, const void *b, size_t nb) {
+    const char *pa = (const char *)a, *pb = (const char *)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+// Checks shared by the forward entry points.
+static int check_fwd(const void *src, const void *dst, int H, int W, size_t pitch, int C, int dtype,
+                     int k, int border, const int32_t *idx, size_t idx_pitch) {
+    if (esize(dtype) == 0) { set_error("unknown dtype %d", dtype); return MF_ERR_DTYPE; }
+    if (k < 1 || k > 75 || (k & 1) == 0) { set_error("k must be odd in 1..75 (got %d)", k); return MF_ERR_ARG; }
+    if (H < 1 || W < 1 || C < 1 || C > 65535) { set_error("bad shape H=%d W=%d C=%d", H, W, C); return MF_ERR_ARG; }
+    if ((long long)H * W > (1ll << 31) - 1) { set_error("plane too large for int32 indices"); return MF_ERR_ARG; }
+    if (border != MF_BORDER_CLAMP) { set_error("only clamp-to-edge borders are supported"); return MF_ERR_ARG; }
+    if (!src || (!dst && !idx)) { set_error("null pointer"); return MF_ERR_ARG; }
+    const int es = esize(dtype);
+    if (pitch < (size_t)W * es || pitch % es) { set_error("bad pitch %zu for W=%d", pitch, W); return MF_ERR_PITCH; }
+    if (idx && (idx_pitch < (size_t)W * 4 || idx_pitch % 4)) { set_error("bad idx_pitch %zu", idx_pitch); return MF_ERR_PITCH; }
+    const size_t bytes = (size_t)C * H * pitch;
+    if (dst && overlap(src, bytes, dst, bytes)) { set_error("src and dst overlap"); return MF_ERR_ALIAS; }
+    if (idx && overlap(src, bytes, idx, (size_t)C * H * idx_pitch)) { set_error("src and argidx overlap"); return MF_ERR_ALIAS; }
+    if (idx && dst && overlap(dst, bytes, idx, (size_t)C * H * idx_pitch)) { set_error("dst and argidx overlap"); return MF_ERR_ALIAS; }
+    return MF_OK;
+}
+
+// ----------------------------------------------------------- k = 1 path
+__global__ void identity_idx_kernel(int32_t *idx, int H, int W, size_t idx_pitch, size_t idx_plane) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= W) return;
+    int32_t *row = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(idx) + blockIdx.z * idx_plane +
+                                               (size_t)y * idx_pitch);
+    row[x] = y * W + x;
+}
+
+int launch_identity_idx(const ImgArgs &a, int C, cudaStream_t s) {
+    dim3 grid((a.W + 255) / 256, a.H, C);
+    identity_idx_kernel<<<grid, 256, 0, s>>>(a.idx, a.H, a.W, a.idx_pitch, a.idx_plane);
+    count_launch();
+    cudaError_t e = cudaPeekAtLastError();
+    return e == cudaSuccess ? MF_OK : cuda_fail(e, "identity index kernel");
+}
+
+// ----------------------------------------------------------- dispatch
+struct Plan {
+    int variant;  // MF_OBLIVIOUS or MF_DATA_AWARE (resolved)
+    const O1Entry *o1;
+    int tile;     // D1 root tile
+};
+
+static int resolve(int k, int dtype, bool arg, int variant, Plan *p) {
+    p->o1 = nullptr;
+    p->tile = 0;
+    const O1Entry *o1 = find_o1(k, dtype, arg);
+    const bool d1 = d1_supported(k, dtype, arg) != 0;
+    if (variant == MF_AUTO) {
+        int tuned = tune_lookup(k, dtype, arg);
+        if (tuned == MF_OBLIVIOUS && o1) variant = MF_OBLIVIOUS;
+        else if (tuned == MF_DATA_AWARE && d1) variant = MF_DATA_AWARE;
+        else variant = o1 ? MF_OBLIVIOUS : MF_DATA_AWARE;
+    }
+    if (variant == MF_OBLIVIOUS) {
+        if (!o1) { set_error("no data-oblivious kernel for k=%d dtype=%d%s", k, dtype, arg ? " (argmedian)" : ""); return MF_ERR_UNSUPPORTED; }
+        p->variant = MF_OBLIVIOUS;
+        p->o1 = o1;
+        return MF_OK;
+    }
+    if (variant == MF_DATA_AWARE) {
+        if (!d1) { set_error("no data-aware kernel for k=%d dtype=%d%s", k, dtype, arg ? " (argmedian)" : ""); return MF_ERR_UNSUPPORTED; }
+        p->variant = MF_DATA_AWARE;
+        p->tile = d1_default_tile(k, dtype, arg);
+        return MF_OK;
+    }
+    set_error("unknown variant %d", variant);
+    return MF_ERR_ARG;
+}
+
+static int run_filter(const void *src, void *dst, int H, int W, size_t pitch, int C, int dtype, int k,
+                      int variant, int32_t *idx, size_t idx_pitch, cudaStream_t s) {
+    ImgArgs a;
+    a.src = (const char *)src;
+    a.dst = (char *)dst;
+    a.idx = idx;
+    a.H = H;
+    a.W = W;
+    a.pitch = pitch;
+    a.plane = (size_t)H * pitch;
+    a.idx_pitch = idx_pitch;
+    a.idx_plane = (size_t)H * idx_pitch;
+    if (k == 1) {
+        if (dst) {
+            cudaError_t e = cudaMemcpy2DAsync(dst, pitch, src, pitch, (size_t)W * esize(dtype),
+                                              (size_t)H * C, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(e, "identity copy");
+        }
+        return idx ? launch_identity_idx(a, C, s) : MF_OK;
+    }
+    Plan p;
+    int rc = resolve(k, dtype, idx != nullptr, variant, &p);
+    if (rc) return rc;
+    if (p.variant == MF_OBLIVIOUS) {
+        rc = p.o1->launch(a, C, s);
+        if (rc == MF_ERR_CUDA) set_error("%s: %s", p.o1->name, cudaGetErrorString(cudaGetLastError()));
+        return rc;
+    }
+    return d1_launch(a, C, k, dtype, p.tile, s);
+}
+
+}  // namespace mf
+
+using namespace mf;
+
+extern "C" {
+
+int mf_median_filter(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                     mf_dtype dtype, int k, mf_border border, mf_stream_t stream) {
+    int rc = check_fwd(src, dst, H, W, pitch, channels, dtype, k, border, nullptr, 0);
+    if (rc || !dst) return rc ? rc : (set_error("null dst"), MF_ERR_ARG);
+    return run_filter(src, dst, H, W, pitch, channels, dtype, k, MF_AUTO, nullptr, 0,
+                      (cudaStream_t)stream);
+}
+
+int mf_median_filter_ex(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                        mf_dtype dtype, int k, mf_border border, mf_variant variant,
+                        int32_t *argidx, size_t idx_pitch, mf_stream_t stream) {
+    int rc = check_fwd(src, dst, H, W, pitch, channels, dtype, k, border, argidx, idx_pitch);
+    if (rc) return rc;
+    if (variant != MF_AUTO && variant != MF_OBLIVIOUS && variant != MF_DATA_AWARE) {
+        set_error("unknown variant %d", (int)variant);
+        return MF_ERR_ARG;
+    }
+    return run_filter(src, dst, H, W, pitch, channels, dtype, k, variant, argidx, idx_pitch,
+                      (cudaStream_t)stream);
+}
+
+// Device staging buffers of the host entry point (one pair per process,
+// grown on demand, serialised by a mutex, released by mf_shutdown).
+static std::mutex g_stage_mu;
+static void *g_stage_src = nullptr, *g_stage_dst = nullptr;
+static size_t g_stage_bytes = 0;
+
+int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, size_t pitch,
+                          int channels, mf_dtype dtype, int k, mf_border border,
+                          mf_variant variant, mf_stream_t stream) {
+    if (!src_host || !dst_host) { set_error("null pointer"); return MF_ERR_ARG; }
+    const int es = esize(dtype);
+    if (es == 0) { set_error("unknown dtype %d", dtype); return MF_ERR_DTYPE; }
+    if (H < 1 || W < 1 || channels < 1) { set_error("bad shape"); return MF_ERR_ARG; }
+    if (pitch < (size_t)W * es || pitch % es) { set_error("bad pitch"); return MF_ERR_PITCH; }
+    const size_t dpitch = ((size_t)W * es + 255) & ~(size_t)255;
+    const size_t bytes = (size_t)channels * H * dpitch;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    if (g_stage_bytes < bytes) {
+        if (g_stage_src) { cudaFree(g_stage_src); cudaFree(g_stage_dst); }
+        g_stage_src = g_stage_dst = nullptr;
+        g_stage_bytes = 0;
+        if (cudaMalloc(&g_stage_src, bytes) != cudaSuccess || cudaMalloc(&g_stage_dst, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            if (g_stage_src) cudaFree(g_stage_src);
+            g_stage_src = g_stage_dst = nullptr;
+            set_error("cannot allocate %zu bytes of device staging", 2 * bytes);
+            return MF_ERR_ALLOC;
+        }
+        g_stage_bytes = bytes;
+    }
+    cudaError_t e = cudaMemcpy2DAsync(g_stage_src, dpitch, src_host, pitch, (size_t)W * es,
+                                      (size_t)channels * H, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
+    int rc = mf_median_filter_ex(g_stage_src, g_stage_dst, H, W, dpitch, channels, dtype, k, border,
+                                 variant, nullptr, 0, stream);
+    if (rc) return rc;
+    e = cudaMemcpy2DAsync(dst_host, pitch, g_stage_dst, dpitch, (size_t)W * es, (size_t)channels * H,
+                          cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return MF_OK;
+}
+
+int mf_median_filter_bwd(const float *grad_out, const int32_t *argidx, float *grad_in, int H, int W,
+                         size_t pitch, size_t idx_pitch, int channels, int k, mf_grad_mode mode,
+                         mf_stream_t stream) {
+    if (!grad_out || !argidx || !grad_in) { set_error("null pointer"); return MF_ERR_ARG; }
+    if (H < 1 || W < 1 || channels < 1 || channels > 65535) { set_error("bad shape"); return MF_ERR_ARG; }
+    if (k < 1 || k > 75 || !(k & 1)) { set_error("k must be odd in 1..75"); return MF_ERR_ARG; }
+    if (pitch < (size_t)W * 4 || pitch % 4) { set_error("bad pitch"); return MF_ERR_PITCH; }
+    if (idx_pitch < (size_t)W * 4 || idx_pitch % 4) { set_error("bad idx_pitch"); return MF_ERR_PITCH; }
+    const size_t gb = (size_t)channels * H * pitch, ib = (size_t)channels * H * idx_pitch;
+    if (overlap(grad_in, gb, grad_out, gb) || overlap(grad_in, gb, argidx, ib)) {
+        set_error("grad_in overlaps an input");
+        return MF_ERR_ALIAS;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mode == MF_GRAD_ATOMIC) return bwd_atomic(grad_out, argidx, grad_in, H, W, pitch, idx_pitch, channels, s);
+    if (mode == MF_GRAD_DETERMINISTIC)
+        return bwd_gather(grad_out, argidx, grad_in, H, W, pitch, idx_pitch, channels, k, s);
+    set_error("unknown gradient mode %d", (int)mode);
+    return MF_ERR_ARG;
+}
+
+int mf_describe(int H, int W, int channels, mf_dtype dtype, int k, mf_variant variant, char *buf,
+                size_t buflen) {
+    if (!buf || buflen == 0) { set_error("null buffer"); return MF_ERR_ARG; }
+    if (esize(dtype) == 0) { set_error("unknown dtype"); return MF_ERR_DTYPE; }
+    if (k < 1 || k > 75 || !(k & 1) || H < 1 || W < 1 || channels < 1) { set_error("bad arguments"); return MF_ERR_ARG; }
+    if (k == 1) { snprintf(buf, buflen, "identity copy"); return MF_OK; }
+    Plan p;
+    int rc = resolve(k, dtype, false, variant, &p);
+    if (rc) return rc;
+    if (p.variant == MF_OBLIVIOUS)
+        snprintf(buf, buflen, "oblivious k=%d tile=%dx%d block=%dx%d net_ops=%d kernel=%s", k, p.o1->tw,
+                 p.o1->th, p.o1->bx, p.o1->by, p.o1->net_ops, p.o1->name);
+    else
+        d1_describe(k, dtype, false, p.tile, buf, buflen);
+    return MF_OK;
+}
+
+uint64_t mf_kernel_launch_count(void) { return g_launches.load(); }
+
+const char *mf_status_string(int status) {
+    switch (status) {
+        case MF_OK: return "ok";
+        case MF_ERR_ARG: return "invalid argument";
+        case MF_ERR_DTYPE: return "unsupported dtype";
+        case MF_ERR_PITCH: return "invalid pitch";
+        case MF_ERR_ALIAS: return "buffers overlap";
+        case MF_ERR_ALLOC: return "allocation failed";
+        case MF_ERR_CUDA: return "CUDA error";
+        case MF_ERR_TIMEOUT: return "device wait timed out";
+        case MF_ERR_INTERNAL: return "internal error";
+        case MF_ERR_UNSUPPORTED: return "no kernel for this configuration";
+        default: return "unknown status";
+    }
+}
+
+const char *mf_last_error(void) { return g_err; }
+
+const char *mf_version(void) { return "medianfilter-gb300 0.1 (sm_103a)"; }
+
+int mf_shutdown(void) {
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    if (g_stage_src) cudaFree(g_stage_src);
+    if (g_stage_dst) cudaFree(g_stage_dst);
+    g_stage_src = g_stage_dst = nullptr;
+    g_stage_bytes = 0;
+    return MF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Shared device-side definitions of the median-filter kernels (sm_103a).
+//
+// Order keys: every element is compared through an unsigned key.  u8/u16/u32
+// keys are the values; f32 keys are the IEEE bits with the sign bit set for
+// non-negative values and all bits inverted for negative ones, so that key
+// order is -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN and equal keys
+// are bit-identical values.  Min/max networks on keys therefore select the
+// exact input element (paper Sec. 4: networks compile to min/max sequences).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/medianfilter.h"
+
+namespace mf {
+
+// ----------------------------------------------------------------- key ops
+// One 32-bit register holds one u32 key, or two u16 keys (two tiles run the
+// same data-oblivious network side by side, paper Sec. 4.3 packing idea:
+// the network is independent of the data, so lanes never diverge).
+struct KoU32 {
+    typedef uint32_t T;
+    static constexpr int lanes = 1;
+    static __device__ __forceinline__ T mn(T a, T b) { return umin(a, b); }
+    static __device__ __forceinline__ T mx(T a, T b) { return umax(a, b); }
+};
+
+struct KoU16x2 {
+    typedef uint32_t T;
+    static constexpr int lanes = 2;
+    static __device__ __forceinline__ T mn(T a, T b) {
+        T d;
+        asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+        return d;
+    }
+    static __device__ __forceinline__ T mx(T a, T b) {
+        T d;
+        asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+        return d;
+    }
+};
+
+// 64-bit composite records (key << 32 | position) for argmedian of 32-bit data.
+struct KoU64 {
+    typedef unsigned long long T;
+    static constexpr int lanes = 1;
+    static __device__ __forceinline__ T mn(T a, T b) { return a < b ? a : b; }
+    static __device__ __forceinline__ T mx(T a, T b) { return a < b ? b : a; }
+};
+
+// ------------------------------------------------------------ dtype traits
+__device__ __forceinline__ uint32_t f32_key(uint32_t b) {
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ uint32_t f32_unkey(uint32_t k) {
+    return (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+}
+
+template <int DT> struct Dt;
+template <> struct Dt<MF_U8> {
+    typedef uint8_t E;
+    static constexpr int bits = 8;
+    static __device__ __forceinline__ uint32_t key(E v) { return v; }
+    static __device__ __forceinline__ E val(uint32_t k) { return (E)k; }
+};
+template <> struct Dt<MF_U16> {
+    typedef uint16_t E;
+    static constexpr int bits = 16;
+    static __device__ __forceinline__ uint32_t key(E v) { return v; }
+    static __device__ __forceinline__ E val(uint32_t k) { return (E)k; }
+};
+template <> struct Dt<MF_U32> {
+    typedef uint32_t E;
+    static constexpr int bits = 32;
+    static __device__ __forceinline__ uint32_t key(E v) { return v; }
+    static __device__ __forceinline__ E val(uint32_t k) { return k; }
+};
+template <> struct Dt<MF_F32> {
+    typedef uint32_t E;  // raw bits
+    static constexpr int bits = 32;
+    static __device__ __forceinline__ uint32_t key(E v) { return f32_key(v); }
+    static __device__ __forceinline__ E val(uint32_t k) { return f32_unkey(k); }
+};
+
+__host__ __device__ __forceinline__ int clampi(int v, int lo, int hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+template <class E>
+__device__ __forceinline__ E ldg_elem(const char *plane, size_t pitch, int y, int x) {
+    return __ldg(reinterpret_cast<const E *>(plane + (size_t)y * pitch) + x);
+}
+
+// Launch arguments common to all image kernels.
+struct ImgArgs {
+    const char *src;
+    char *dst;
+    int32_t *idx;       // argmedian output or nullptr
+    int H, W;
+    size_t pitch;       // bytes per row, src and dst
+    size_t plane;       // bytes per plane = H * pitch
+    size_t idx_pitch;   // bytes per row of idx
+    size_t idx_plane;   // bytes per plane of idx
+};
+
+// Kernel launch counter (host side, see mf_kernel_launch_count).
+void count_launch(unsigned n = 1);
+
+}  // namespace mf

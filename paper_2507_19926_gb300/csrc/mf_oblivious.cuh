@@ -1,0 +1,204 @@
+// Data-oblivious variant (paper Sec. 4): one root tile per thread, its whole
+// hierarchical selection network unrolled into register min/max code.
+//
+// Block: BX x BY threads, each owning `lanes` root tiles of TW x TH pixels
+// (two tiles per thread for 8/16-bit data, packed in the two 16-bit halves
+// of every register: the network is data-oblivious, so both run the same
+// instruction stream).  The lane-0 tiles cover the left half of the block's
+// region, the lane-1 tiles the right half.
+//
+// Stages (paper Sec. 4.3, re-planned for sm_103a):
+//   1. the block footprint (clamp-to-edge) is loaded into shared memory as
+//      keys, two lanes per 32-bit word;
+//   2. every footprint column, restricted to the root-core rows of each
+//      tile row, is sorted once (round-robin over the block's threads) and
+//      written back: horizontally adjacent tiles share these sorted columns
+//      (Sec. 3.3, column sort);
+//   3. each thread runs the generated network for its tile: multi-way merge
+//      of its sorted core columns, sorting of its extra rows, then the
+//      horizontal/vertical splits down to single pixels (Sec. 3.4), reading
+//      its inputs from shared memory at compile-time offsets;
+//   4. the TW x TH medians of every lane are stored (or, in argmedian mode,
+//      the source index recovered from the composite record).
+//
+// Shared-memory words are stored column-group-transposed: word (row, gx) at
+// row*RS + (gx % TW)*G + gx / TW with G odd.  Thread tx then reads
+// footprint column tx*TW + fx at base + tx + const, so a warp's 32 lanes
+// hit 32 consecutive words (no bank conflicts) for every network input.
+#pragma once
+#include "mf_common.cuh"
+
+namespace mf {
+
+template <int K, int TW, int TH, int BX, int BY>
+struct O1Layout {
+    static constexpr int R = (K - 1) / 2;
+    static constexpr int FW = BX * TW + K - 1;  // footprint width of one lane half
+    static constexpr int FH = BY * TH + K - 1;  // footprint height
+    static constexpr int CH0 = K - TH + 1;      // root core height
+    static constexpr int NG = (FW + TW - 1) / TW;
+    static constexpr int G = NG | 1;            // odd stride between column residues
+    static constexpr int RS = TW * G;           // words per shared-memory row
+    static constexpr int CSB = FH * RS;         // start of the sorted column segments
+    static constexpr int CSTY = CH0 * RS;       // words per tile row of segments
+    static constexpr int WORDS = CSB + BY * CSTY;
+    static __host__ __device__ constexpr int at(int fy, int gx) {
+        return fy * RS + (gx % TW) * G + gx / TW;
+    }
+    // offsets relative to a thread's base (tx folded in): raw pixel and
+    // element i of the sorted segment of footprint column fx
+    static __host__ __device__ constexpr int px(int fy, int fx) {
+        return fy * RS + (fx % TW) * G + fx / TW;
+    }
+    static __host__ __device__ constexpr int col(int fx, int i) {
+        return i * RS + (fx % TW) * G + fx / TW;
+    }
+};
+
+// Builds the comparison word of footprint element (fy, gx) for every lane.
+// Value mode: the key (two 16-bit keys per word for 8/16-bit data).
+// Argmedian mode: the composite record key << IB | (fy * FW + gx), which
+// orders equal keys by block-footprint row-major position -- within one
+// pixel's window that is its row-major window-slot order.
+template <int DT, class KO, bool ARG, int IB>
+struct O1Words;
+
+template <int DT, int IB>
+struct O1Words<DT, KoU16x2, false, IB> {
+    template <class L>
+    static __device__ __forceinline__ uint32_t make(const char *src, const ImgArgs &a, int y,
+                                                    int xl0, int xl1, int, int) {
+        typedef typename Dt<DT>::E E;
+        uint32_t k0 = Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, xl0));
+        uint32_t k1 = Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, xl1));
+        return k0 | (k1 << 16);
+    }
+};
+
+template <int DT, int IB>
+struct O1Words<DT, KoU32, false, IB> {
+    template <class L>
+    static __device__ __forceinline__ uint32_t make(const char *src, const ImgArgs &a, int y,
+                                                    int xl0, int, int, int) {
+        typedef typename Dt<DT>::E E;
+        return Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, xl0));
+    }
+};
+
+template <int DT, int IB>
+struct O1Words<DT, KoU32, true, IB> {  // 8/16-bit argmedian: key << IB | index
+    template <class L>
+    static __device__ __forceinline__ uint32_t make(const char *src, const ImgArgs &a, int y,
+                                                    int xl0, int, int fy, int gx) {
+        typedef typename Dt<DT>::E E;
+        return (Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, xl0)) << IB) | (uint32_t)(fy * L::FW + gx);
+    }
+};
+
+template <int DT, int IB>
+struct O1Words<DT, KoU64, true, IB> {  // 32-bit argmedian: key << 32 | index
+    template <class L>
+    static __device__ __forceinline__ unsigned long long make(const char *src, const ImgArgs &a,
+                                                              int y, int xl0, int, int fy, int gx) {
+        typedef typename Dt<DT>::E E;
+        return ((unsigned long long)Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, xl0)) << 32) |
+               (unsigned long long)(fy * L::FW + gx);
+    }
+};
+
+template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
+          class CSORT>
+__global__ void __launch_bounds__(BX *BY) o1_kernel(ImgArgs a) {
+    typedef O1Layout<K, TW, TH, BX, BY> L;
+    typedef typename KO::T T;
+    typedef typename Dt<DT>::E E;
+    constexpr int P = KO::lanes;
+    constexpr int NT = BX * BY;
+    extern __shared__ __align__(16) unsigned char o1_smem[];
+    T *sm = reinterpret_cast<T *>(o1_smem);
+
+    const int tid = threadIdx.x;
+    const int tx = tid % BX, ty = tid / BX;
+    const int bx0 = blockIdx.x * (P * BX * TW);
+    const int by0 = blockIdx.y * (BY * TH);
+    const char *src = a.src + (size_t)blockIdx.z * a.plane;
+
+    // 1. block footprint -> shared memory (clamp to edge)
+    for (int i = tid; i < L::FH * L::FW; i += NT) {
+        const int fy = i / L::FW, gx = i - fy * L::FW;
+        const int y = clampi(by0 - L::R + fy, 0, a.H - 1);
+        const int x0 = clampi(bx0 - L::R + gx, 0, a.W - 1);
+        const int x1 = clampi(bx0 + BX * TW - L::R + gx, 0, a.W - 1);
+        sm[L::at(fy, gx)] = O1Words<DT, KO, ARG, IB>::template make<L>(src, a, y, x0, x1, fy, gx);
+    }
+    __syncthreads();
+
+    // 2. sort every footprint column over the root-core rows of each tile row
+    for (int i = tid; i < BY * L::FW; i += NT) {
+        const int cty = i / L::FW, gx = i - cty * L::FW;
+        T v[L::CH0];
+#pragma unroll
+        for (int j = 0; j < L::CH0; j++) v[j] = sm[L::at(cty * TH + TH - 1 + j, gx)];
+        CSORT::template run<KO>(v);
+        T *dstc = sm + L::CSB + cty * L::CSTY + (gx % TW) * L::G + gx / TW;
+#pragma unroll
+        for (int j = 0; j < L::CH0; j++) dstc[j * L::RS] = v[j];
+    }
+    __syncthreads();
+
+    // 3. the tile's hierarchical network
+    T o[TW * TH];
+    NET::template run<KO, L>(sm + L::CSB + ty * L::CSTY + tx, sm + ty * TH * L::RS + tx, o);
+
+    // 4. results
+    char *dst = a.dst ? a.dst + (size_t)blockIdx.z * a.plane : nullptr;
+    char *idx = a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)blockIdx.z * a.idx_plane : nullptr;
+#pragma unroll
+    for (int py = 0; py < TH; py++) {
+        const int y = by0 + ty * TH + py;
+        if (y >= a.H) break;
+#pragma unroll
+        for (int l = 0; l < P; l++) {
+#pragma unroll
+            for (int px = 0; px < TW; px++) {
+                const int x = bx0 + l * BX * TW + tx * TW + px;
+                if (x >= a.W) break;
+                const T w = o[py * TW + px];
+                if (!ARG) {
+                    const uint32_t key = P == 2 ? (uint32_t)((w >> (16 * l)) & 0xffffu) : (uint32_t)w;
+                    if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
+                } else {
+                    const uint32_t fidx = (uint32_t)(w & ((1ull << IB) - 1));
+                    const uint32_t key = (uint32_t)(w >> IB);
+                    const int fy = fidx / L::FW, gx = fidx - fy * L::FW;
+                    const int ys = clampi(by0 - L::R + fy, 0, a.H - 1);
+                    const int xs = clampi(bx0 - L::R + gx, 0, a.W - 1);
+                    if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
+                    if (idx) reinterpret_cast<int32_t *>(idx + (size_t)y * a.idx_pitch)[x] = ys * a.W + xs;
+                }
+            }
+        }
+    }
+}
+
+template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
+          class CSORT>
+int launch_o1(const ImgArgs &a, int channels, cudaStream_t s) {
+    typedef O1Layout<K, TW, TH, BX, BY> L;
+    constexpr int P = KO::lanes;
+    constexpr size_t smem = sizeof(typename KO::T) * (size_t)L::WORDS;
+    auto kern = o1_kernel<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT>;
+    static bool configured = false;  // per instantiation; benign race: idempotent
+    if (!configured) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return MF_ERR_CUDA;
+        configured = true;
+    }
+    dim3 grid((a.W + P * BX * TW - 1) / (P * BX * TW), (a.H + BY * TH - 1) / (BY * TH), channels);
+    kern<<<grid, BX * BY, smem, s>>>(a);
+    count_launch();
+    return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;
+}
+
+}  // namespace mf

@@ -1,0 +1,169 @@
+// Autotuner: times the instantiated candidates of one (k, dtype) on the
+// current device with CUDA events and records the fastest.  The paper picks
+// its block shape per kernel size and data type by measurement (Sec. 4.3);
+// here the choice covers the variant (Sec. 4 vs Sec. 5) and the
+// data-aware root tile.  The table can be persisted as JSON (MF_TUNE_CACHE),
+// keyed by GPU name and SM count.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "mf_registry.h"
+#include "mf_tune.h"
+
+namespace mf {
+
+struct TuneVal {
+    int variant;
+    int tile;
+    float ms;
+};
+
+static std::mutex g_mu;
+static std::map<std::tuple<int, int, int>, TuneVal> *g_table = new std::map<std::tuple<int, int, int>, TuneVal>();
+static bool g_loaded = false;
+
+static std::string device_key() {
+    int dev = 0;
+    cudaDeviceProp p;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    char buf[300];
+    snprintf(buf, sizeof buf, "%s/%d", p.name, p.multiProcessorCount);
+    for (char *c = buf; *c; c++)
+        if (*c == '"' || *c == '\\') *c = '_';
+    return buf;
+}
+
+// Cache file format: one JSON object per line,
+// {"device": "...", "k": K, "dtype": D, "arg": A, "variant": V, "tile": T, "ms": M}
+static void load_locked() {
+    if (g_loaded) return;
+    g_loaded = true;
+    const char *path = getenv("MF_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    const std::string dk = device_key();
+    char line[1024], dev[400];
+    while (fgets(line, sizeof line, f)) {
+        int k, dt, arg, var, tile;
+        float ms;
+        if (sscanf(line, " {\"device\": \"%399[^\"]\", \"k\": %d, \"dtype\": %d, \"arg\": %d, \"variant\": %d, \"tile\": %d, \"ms\": %f",
+                   dev, &k, &dt, &arg, &var, &tile, &ms) == 7 &&
+            dk == dev)
+            (*g_table)[std::make_tuple(k, dt, arg)] = TuneVal{var, tile, ms};
+    }
+    fclose(f);
+}
+
+int tune_lookup(int k, int dtype, bool arg) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_locked();
+    auto it = g_table->find(std::make_tuple(k, dtype, arg ? 1 : 0));
+    return it == g_table->end() ? MF_AUTO : it->second.variant;
+}
+
+int tune_tile(int k, int dtype, bool arg) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_locked();
+    auto it = g_table->find(std::make_tuple(k, dtype, arg ? 1 : 0));
+    return it == g_table->end() ? 0 : it->second.tile;
+}
+
+void tune_record(int k, int dtype, bool arg, int variant, int tile, float ms) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_locked();
+    (*g_table)[std::make_tuple(k, dtype, arg ? 1 : 0)] = TuneVal{variant, tile, ms};
+    const char *path = getenv("MF_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "{\"device\": \"%s\", \"k\": %d, \"dtype\": %d, \"arg\": %d, \"variant\": %d, \"tile\": %d, \"ms\": %.6f}\n",
+            device_key().c_str(), k, dtype, arg ? 1 : 0, variant, tile, ms);
+    fclose(f);
+}
+
+static float time_ms(int (*fn)(void *), void *ctx, cudaStream_t s, int *rc) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    *rc = fn(ctx);  // warm-up (also sets kernel attributes)
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && *rc == MF_OK; rep++) {
+        cudaEventRecord(a, s);
+        *rc = fn(ctx);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best) best = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+struct Cand {
+    const ImgArgs *a;
+    int C, k, dtype, tile;
+    const O1Entry *o1;
+    cudaStream_t s;
+};
+
+static int run_cand(void *p) {
+    Cand *c = (Cand *)p;
+    if (c->o1) return c->o1->launch(*c->a, c->C, c->s);
+    return d1_launch(*c->a, c->C, c->k, c->dtype, c->tile, c->s);
+}
+
+}  // namespace mf
+
+using namespace mf;
+
+extern "C" int mf_autotune(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                           mf_dtype dtype, int k, mf_stream_t stream) {
+    if (!src || !dst || H < 1 || W < 1 || channels < 1 || k < 3 || k > 75 || !(k & 1)) {
+        set_error("bad autotune arguments");
+        return MF_ERR_ARG;
+    }
+    ImgArgs a;
+    a.src = (const char *)src;
+    a.dst = (char *)dst;
+    a.idx = nullptr;
+    a.H = H;
+    a.W = W;
+    a.pitch = pitch;
+    a.plane = (size_t)H * pitch;
+    a.idx_pitch = a.idx_plane = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    float best = 1e30f;
+    int best_var = 0, best_tile = 0;
+    const O1Entry *o1 = find_o1(k, dtype, false);
+    if (o1) {
+        Cand c{&a, channels, k, dtype, 0, o1, s};
+        int rc;
+        float ms = time_ms(run_cand, &c, s, &rc);
+        if (rc == MF_OK && ms < best) { best = ms; best_var = MF_OBLIVIOUS; best_tile = 0; }
+    }
+    if (d1_supported(k, dtype, false)) {
+        for (int tile = 2; tile <= 32; tile *= 2) {
+            if (!d1_supported_tile(k, dtype, false, tile)) continue;
+            Cand c{&a, channels, k, dtype, tile, nullptr, s};
+            int rc;
+            float ms = time_ms(run_cand, &c, s, &rc);
+            if (rc == MF_OK && ms < best) { best = ms; best_var = MF_DATA_AWARE; best_tile = tile; }
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error("autotune: %s", cudaGetErrorString(e)); return MF_ERR_CUDA; }
+    if (best_var == 0) { set_error("no candidate for k=%d dtype=%d", k, (int)dtype); return MF_ERR_UNSUPPORTED; }
+    tune_record(k, dtype, false, best_var, best_tile, best);
+    return MF_OK;
+}

@@ -1,0 +1,342 @@
+"""Selection-network generator for the data-oblivious variant.
+
+Builds, for a k x k kernel and a t_w x t_h root tile, the complete
+min/max network that turns one root tile's footprint into its t_w*t_h
+medians by hierarchical tiling (paper Sec. 3):
+
+  * initialisation (Sec. 3.3): the footprint columns restricted to the core
+    rows arrive already sorted (a block-wide column sort shares them between
+    horizontally adjacent tiles); each extra row is sorted here; the core is
+    a multi-way merge of the sorted core columns;
+  * recursion (Sec. 3.4): a tile is split on its longer side, or on its
+    width when square (Sec. 3.1).  A horizontal split merges t_w/2 extra
+    columns into one list and that list into the parent's sorted core, and
+    extends every extra row with its t_w/2 new corners; a vertical split is
+    the same with rows and columns exchanged;
+  * forgetfulness (Sec. 2.2, Fig. 3): a sorted core that covers c of the
+    k*k window elements of every pixel of its tile keeps only the ranks
+    that can still hold the median; extra rows and columns are never pruned.
+
+The base networks (Sec. 4.1) are built here from textbook constructions:
+Batcher's odd-even merge generalised to any two sizes, Batcher's
+merge-sort for the small sorts, and a balanced tree of two-way merges for
+the multi-way merge.  Every merge whose needed output ranks are known is
+first trimmed to the input ranks that can reach them, and a final liveness
+pass removes every comparator half whose result is never used, so a
+compare-exchange becomes a lone min or max where only one side is needed.
+
+The result is a straight-line SSA program over "values" that the CUDA
+emitter turns into register code, and that ``evaluate`` interprets on the
+host (numpy, vectorised over many tiles) for tests.
+"""
+from __future__ import annotations
+
+import itertools
+from dataclasses import dataclass, field
+
+NEG, POS = -1, -2  # the -inf / +inf sentinels (never materialised)
+
+
+@dataclass
+class Network:
+    k: int
+    tw: int
+    th: int
+    # inputs: ("col", fx, i) = element i of the sorted column segment fx over
+    # the root core rows; ("px", fy, fx) = raw footprint pixel
+    inputs: list = field(default_factory=list)
+    ops: list = field(default_factory=list)      # (kind, a, b) kind in {"min", "max"}
+    outputs: list = field(default_factory=list)  # value id of each pixel (row-major in tile)
+    _memo: dict = field(default_factory=dict)
+
+    # ------------------------------------------------------------ values
+    def inp(self, desc):
+        v = self._memo.get(desc)
+        if v is None:
+            v = len(self.inputs) + len(self.ops)
+            self.inputs.append(desc)
+            self._ids_append(v, ("in", desc))
+            self._memo[desc] = v
+        return v
+
+    def _ids_append(self, v, what):
+        self._kind.append(what)
+
+    def __post_init__(self):
+        self._kind = []  # value id -> ("in", desc) | ("op", index)
+
+    def _op(self, kind, a, b):
+        v = len(self._kind)
+        self.ops.append((kind, a, b, v))
+        self._kind.append(("op", len(self.ops) - 1))
+        return v
+
+    def vmin(self, a, b):
+        if a == NEG or b == NEG:
+            return NEG
+        if a == POS:
+            return b
+        if b == POS:
+            return a
+        if a == b:
+            return a
+        return self._op("min", a, b)
+
+    def vmax(self, a, b):
+        if a == POS or b == POS:
+            return POS
+        if a == NEG:
+            return b
+        if b == NEG:
+            return a
+        if a == b:
+            return a
+        return self._op("max", a, b)
+
+    def cas(self, a, b):
+        return self.vmin(a, b), self.vmax(a, b)
+
+    # ------------------------------------------------------------ networks
+    def merge(self, A, B):
+        """Batcher's odd-even merge of two ascending lists of any lengths:
+        merge the even-indexed and the odd-indexed subsequences separately
+        (v, w), then compare w[i] with v[i+1]."""
+        if not A:
+            return list(B)
+        if not B:
+            return list(A)
+        if len(A) == 1 and len(B) == 1:
+            return list(self.cas(A[0], B[0]))
+        v = self.merge(A[0::2], B[0::2])
+        w = self.merge(A[1::2], B[1::2])
+        out = [v[0]]
+        for i in range(len(w)):
+            if i + 1 < len(v):
+                out.extend(self.cas(w[i], v[i + 1]))
+            else:
+                out.append(w[i])
+        out.extend(v[len(w) + 1:])
+        return out
+
+    def merge_range(self, A, B, lo, hi):
+        """Ranks lo..hi (inclusive) of merge(A, B).  Inputs that cannot
+        reach those ranks are cut first: A[i] with i < lo - |B| lies below
+        rank lo whatever B holds, A[i] with i > hi above rank hi."""
+        n = len(A) + len(B)
+        lo, hi = max(lo, 0), min(hi, n - 1)
+        if lo > hi:
+            return []
+        a0, a1 = max(0, lo - len(B)), min(len(A) - 1, hi)
+        b0, b1 = max(0, lo - len(A)), min(len(B) - 1, hi)
+        As, Bs = A[a0:a1 + 1], B[b0:b1 + 1]
+        off = a0 + b0
+        if len(As) == 1 and len(Bs) == 0:
+            return As
+        if lo - off == 0 and hi - off == len(As) + len(Bs) - 1:
+            return self.merge(As, Bs)
+        if lo == hi and len(As) + len(Bs) > 2:
+            return [self.select_one(As, Bs, lo - off)]
+        return self.merge(As, Bs)[lo - off:hi - off + 1]
+
+    def select_one(self, A, B, r):
+        """Rank r of merge(A, B) as min over i + j = r + 1 of
+        max(A[i-1], B[j-1]) (A[-1] = B[-1] = -inf): the rank-r element is
+        the smallest x with at least r + 1 elements <= x."""
+        best = POS
+        for i in range(0, r + 2):
+            j = r + 1 - i
+            if i > len(A) or j > len(B):
+                continue
+            a = A[i - 1] if i > 0 else NEG
+            b = B[j - 1] if j > 0 else NEG
+            best = self.vmin(best, self.vmax(a, b))
+        return best
+
+    def sort(self, L):
+        """Batcher's odd-even merge-sort: sort both halves, merge."""
+        if len(L) <= 1:
+            return list(L)
+        h = len(L) // 2
+        return self.merge(self.sort(L[:h]), self.sort(L[h:]))
+
+    def multiway_range(self, lists, lo, hi):
+        """Ranks lo..hi of the union of sorted lists: a balanced tree of
+        two-way merges, each restricted to the ranks that can reach lo..hi
+        (an element of rank j in a partial merge of p of the n elements ends
+        at a rank in [j, j + n - p])."""
+        lists = [l for l in lists if l]
+        if not lists:
+            return []
+        n = sum(len(l) for l in lists)
+
+        def rec(ls, lo_, hi_):
+            # ranks lo_..hi_ (clipped) of the union of ls; returns (list, offset)
+            if len(ls) == 1:
+                l = ls[0]
+                a, b = max(0, lo_), min(len(l) - 1, hi_)
+                return l[a:b + 1], a
+            h = len(ls) // 2
+            L, R = ls[:h], ls[h:]
+            nl, nr = sum(len(x) for x in L), sum(len(x) for x in R)
+            # ranks of the left partial that can reach lo_..hi_ of the whole
+            la, lb = max(0, lo_ - nr), min(nl - 1, hi_)
+            ra, rb = max(0, lo_ - nl), min(nr - 1, hi_)
+            PL, ol = rec(L, la, lb)
+            PR, orr = rec(R, ra, rb)
+            off = ol + orr
+            out = self.merge_range(PL, PR, lo_ - off, hi_ - off)
+            return out, max(lo_, 0)
+
+        out, _ = rec(lists, lo, hi)
+        return out
+
+
+def keep_range(k, c, d, n_held):
+    """Forgetfulness: with c of the k*k window elements covered by the
+    held list of n_held values and d values already dropped below the
+    median, the median sits at held ranks [max(0, m-d-u), min(n_held-1, m-d)]
+    where m = (k*k-1)/2 and u = k*k - c is the number still unseen."""
+    m = (k * k - 1) // 2
+    u = k * k - c
+    return max(0, m - d - u), min(n_held - 1, m - d)
+
+
+def build(k, tw, th=None):
+    """The full network for one root tile of tw x th pixels."""
+    th = tw if th is None else th
+    assert k % 2 == 1 and k >= 1
+    assert tw >= 1 and th >= 1 and tw & (tw - 1) == 0 and th & (th - 1) == 0
+    assert tw <= k and th <= k
+    net = Network(k, tw, th)
+    ch0 = k - th + 1  # root core height: footprint rows th-1 .. k-1
+
+    def col_seg(fx):
+        return [net.inp(("col", fx, i)) for i in range(ch0)]
+
+    def px(fy, fx):
+        return net.inp(("px", fy, fx))
+
+    # Node state: core (sorted kept list), d (dropped low), and the sorted
+    # extra rows/columns as dicts keyed by footprint row/column.
+    # Footprint coordinates: pixel (py, px) of the root tile sees footprint
+    # rows py .. py+k-1 and columns px .. px+k-1.
+    def node_core_rect(x0, y0, tw_, th_):
+        return (x0 + tw_ - 1, x0 + k - 1), (y0 + th_ - 1, y0 + k - 1)
+
+    (cx0, cx1), (cy0, cy1) = node_core_rect(0, 0, tw, th)
+    # root core: multi-way merge of the sorted core columns
+    c0 = (cx1 - cx0 + 1) * (cy1 - cy0 + 1)
+    core_cols = [col_seg(fx) for fx in range(cx0, cx1 + 1)]
+    lo, hi = keep_range(k, c0, 0, c0)
+    core = net.multiway_range(core_cols, lo, hi)
+    d = lo
+    # extra columns: footprint columns outside the core, over the core rows
+    cols = {fx: col_seg(fx) for fx in range(0, k + tw - 1) if not (cx0 <= fx <= cx1)}
+    # extra rows: footprint rows outside the core rows, over the core columns
+    rows = {fy: net.sort([px(fy, fx) for fx in range(cx0, cx1 + 1)])
+            for fy in range(0, k + th - 1) if not (cy0 <= fy <= cy1)}
+
+    outputs = {}
+
+    def recurse(x0, y0, tw_, th_, core, d, cols, rows):
+        if tw_ == 1 and th_ == 1:
+            assert len(core) == 1
+            outputs[(y0, x0)] = core[0]
+            return
+        (cx0, cx1), (cy0, cy1) = node_core_rect(x0, y0, tw_, th_)
+        if tw_ >= th_:  # horizontal split: halve the width
+            h = tw_ // 2
+            for cx in (x0, x0 + h):
+                ncx0, ncx1 = cx + h - 1, cx + k - 1
+                new = [fx for fx in range(ncx0, ncx1 + 1) if not (cx0 <= fx <= cx1)]
+                c = (ncx1 - ncx0 + 1) * (cy1 - cy0 + 1)
+                extra = net.multiway_range([cols[fx] for fx in new], 0, 10**9)
+                lo, hi = keep_range(k, c, d, len(core) + len(extra))
+                ncore = net.merge_range(core, extra, lo, hi)
+                # extra columns of the child: its footprint columns outside its core
+                ncols = {fx: cols[fx] for fx in range(cx, cx + h + k - 1)
+                         if not (ncx0 <= fx <= ncx1)}
+                # extra rows of the child: parent row + the new corners
+                nrows = {}
+                for fy, r in rows.items():
+                    if y0 <= fy <= y0 + th_ + k - 2:
+                        corners = net.sort([px(fy, fx) for fx in new])
+                        nrows[fy] = net.merge(r, corners)
+                recurse(cx, y0, h, th_, ncore, d + lo, ncols, nrows)
+        else:  # vertical split: halve the height
+            h = th_ // 2
+            for cy in (y0, y0 + h):
+                ncy0, ncy1 = cy + h - 1, cy + k - 1
+                new = [fy for fy in range(ncy0, ncy1 + 1) if not (cy0 <= fy <= cy1)]
+                c = (cx1 - cx0 + 1) * (ncy1 - ncy0 + 1)
+                extra = net.multiway_range([rows[fy] for fy in new], 0, 10**9)
+                lo, hi = keep_range(k, c, d, len(core) + len(extra))
+                ncore = net.merge_range(core, extra, lo, hi)
+                nrows = {fy: rows[fy] for fy in range(cy, cy + h + k - 1)
+                         if not (ncy0 <= fy <= ncy1)}
+                ncols = {}
+                for fx, cl in cols.items():
+                    if x0 <= fx <= x0 + tw_ + k - 2:
+                        corners = net.sort([px(fy, fx) for fy in new])
+                        ncols[fx] = net.merge(cl, corners)
+                recurse(x0, cy, tw_, h, ncore, d + lo, ncols, nrows)
+
+    recurse(0, 0, tw, th, core, d, cols, rows)
+    net.outputs = [outputs[(y, x)] for y in range(th) for x in range(tw)]
+    return prune(net)
+
+
+def prune(net):
+    """Drop every op whose value no output depends on; renumber."""
+    live = set(v for v in net.outputs if v >= 0)
+    for kind, a, b, v in reversed(net.ops):
+        if v in live:
+            live.add(a)
+            live.add(b)
+    ops = [op for op in net.ops if op[3] in live]
+    used_inputs = [i for i, desc in enumerate(net.inputs)
+                   if net._memo[desc] in live]
+    # renumber: inputs first (in first-use order), then ops
+    order = {}
+    for i in used_inputs:
+        order[net._memo[net.inputs[i]]] = len(order)
+    new_inputs = [net.inputs[i] for i in used_inputs]
+    new_ops = []
+    for kind, a, b, v in ops:
+        order[v] = len(order)
+        new_ops.append((kind, order[a], order[b], order[v]))
+    out = Network(net.k, net.tw, net.th)
+    out.inputs = new_inputs
+    out.ops = new_ops
+    out.outputs = [order[v] for v in net.outputs]
+    out._memo = {d: order[net._memo[d]] for d in new_inputs}
+    return out
+
+
+def evaluate(net, col_fn, px_fn):
+    """Run the network on the host.  col_fn(fx, i) and px_fn(fy, fx) return
+    numpy arrays (one entry per tile instance); returns the outputs."""
+    import numpy as np
+    vals = [None] * (len(net.inputs) + len(net.ops))
+    for i, desc in enumerate(net.inputs):
+        vals[i] = col_fn(desc[1], desc[2]) if desc[0] == "col" else px_fn(desc[1], desc[2])
+    for kind, a, b, v in net.ops:
+        vals[v] = np.minimum(vals[a], vals[b]) if kind == "min" else np.maximum(vals[a], vals[b])
+    return [vals[v] for v in net.outputs]
+
+
+def column_sort_network(n):
+    """The block-wide column sort: a full sort of n values (ascending)."""
+    net = Network(0, 1, 1)
+    ins = [net.inp(("in", i)) for i in range(n)]
+    net.outputs = net.sort(ins)
+    return prune(net)
+
+
+def count(net):
+    return len(net.ops)
+
+
+def default_tile(k):
+    """Root tile heuristic t(k) = 2^(floor(log2 k) - 1) (paper Sec. 4.2)."""
+    return max(1, 1 << (k.bit_length() - 2)) if k >= 2 else 1

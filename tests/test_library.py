@@ -1,0 +1,66 @@
+"""Host-side checks of the C ABI (no GPU): the library builds, loads and
+exports every function include/medianfilter.h declares, and argument errors
+come back as status codes before anything touches a device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2507_19926_gb300 as mf
+from paper_2507_19926_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()  # incremental: recompiles only what changed
+    return mf.load_library()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "medianfilter.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mf_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declarations_exported(lib):
+    names = declared_functions()
+    assert "mf_median_filter" in names and len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(mf.EXPORTS)
+
+
+def test_status_strings(lib):
+    assert mf.mf_version().startswith("medianfilter")
+    for code in range(0, -10, -1):
+        assert lib.mf_status_string(code)
+
+
+@pytest.mark.parametrize("k", [0, 2, 4, 77, -3])
+def test_rejects_bad_k(lib, k):
+    rc = lib.mf_median_filter(ctypes.c_void_p(0x10000), ctypes.c_void_p(0x90000), 8, 8, 8, 1, 0, k, 0, None)
+    assert rc == -1
+    assert b"k must be odd" in lib.mf_last_error()
+
+
+def test_rejects_bad_pitch_alias_dtype_shape(lib):
+    a, b = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x900000)
+    assert lib.mf_median_filter(a, b, 8, 8, 7, 1, 0, 3, 0, None) == -3
+    assert lib.mf_median_filter(a, b, 8, 8, 18, 1, 2, 3, 0, None) == -3   # u32 pitch not multiple of 4
+    assert lib.mf_median_filter(a, a, 8, 8, 8, 1, 0, 3, 0, None) == -4    # alias
+    assert lib.mf_median_filter(a, b, 8, 8, 8, 1, 7, 3, 0, None) == -2    # dtype
+    assert lib.mf_median_filter(a, b, 0, 8, 8, 1, 0, 3, 0, None) == -1    # H
+    assert lib.mf_median_filter(a, b, 8, 8, 8, 0, 0, 3, 0, None) == -1    # channels
+    assert lib.mf_median_filter(a, b, 8, 8, 8, 1, 0, 3, 1, None) == -1    # border
+    assert lib.mf_median_filter(None, b, 8, 8, 8, 1, 0, 3, 0, None) == -1  # null
+    assert lib.mf_median_filter_bwd(a, b, a, 8, 8, 32, 32, 1, 3, 0, None) == -4  # grad_in aliases
+    assert lib.mf_median_filter_bwd(a, b, ctypes.c_void_p(0x5000000), 8, 8, 32, 32, 1, 3, 9, None) == -1
+
+
+def test_describe_dispatch(lib):
+    d = mf.mf_describe(480, 640, 1, mf.MF_U8, 5)
+    assert "oblivious" in d and "k=5" in d
+    assert mf.mf_describe(10, 10, 1, mf.MF_F32, 1) == "identity copy"

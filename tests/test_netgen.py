@@ -1,0 +1,135 @@
+"""The network generator of the data-oblivious variant (host only).
+
+Merging networks are checked with the 0-1 principle (a comparator network
+sorts every input iff it sorts every 0/1 input), exhaustively over all
+sorted 0/1 inputs; the full hierarchical networks are interpreted on the
+host and compared with the CPU oracle on random tie-heavy images."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_19926_gb300 import netgen, synth
+
+
+def _merge_net(p, q):
+    net = netgen.Network(0, 1, 1)
+    A = [net.inp(("a", i)) for i in range(p)]
+    B = [net.inp(("b", i)) for i in range(q)]
+    net.outputs = net.merge(A, B)
+    return net
+
+
+def _run(net, env):
+    vals = {}
+    for desc in net.inputs:
+        vals[net._memo[desc]] = env[desc]
+    for kind, a, b, v in net.ops:
+        vals[v] = min(vals[a], vals[b]) if kind == "min" else max(vals[a], vals[b])
+    return [vals[v] for v in net.outputs]
+
+
+@pytest.mark.parametrize("p", range(0, 13))
+@pytest.mark.parametrize("q", range(0, 13))
+def test_merge_zero_one_principle(p, q):
+    net = _merge_net(p, q)
+    for za in range(p + 1):
+        for zb in range(q + 1):
+            env = {("a", i): int(i >= za) for i in range(p)}
+            env.update({("b", i): int(i >= zb) for i in range(q)})
+            out = _run(net, env)
+            assert out == sorted(out) and len(out) == p + q
+
+
+@pytest.mark.parametrize("n", list(range(1, 18)) + [24, 33])
+def test_sort_zero_one_principle(n):
+    net = netgen.column_sort_network(n)
+    rng = np.random.default_rng(n)
+    cases = itertools.product((0, 1), repeat=n) if n <= 14 else (tuple(rng.integers(0, 2, n)) for _ in range(4000))
+    for bits in cases:
+        env = {("in", i): bits[i] for i in range(n)}
+        out = _run(net, env)
+        assert out == sorted(bits)
+
+
+def test_merge_range_and_select_one():
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        p, q = rng.integers(0, 20, 2)
+        A, B = np.sort(rng.integers(0, 6, p)), np.sort(rng.integers(0, 6, q))
+        n = p + q
+        if n == 0:
+            continue
+        lo = int(rng.integers(0, n))
+        hi = int(rng.integers(lo, n))
+        net = netgen.Network(0, 1, 1)
+        ia = [net.inp(("a", i)) for i in range(p)]
+        ib = [net.inp(("b", i)) for i in range(q)]
+        net.outputs = net.merge_range(ia, ib, lo, hi)
+        env = {("a", i): int(A[i]) for i in range(p)}
+        env.update({("b", i): int(B[i]) for i in range(q)})
+        assert _run(net, env) == sorted(list(A) + list(B))[lo:hi + 1]
+
+
+def test_keep_range_forgetfulness():
+    # all of the window seen: exactly the median rank survives
+    assert netgen.keep_range(5, 25, 0, 25) == (12, 12)
+    # k = 5, 2x2 root tile: core 4x4 = 16 seen, 9 unseen -> ranks 3..12
+    assert netgen.keep_range(5, 16, 0, 16) == (3, 12)
+    # after dropping 3 low values the median rank among the rest is 9
+    assert netgen.keep_range(5, 20, 3, 14) == (4, 9)
+
+
+def test_default_tile_heuristic():
+    # t(k) = 2^(floor(log2 k) - 1) lies in (k/4, k/2)
+    for k in range(3, 76, 2):
+        t = netgen.default_tile(k)
+        assert k / 4 < t < k / 2
+    assert [netgen.default_tile(k) for k in (3, 5, 7, 9, 15, 17, 31, 33, 63, 65, 75)] == \
+        [1, 2, 2, 4, 4, 8, 8, 16, 16, 32, 32]
+
+
+def _run_hierarchy(img, k, tw, th, net):
+    H, W = img.shape
+    r = k // 2
+    nty, ntx = -(-H // th), -(-W // tw)
+    TY, TX = np.meshgrid(np.arange(nty), np.arange(ntx), indexing="ij")
+    TY, TX = TY.ravel(), TX.ravel()
+    cache = {}
+
+    def colseg(fx):
+        if fx not in cache:
+            xs = np.clip(TX * tw - r + fx, 0, W - 1)
+            rows = [img[np.clip(TY * th - r + fy, 0, H - 1), xs] for fy in range(th - 1, k)]
+            cache[fx] = np.sort(np.stack(rows), axis=0)
+        return cache[fx]
+
+    outs = netgen.evaluate(net, lambda fx, i: colseg(fx)[i],
+                           lambda fy, fx: img[np.clip(TY * th - r + fy, 0, H - 1),
+                                              np.clip(TX * tw - r + fx, 0, W - 1)])
+    res = np.zeros((nty * th, ntx * tw), img.dtype)
+    for i, (py, px) in enumerate([(y, x) for y in range(th) for x in range(tw)]):
+        res[TY * th + py, TX * tw + px] = outs[i]
+    return res[:H, :W]
+
+
+@pytest.mark.parametrize("k,tw,th", [(3, 1, 1), (3, 2, 2), (5, 2, 2), (5, 4, 4), (7, 4, 4), (9, 4, 4),
+                                     (9, 8, 8), (11, 4, 4), (13, 4, 4), (17, 4, 4), (7, 4, 2), (9, 2, 4)])
+def test_hierarchy_matches_oracle(k, tw, th):
+    net = netgen.build(k, tw, th)
+    for s in range(4):
+        img = (synth.levels16 if s % 2 else synth.uniform)((21, 26), "u16", 50 * k + s)
+        assert np.array_equal(_run_hierarchy(img, k, tw, th, net), oracle.median_filter(img, k))
+
+
+def test_op_counts_grow_like_k_log_k():
+    # per-pixel ops of the heuristic tile, normalised by k log2 k, stay bounded (Sec. 4.2)
+    ratios = []
+    for k in (5, 9, 17):
+        t = netgen.default_tile(k)
+        net = netgen.build(k, t)
+        cs = netgen.column_sort_network(k - t + 1)
+        per_px = len(net.ops) / (t * t) + len(cs.ops) / t
+        ratios.append(per_px / (k * np.log2(k)))
+    assert max(ratios) / min(ratios) < 3.0
