@@ -81,6 +81,14 @@ int mf_median_filter_ex(const void *src, void *dst, int H, int W, size_t pitch, 
                         mf_dtype dtype, int k, mf_border border, mf_variant variant,
                         int32_t *argidx, size_t idx_pitch, mf_stream_t stream);
 
+/* The data-aware variant (Sec. 5) with an explicit root tile of tile x tile
+ * pixels (a power of two, 2..32, at most k): every tile size is a different
+ * tiling tree (Sec. 3.1) computing the same filter.  Arguments and errors
+ * as mf_median_filter; MF_ERR_UNSUPPORTED if the tree's state for this tile
+ * does not fit in shared memory. */
+int mf_median_filter_tile(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                          mf_dtype dtype, int k, int tile, mf_stream_t stream);
+
 /* Gradient of the filter with respect to its f32 input: grad_in[p] = sum
  * of grad_out[q] over the outputs q whose argmedian is p (the median is the
  * identity on its selected input).  All pointers are caller-owned device
@@ -143,12 +151,23 @@ int mf_describe(int H, int W, int channels, mf_dtype dtype, int k, mf_variant va
 
 /* Min/max throughput microbenchmark (the denominator of the data-oblivious
  * kernels' ALU roofline; no counterpart in the paper).  kind: 0 = u32,
- * 1 = packed u16x2, 2 = f32, 3 = packed f16x2 min/max.  Runs `iters`
+ * 1 = packed u16x2, 2 = f32, 3 = packed f16x2, 4 = u16x2 min interleaved
+ * with f16x2 max, 5 = u32 min interleaved with f32 max.  Runs `iters`
  * iterations of 16 min/max per thread on 4 blocks of 256 threads per SM of
  * the current device (the library allocates and frees its own 8 KB-scale
  * buffers) and writes instructions per second (one per thread-instruction)
  * and the best of three elapsed times in milliseconds (ms may be NULL). */
 int mf_probe_minmax(int kind, int iters, double *instr_per_s, double *ms);
+
+/* Host-side check of the data-aware schedule (paper Sec. 5 method, as
+ * planned by this library): builds the plan for a k x k kernel and a
+ * tile x tile root tile and, if footprint and medians are non-NULL, runs
+ * it on the CPU for one footprint of (tile + k - 1)^2 order keys (row-major,
+ * 64-bit, clamped by the caller), writing the tile*tile medians (row-major).
+ * stats (NULL or 7 ints): shared-memory list elements, phases, tasks, work
+ * items, merged elements, sorted elements, longest sort.  No GPU is used.
+ * Returns MF_ERR_UNSUPPORTED when no plan exists for (k, tile). */
+int mf_d1_plan_check(int k, int tile, const uint64_t *footprint, uint64_t *medians, int *stats);
 
 /* Number of CUDA kernels this library launched since load (all threads). */
 uint64_t mf_kernel_launch_count(void);

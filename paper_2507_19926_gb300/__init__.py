@@ -25,10 +25,11 @@ VARIANTS = {"auto": MF_AUTO, "oblivious": MF_OBLIVIOUS, "data_aware": MF_DATA_AW
 GRAD_MODES = {"atomic": MF_GRAD_ATOMIC, "deterministic": MF_GRAD_DETERMINISTIC}
 
 # C symbols declared in include/medianfilter.h
-EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_bwd",
+EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_tile", "mf_median_filter_bwd",
            "mf_median_filter_host", "mf_batch_plan_create", "mf_batch_run",
            "mf_batch_plan_destroy", "mf_autotune", "mf_describe", "mf_kernel_launch_count",
-           "mf_status_string", "mf_last_error", "mf_version", "mf_shutdown", "mf_probe_minmax"]
+           "mf_status_string", "mf_last_error", "mf_version", "mf_shutdown", "mf_probe_minmax",
+           "mf_d1_plan_check"]
 
 
 class MedianFilterError(RuntimeError):
@@ -59,6 +60,7 @@ def load_library(path=LIB_PATH):
         vp, i, sz, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_uint64
         lib.mf_median_filter.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp]
         lib.mf_median_filter_ex.argtypes = [vp, vp, i, i, sz, i, i, i, i, i, vp, sz, vp]
+        lib.mf_median_filter_tile.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp]
         lib.mf_median_filter_bwd.argtypes = [vp, vp, vp, i, i, sz, sz, i, i, i, vp]
         lib.mf_median_filter_host.argtypes = [vp, vp, i, i, sz, i, i, i, i, i, vp]
         lib.mf_batch_plan_create.argtypes = [ctypes.POINTER(ImageDesc), i, ctypes.POINTER(vp)]
@@ -68,6 +70,7 @@ def load_library(path=LIB_PATH):
         lib.mf_describe.argtypes = [i, i, i, i, i, i, ctypes.c_char_p, sz]
         lib.mf_kernel_launch_count.restype = u64
         lib.mf_probe_minmax.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        lib.mf_d1_plan_check.argtypes = [i, i, vp, vp, vp]
         lib.mf_status_string.argtypes = [i]
         lib.mf_status_string.restype = ctypes.c_char_p
         lib.mf_last_error.restype = ctypes.c_char_p
@@ -96,6 +99,11 @@ def mf_median_filter_ex(src, dst, H, W, pitch, channels, dtype, k, border, varia
                         idx_pitch, stream=None):
     return _check(load_library().mf_median_filter_ex(src, dst, H, W, pitch, channels, dtype, k, border,
                                                      variant, argidx, idx_pitch, stream))
+
+
+def mf_median_filter_tile(src, dst, H, W, pitch, channels, dtype, k, tile, stream=None):
+    return _check(load_library().mf_median_filter_tile(src, dst, H, W, pitch, channels, dtype, k, tile,
+                                                       stream))
 
 
 def mf_median_filter_bwd(grad_out, argidx, grad_in, H, W, pitch, idx_pitch, channels, k, mode,
@@ -145,6 +153,23 @@ def mf_probe_minmax(kind, iters=4096):
     rate, ms = ctypes.c_double(), ctypes.c_double()
     _check(load_library().mf_probe_minmax(kind, iters, ctypes.byref(rate), ctypes.byref(ms)))
     return rate.value, ms.value
+
+
+def mf_d1_plan_check(k, tile, footprint=None):
+    """Builds the data-aware schedule for (k, tile); with a (tile+k-1)^2
+    uint64 footprint of keys also runs it on the CPU.  Returns (stats dict,
+    medians or None)."""
+    import numpy as np
+    st = np.zeros(7, np.int32)
+    med = None
+    fp = None
+    if footprint is not None:
+        fp = np.ascontiguousarray(footprint, dtype=np.uint64)
+        med = np.zeros(tile * tile, np.uint64)
+    _check(load_library().mf_d1_plan_check(k, tile, fp.ctypes.data if fp is not None else None,
+                                           med.ctypes.data if med is not None else None, st.ctypes.data))
+    names = ["smem_elems", "phases", "tasks", "work_items", "merged", "sorted", "max_sort"]
+    return dict(zip(names, [int(v) for v in st])), med
 
 
 def mf_version():

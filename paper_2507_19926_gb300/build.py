@@ -59,6 +59,7 @@ def _o1_instances():
 
 def generate():
     os.makedirs(GEN, exist_ok=True)
+    codegen.write_if_changed(os.path.join(GEN, "d1_sortnets.cuh"), codegen.emit_d1_sortnets())
     insts = _o1_instances()
     by_k = {}
     for inst in insts:
@@ -115,6 +116,10 @@ def _flags_hash(src, flags):
                 h.update(f.read())
     with open(os.path.join(INCLUDE, "medianfilter.h"), "rb") as f:
         h.update(f.read())
+    for name in sorted(os.listdir(GEN)):
+        if name.endswith(".cuh"):
+            with open(os.path.join(GEN, name), "rb") as f:
+                h.update(f.read())
     return h.hexdigest()[:16]
 
 

@@ -91,3 +91,27 @@ def write_if_changed(path, text):
         f.write(text)
     os.replace(tmp, path)
     return True
+
+
+def emit_d1_sortnets(sizes=(2, 4, 8, 16, 32, 64)):
+    """Register sorting networks (Batcher) for the data-aware variant's small
+    sorts, as SortNet<N>::run(v) on a register array of N keys."""
+    out = ["// generated by codegen.emit_d1_sortnets -- do not edit", "#pragma once", "namespace mf {",
+           "template <int N> struct SortNet;"]
+    for n in sizes:
+        net = netgen.column_sort_network(n)
+        out.append("template <> struct SortNet<%d> {" % n)
+        out.append("  template <class KT> static __host__ __device__ __forceinline__ void run(KT *v) {")
+        for j, desc in enumerate(net.inputs):
+            out.append("    KT v%d = v[%d];" % (j, desc[1]))
+        for kind, a, b, v in net.ops:
+            if kind == "min":
+                out.append("    KT v%d = v%d < v%d ? v%d : v%d;" % (v, a, b, a, b))
+            else:
+                out.append("    KT v%d = v%d < v%d ? v%d : v%d;" % (v, a, b, b, a))
+        for i, v in enumerate(net.outputs):
+            out.append("    v[%d] = v%d;" % (i, v))
+        out.append("  }")
+        out.append("};")
+    out.append("}  // namespace mf")
+    return "\n".join(out) + "\n"

@@ -183,6 +183,29 @@ int mf_median_filter_ex(const void *src, void *dst, int H, int W, size_t pitch, 
                       (cudaStream_t)stream);
 }
 
+int mf_median_filter_tile(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                          mf_dtype dtype, int k, int tile, mf_stream_t stream) {
+    int rc = check_fwd(src, dst, H, W, pitch, channels, dtype, k, MF_BORDER_CLAMP, nullptr, 0);
+    if (rc) return rc;
+    if (!dst) { set_error("null dst"); return MF_ERR_ARG; }
+    if (k == 1)
+        return run_filter(src, dst, H, W, pitch, channels, dtype, k, MF_AUTO, nullptr, 0, (cudaStream_t)stream);
+    if (!d1_supported_tile(k, dtype, false, tile)) {
+        set_error("no data-aware plan for k=%d with a %dx%d root tile", k, tile, tile);
+        return MF_ERR_UNSUPPORTED;
+    }
+    ImgArgs a;
+    a.src = (const char *)src;
+    a.dst = (char *)dst;
+    a.idx = nullptr;
+    a.H = H;
+    a.W = W;
+    a.pitch = pitch;
+    a.plane = (size_t)H * pitch;
+    a.idx_pitch = a.idx_plane = 0;
+    return d1_launch(a, channels, k, dtype, tile, (cudaStream_t)stream);
+}
+
 // Device staging buffers of the host entry point (one pair per process,
 // grown on demand, serialised by a mutex, released by mf_shutdown).
 static std::mutex g_stage_mu;
@@ -294,6 +317,7 @@ int mf_shutdown(void) {
     if (g_stage_dst) cudaFree(g_stage_dst);
     g_stage_src = g_stage_dst = nullptr;
     g_stage_bytes = 0;
+    d1_release_all();
     return MF_OK;
 }
 

@@ -1,0 +1,446 @@
+// Planner of the data-aware variant: turns hierarchical tiling (paper Sec. 3)
+// of one T x T root tile into a static schedule of sort and merge tasks over
+// shared-memory lists (see mf_d1_plan.h).
+//
+// State kept per level, breadth-first over the root tile's tree (tiles of
+// tw x th, NX = T/tw node columns, NY = T/th node rows):
+//   - core[j][i]: the sorted core of node (i, j) minus the extrema already
+//     discarded (forgetfulness, Sec. 2.2); all cores of a level have the
+//     same length and the same count d of values dropped below the median;
+//   - rows[i][fy]: sorted extra row fy over the core columns of node column
+//     i -- shared by every node of that column (Sec. 5.2: sorted rows are
+//     shared between vertically contiguous tiles);
+//   - cols[j][fx]: sorted extra column fx over the core rows of node row j,
+//     shared by the nodes of that row.
+// Initialisation (Sec. 3.3): sort every footprint column over the root core
+// rows and every extra row over the root core columns, then multi-way merge
+// the core columns into the root core.  Recursion (Sec. 3.4): a horizontal
+// split merges the t_w/2 new columns into one list and that into the
+// parent core, keeping the ranks that can still hold the median, and
+// extends every extra row with its t_w/2 sorted corners; a vertical split
+// exchanges rows and columns.  Merges whose needed output ranks are known
+// only read the input ranks that can reach them.
+#include <algorithm>
+#include <cstdio>
+#include <functional>
+#include <map>
+
+#include "../../include/medianfilter.h"
+#include "mf_d1_ops.cuh"
+#include "mf_d1_plan.h"
+
+namespace mf {
+
+namespace {
+
+struct Ref {
+    int list;   // -1: footprint; -2: empty
+    int start;
+    int len;
+};
+
+struct PTask {
+    int type;
+    Ref a;
+    int a_stride;
+    Ref b;
+    int lo, hi;
+    int out;    // output list id
+    int phase;
+};
+
+struct ListInfo {
+    int len;
+    int phase;      // phase that produces it
+    int last_use;   // last phase that reads it
+    bool needed;
+    int off;
+};
+
+struct Builder {
+    int k, T, FW;
+    std::vector<ListInfo> lists;
+    std::vector<PTask> tasks;
+
+    int phase_of(const Ref &r) const { return r.list >= 0 ? lists[r.list].phase : -1; }
+
+    int new_list(int len, int phase) {
+        lists.push_back(ListInfo{len, phase, -1, false, -1});
+        return (int)lists.size() - 1;
+    }
+
+    // Sorts n footprint elements at f_off + i*stride.  Runs longer than the
+    // largest register sorting network are sorted in pieces and merged.
+    Ref sort_gather(int f_off, int stride, int n) {
+        if (n > D1_MAX_SORT) {
+            std::vector<Ref> parts;
+            for (int s = 0; s < n; s += D1_MAX_SORT)
+                parts.push_back(sort_gather(f_off + s * stride, stride, std::min(D1_MAX_SORT, n - s)));
+            return multiway(parts, 0, n - 1);
+        }
+        const int id = new_list(n, 0);
+        tasks.push_back(PTask{D1_SORT, Ref{-1, f_off, n}, stride, Ref{-2, 0, 0}, 0, n - 1, id, 0});
+        return Ref{id, 0, n};
+    }
+
+    static Ref sub(const Ref &r, int a0, int a1) {  // elements a0..a1 (inclusive) of r
+        if (a1 < a0) return Ref{-2, 0, 0};
+        return Ref{r.list, r.start + a0, a1 - a0 + 1};
+    }
+
+    // Ranks lo..hi of merge(A, B).
+    Ref merge_range(const Ref &A, const Ref &B, int lo, int hi) {
+        const int n = A.len + B.len;
+        lo = std::max(lo, 0);
+        hi = std::min(hi, n - 1);
+        if (lo > hi) return Ref{-2, 0, 0};
+        const int a0 = std::max(0, lo - B.len), a1 = std::min(A.len - 1, hi);
+        const int b0 = std::max(0, lo - A.len), b1 = std::min(B.len - 1, hi);
+        const Ref As = sub(A, a0, a1), Bs = sub(B, b0, b1);
+        const int off = (As.len ? a0 : 0) + (Bs.len ? b0 : 0);
+        const int l2 = lo - off, h2 = hi - off;
+        if (Bs.len == 0) return sub(As, l2, h2);
+        if (As.len == 0) return sub(Bs, l2, h2);
+        const int phase = 1 + std::max(phase_of(As), phase_of(Bs));
+        const int id = new_list(h2 - l2 + 1, phase);
+        tasks.push_back(PTask{D1_MERGE, As, 0, Bs, l2, h2, id, phase});
+        return Ref{id, 0, h2 - l2 + 1};
+    }
+
+    Ref merge_full(const Ref &A, const Ref &B) { return merge_range(A, B, 0, A.len + B.len - 1); }
+
+    // Ranks lo..hi of the union of sorted lists: balanced tree of two-way
+    // merges, each restricted to the ranks that can reach lo..hi (a rank-j
+    // element of a partial merge of p of the n elements ends at a rank in
+    // [j, j + n - p]).
+    Ref multiway(const std::vector<Ref> &ls, int lo, int hi) {
+        std::vector<Ref> v;
+        for (const Ref &r : ls)
+            if (r.len > 0) v.push_back(r);
+        if (v.empty()) return Ref{-2, 0, 0};
+        int n = 0;
+        for (const Ref &r : v) n += r.len;
+        hi = std::min(hi, n - 1);
+        int off;
+        Ref out = rec(v, 0, (int)v.size(), lo, hi, &off);
+        (void)off;
+        return out;
+    }
+
+    Ref rec(const std::vector<Ref> &v, int b, int e, int lo, int hi, int *off) {
+        if (e - b == 1) {
+            const Ref &l = v[b];
+            const int a0 = std::max(0, lo), a1 = std::min(l.len - 1, hi);
+            *off = a0;
+            return sub(l, a0, a1);
+        }
+        const int m = (b + e) / 2;
+        int nl = 0, nr = 0;
+        for (int i = b; i < m; i++) nl += v[i].len;
+        for (int i = m; i < e; i++) nr += v[i].len;
+        const int la = std::max(0, lo - nr), lb = std::min(nl - 1, hi);
+        const int ra = std::max(0, lo - nl), rb = std::min(nr - 1, hi);
+        int ol, orr;
+        const Ref L = rec(v, b, m, la, lb, &ol);
+        const Ref R = rec(v, m, e, ra, rb, &orr);
+        const int o = (L.len ? ol : 0) + (R.len ? orr : 0);
+        *off = std::max(lo, 0);
+        return merge_range(L, R, lo - o, hi - o);
+    }
+};
+
+// Forgetfulness: ranks of the held list that can still be the median.
+static void keep_range(int k, int c, int d, int n_held, int *lo, int *hi) {
+    const int m = (k * k - 1) / 2, u = k * k - c;
+    *lo = std::max(0, m - d - u);
+    *hi = std::min(n_held - 1, m - d);
+}
+
+}  // namespace
+
+bool d1_build_plan(int k, int T, D1Plan *plan) {
+    if (k < 3 || (k & 1) == 0 || T < 2 || (T & (T - 1)) || T > k || T > 32) return false;
+    Builder B;
+    B.k = k;
+    B.T = T;
+    B.FW = T + k - 1;
+    const int FW = B.FW;
+    auto F = [&](int fy, int fx) { return fy * FW + fx; };
+
+    // ---------------------------------------------------------- initialisation
+    int tw = T, th = T;
+    // sorted column segments over the root core rows, for every footprint column
+    std::map<int, Ref> col0;
+    for (int fx = 0; fx < FW; fx++) col0[fx] = B.sort_gather(F(T - 1, fx), FW, k - T + 1);
+    // sorted extra rows over the root core columns
+    std::map<int, Ref> row0;
+    for (int fy = 0; fy < FW; fy++)
+        if (fy < T - 1 || fy > k - 1) row0[fy] = B.sort_gather(F(fy, T - 1), 1, k - T + 1);
+    // root core: multi-way merge of the core columns
+    std::vector<Ref> cc;
+    for (int fx = T - 1; fx <= k - 1; fx++) cc.push_back(col0[fx]);
+    int c = (k - T + 1) * (k - T + 1), lo, hi;
+    keep_range(k, c, 0, c, &lo, &hi);
+    int d = lo;
+    // per level state
+    std::vector<std::vector<Ref>> core(1, std::vector<Ref>(1, B.multiway(cc, lo, hi)));  // [j][i]
+    std::vector<std::map<int, Ref>> rows(1, row0);  // [i][fy]
+    std::vector<std::map<int, Ref>> cols(1);        // [j][fx]
+    for (auto &kv : col0)
+        if (kv.first < T - 1 || kv.first > k - 1) cols[0][kv.first] = kv.second;
+
+    // ---------------------------------------------------------- recursion
+    while (tw * th > 1) {
+        const int NX = T / tw, NY = T / th;
+        if (tw >= th) {  // horizontal split: halve the width
+            const int h = tw / 2;
+            const int cw = k - h + 1, ch = k - th + 1;
+            c = cw * ch;
+            const int K = core[0][0].len;
+            const int n_held = K + h * ch;
+            keep_range(k, c, d, n_held, &lo, &hi);
+            std::vector<std::vector<Ref>> ncore(NY, std::vector<Ref>(2 * NX));
+            std::vector<std::map<int, Ref>> nrows(2 * NX);
+            for (int i = 0; i < NX; i++) {
+                const int x0 = i * tw;
+                for (int s = 0; s < 2; s++) {
+                    const int nx0 = s == 0 ? x0 + h - 1 : x0 + k;  // first new core column
+                    for (int j = 0; j < NY; j++) {
+                        std::vector<Ref> nc;
+                        for (int fx = nx0; fx < nx0 + h; fx++) nc.push_back(cols[j].at(fx));
+                        const Ref extra = B.multiway(nc, 0, 1 << 30);
+                        ncore[j][2 * i + s] = B.merge_range(core[j][i], extra, lo, hi);
+                    }
+                    for (auto &kv : rows[i]) {
+                        const Ref corners = B.sort_gather(F(kv.first, nx0), 1, h);
+                        nrows[2 * i + s][kv.first] = B.merge_full(kv.second, corners);
+                    }
+                }
+            }
+            core.swap(ncore);
+            rows.swap(nrows);
+            tw = h;
+        } else {  // vertical split: halve the height
+            const int h = th / 2;
+            const int cw = k - tw + 1, ch = k - h + 1;
+            c = cw * ch;
+            const int K = core[0][0].len;
+            const int n_held = K + h * cw;
+            keep_range(k, c, d, n_held, &lo, &hi);
+            std::vector<std::vector<Ref>> ncore(2 * NY, std::vector<Ref>(NX));
+            std::vector<std::map<int, Ref>> ncols(2 * NY);
+            for (int j = 0; j < NY; j++) {
+                const int y0 = j * th;
+                for (int s = 0; s < 2; s++) {
+                    const int ny0 = s == 0 ? y0 + h - 1 : y0 + k;  // first new core row
+                    for (int i = 0; i < NX; i++) {
+                        std::vector<Ref> nr;
+                        for (int fy = ny0; fy < ny0 + h; fy++) nr.push_back(rows[i].at(fy));
+                        const Ref extra = B.multiway(nr, 0, 1 << 30);
+                        ncore[2 * j + s][i] = B.merge_range(core[j][i], extra, lo, hi);
+                    }
+                    for (auto &kv : cols[j]) {
+                        const Ref corners = B.sort_gather(F(ny0, kv.first), FW, h);
+                        ncols[2 * j + s][kv.first] = B.merge_full(kv.second, corners);
+                    }
+                }
+            }
+            core.swap(ncore);
+            cols.swap(ncols);
+            th = h;
+        }
+        d += lo;
+    }
+
+    // ---------------------------------------------------------- liveness
+    std::vector<Ref> outs(T * T);
+    for (int j = 0; j < T; j++)
+        for (int i = 0; i < T; i++) outs[j * T + i] = core[j][i];
+    for (const Ref &r : outs) {
+        if (r.len != 1) return false;
+        if (r.list >= 0) B.lists[r.list].needed = true;
+    }
+    std::vector<bool> keep(B.tasks.size(), false);
+    for (int ti = (int)B.tasks.size() - 1; ti >= 0; ti--) {
+        const PTask &t = B.tasks[ti];
+        if (!B.lists[t.out].needed) continue;
+        keep[ti] = true;
+        if (t.a.list >= 0) B.lists[t.a.list].needed = true;
+        if (t.b.list >= 0) B.lists[t.b.list].needed = true;
+    }
+    // recompute phases on the kept tasks (tasks are in creation = dependency order)
+    std::vector<int> lphase(B.lists.size(), -1);
+    int nph = 0;
+    std::vector<int> task_phase(B.tasks.size(), -1);
+    for (size_t ti = 0; ti < B.tasks.size(); ti++) {
+        if (!keep[ti]) continue;
+        const PTask &t = B.tasks[ti];
+        int p = 0;
+        if (t.a.list >= 0) p = std::max(p, lphase[t.a.list] + 1);
+        if (t.b.list >= 0) p = std::max(p, lphase[t.b.list] + 1);
+        task_phase[ti] = p;
+        lphase[t.out] = p;
+        nph = std::max(nph, p + 1);
+    }
+    // last use of every list
+    std::vector<int> last(B.lists.size(), -1);
+    for (size_t ti = 0; ti < B.tasks.size(); ti++) {
+        if (!keep[ti]) continue;
+        const PTask &t = B.tasks[ti];
+        if (t.a.list >= 0) last[t.a.list] = std::max(last[t.a.list], task_phase[ti]);
+        if (t.b.list >= 0) last[t.b.list] = std::max(last[t.b.list], task_phase[ti]);
+    }
+    for (const Ref &r : outs)
+        if (r.list >= 0) last[r.list] = nph;  // read after the last phase
+
+    // ---------------------------------------------------------- allocation
+    // first fit over a free list, phase by phase; the footprint sits at 0
+    const int base = FW * FW;
+    std::vector<std::pair<int, int>> freel;  // (off, len), sorted by off
+    int top = base;
+    std::vector<std::vector<int>> prod(nph + 1), dies(nph + 2);
+    for (size_t li = 0; li < B.lists.size(); li++) {
+        if (lphase[li] < 0) continue;
+        prod[lphase[li]].push_back((int)li);
+        dies[std::max(last[li], lphase[li]) + 1].push_back((int)li);
+    }
+    auto release = [&](int off, int len) {
+        freel.push_back({off, len});
+        std::sort(freel.begin(), freel.end());
+        std::vector<std::pair<int, int>> m;
+        for (auto &f : freel) {
+            if (!m.empty() && m.back().first + m.back().second == f.first) m.back().second += f.second;
+            else m.push_back(f);
+        }
+        freel.swap(m);
+    };
+    auto alloc = [&](int len) {
+        for (size_t i = 0; i < freel.size(); i++) {
+            if (freel[i].second >= len) {
+                const int off = freel[i].first;
+                freel[i].first += len;
+                freel[i].second -= len;
+                if (freel[i].second == 0) freel.erase(freel.begin() + i);
+                return off;
+            }
+        }
+        // grow: merge with a free block ending at top
+        if (!freel.empty() && freel.back().first + freel.back().second == top) {
+            const int off = freel.back().first;
+            top = off + len;
+            freel.pop_back();
+            return off;
+        }
+        const int off = top;
+        top += len;
+        return off;
+    };
+    for (int p = 0; p <= nph; p++) {
+        for (int li : dies[p]) release(B.lists[li].off, B.lists[li].len);
+        if (p < nph)
+            for (int li : prod[p]) B.lists[li].off = alloc(B.lists[li].len);
+    }
+
+    // ---------------------------------------------------------- emit
+    plan->k = k;
+    plan->T = T;
+    plan->FW = FW;
+    plan->smem_elems = top;
+    plan->tasks.clear();
+    plan->work.clear();
+    plan->phase_begin.clear();
+    plan->max_sort = 0;
+    plan->merge_outputs = plan->sort_elems = 0;
+    auto resolve = [&](const Ref &r) { return r.list >= 0 ? B.lists[r.list].off + r.start : (r.list == -1 ? r.start : 0); };
+    std::vector<std::vector<int>> by_phase(nph);
+    for (size_t ti = 0; ti < B.tasks.size(); ti++)
+        if (keep[ti]) by_phase[task_phase[ti]].push_back((int)ti);
+    const int NT = 256;
+    for (int p = 0; p < nph; p++) {
+        plan->phase_begin.push_back((int)plan->work.size());
+        long long outs_p = 0;
+        for (int ti : by_phase[p])
+            if (B.tasks[ti].type == D1_MERGE) outs_p += B.tasks[ti].hi - B.tasks[ti].lo + 1;
+        int chunk = (int)std::min<long long>(32, std::max<long long>(8, outs_p / NT));
+        // sorts first, grouped by size class, then merges
+        std::vector<int> order = by_phase[p];
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            const PTask &a = B.tasks[x], &b = B.tasks[y];
+            if (a.type != b.type) return a.type < b.type;
+            if (a.type == D1_SORT) return a.a.len < b.a.len;
+            return false;
+        });
+        for (int ti : order) {
+            const PTask &t = B.tasks[ti];
+            D1Task o;
+            o.type = t.type;
+            o.a_off = resolve(t.a);
+            o.a_len = t.a.len;
+            o.a_stride = t.a_stride;
+            o.b_off = resolve(t.b);
+            o.b_len = t.b.len;
+            o.lo = t.lo;
+            o.hi = t.hi;
+            o.out_off = B.lists[t.out].off;
+            const int tid = (int)plan->tasks.size();
+            if (t.type == D1_SORT) {
+                o.chunk = 0;
+                plan->work.push_back((uint32_t)tid << 12);
+                plan->max_sort = std::max(plan->max_sort, t.a.len);
+                plan->sort_elems += t.a.len;
+            } else {
+                const int n = t.hi - t.lo + 1;
+                o.chunk = std::min(chunk, n);
+                const int nchunks = (n + o.chunk - 1) / o.chunk;
+                for (int cidx = 0; cidx < nchunks; cidx++) plan->work.push_back(((uint32_t)tid << 12) | (uint32_t)cidx);
+                plan->merge_outputs += n;
+            }
+            plan->tasks.push_back(o);
+        }
+    }
+    plan->phase_begin.push_back((int)plan->work.size());
+    plan->out_off.resize(T * T);
+    for (int i = 0; i < T * T; i++) plan->out_off[i] = resolve(outs[i]);
+    return plan->tasks.size() < (1u << 20);
+}
+
+void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *medians) {
+    std::vector<uint64_t> sm(plan.smem_elems, 0xdeadbeefdeadbeefull);
+    std::copy(footprint, footprint + plan.FW * plan.FW, sm.begin());
+    const int nph = (int)plan.phase_begin.size() - 1;
+    for (int p = 0; p < nph; p++) {
+        for (int w = plan.phase_begin[p]; w < plan.phase_begin[p + 1]; w++) {
+            const D1Task &t = plan.tasks[plan.work[w] >> 12];
+            const int chunk = plan.work[w] & 4095;
+            if (t.type == D1_SORT) {
+                std::vector<uint64_t> v(t.a_len);
+                for (int i = 0; i < t.a_len; i++) v[i] = sm[t.a_off + (size_t)i * t.a_stride];
+                std::sort(v.begin(), v.end());
+                std::copy(v.begin(), v.end(), sm.begin() + t.out_off);
+            } else {
+                d1_merge_chunk<uint64_t>(sm.data(), t, chunk);
+            }
+        }
+    }
+    for (int i = 0; i < plan.T * plan.T; i++) medians[i] = sm[plan.out_off[i]];
+}
+
+}  // namespace mf
+
+// Host check of the data-aware schedule (declared in medianfilter.h).
+extern "C" int mf_d1_plan_check(int k, int tile, const uint64_t *footprint, uint64_t *medians,
+                                int *stats) {
+    mf::D1Plan plan;
+    if (!mf::d1_build_plan(k, tile, &plan)) return MF_ERR_UNSUPPORTED;
+    if (stats) {
+        stats[0] = plan.smem_elems;
+        stats[1] = (int)plan.phase_begin.size() - 1;
+        stats[2] = (int)plan.tasks.size();
+        stats[3] = (int)plan.work.size();
+        stats[4] = (int)std::min<long long>(plan.merge_outputs, 2147483647ll);
+        stats[5] = (int)std::min<long long>(plan.sort_elems, 2147483647ll);
+        stats[6] = plan.max_sort;
+    }
+    if (footprint && medians) mf::d1_run_plan_host(plan, footprint, medians);
+    return MF_OK;
+}

@@ -1,0 +1,53 @@
+// Static schedule of the data-aware variant (paper Sec. 5).
+//
+// Every list length in hierarchical tiling depends only on (k, root tile),
+// never on pixel values, so the whole recursion of one root tile -- which
+// lists are sorted, which are merged, which output ranks each merge keeps
+// -- is planned once on the host.  The plan is a sequence of phases; the
+// tasks of one phase are independent and run in parallel across a thread
+// block, with a barrier between phases.  Only the merges themselves are
+// data-aware (merge path + sequential merge, Sec. 5.1).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace mf {
+
+enum { D1_SORT = 0, D1_MERGE = 1 };
+
+// Longest list one thread sorts with a register network.
+constexpr int D1_MAX_SORT = 64;
+
+// One task.  Offsets and lengths are in list elements of shared memory.
+struct D1Task {
+    int32_t type;
+    int32_t a_off, a_len, a_stride;  // SORT: gathers a_len elements at a_off + i*a_stride
+    int32_t b_off, b_len;            // MERGE: second input (a_stride unused)
+    int32_t lo, hi;                  // MERGE: output ranks lo..hi (inclusive) of merge(A, B)
+    int32_t out_off;                 // first output element
+    int32_t chunk;                   // MERGE: outputs per work item
+};
+
+struct D1Plan {
+    int k = 0, T = 0;
+    int FW = 0;                      // footprint side T + k - 1 (footprint at offset 0, row-major)
+    int smem_elems = 0;              // shared-memory list elements needed (footprint included)
+    std::vector<D1Task> tasks;
+    std::vector<uint32_t> work;      // task << 12 | chunk, grouped by phase
+    std::vector<int32_t> phase_begin;  // phases + 1 entries into work
+    std::vector<int32_t> out_off;    // T*T: offset of each pixel's median (row-major in tile)
+    int max_sort = 0;                // longest SORT task
+    long long merge_outputs = 0;     // total merged elements (work measure)
+    long long sort_elems = 0;
+};
+
+// Builds the plan for a k x k kernel and a T x T root tile (T a power of
+// two, 2 <= T <= min(k, 32)).  Returns false if the parameters are outside
+// that range.
+bool d1_build_plan(int k, int T, D1Plan *plan);
+
+// Runs a plan on the host for one footprint of keys (FW*FW, row-major),
+// writing the T*T medians.  Used by tests to check the schedule itself.
+void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *medians);
+
+}  // namespace mf

@@ -1,18 +1,292 @@
-// Data-aware variant (paper Sec. 5) -- placeholder until the kernel lands.
+// Data-aware variant (paper Sec. 5), re-planned for sm_103a.
+//
+// The paper runs the recursion as a multi-pass pipeline of seven kernels
+// over three streams with the per-level state in global memory (up to two
+// orders of magnitude above the image size, Sec. 5.2 / 6.1).  Here one
+// thread block owns one T x T root tile and keeps the whole state of its
+// tree -- footprint, sorted columns, rows, cores -- in shared memory; the
+// statically planned phases (mf_d1_plan.cu) replace the kernel boundaries
+// with block barriers, so nothing but the image and the medians touches
+// HBM.  Within a phase, small sorts run as register networks (one thread
+// per list) and merges as merge-path chunks (one thread per chunk).
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
 
+#include "d1_sortnets.cuh"
+#include "mf_d1_ops.cuh"
 #include "mf_registry.h"
+#include "mf_tune.h"
 
 namespace mf {
-int d1_supported(int, int, bool) { return 0; }
-int d1_supported_tile(int, int, bool, int) { return 0; }
-int d1_default_tile(int, int, bool) { return 0; }
-int d1_launch(const ImgArgs &, int, int, int, int, cudaStream_t) {
-    set_error("data-aware variant not built");
-    return MF_ERR_UNSUPPORTED;
+
+constexpr int D1_NT = 256;
+constexpr size_t D1_SMEM_BUDGET = 200 * 1024;
+
+struct D1Dev {
+    const D1Task *tasks;
+    const uint32_t *work;
+    const int32_t *phase_begin;
+    const int32_t *out_off;
+    int nphases;
+    int k, T, FW;
+};
+
+template <class KT, int N>
+__device__ __forceinline__ void d1_sort_task(KT *sm, const D1Task &t) {
+    KT v[N];
+    const KT S = d1_sentinel<KT>();
+#pragma unroll
+    for (int i = 0; i < N; i++) v[i] = i < t.a_len ? sm[t.a_off + i * t.a_stride] : S;
+    SortNet<N>::run(v);
+#pragma unroll
+    for (int i = 0; i < N; i++)
+        if (i < t.a_len) sm[t.out_off + i] = v[i];
 }
-int d1_describe(int k, int, bool, int tile, char *buf, size_t n) {
-    snprintf(buf, n, "data-aware k=%d tile=%d", k, tile);
+
+template <class KT>
+__device__ __forceinline__ void d1_sort_any(KT *sm, const D1Task &t) {
+    const int n = t.a_len;
+    if (n <= 2) d1_sort_task<KT, 2>(sm, t);
+    else if (n <= 4) d1_sort_task<KT, 4>(sm, t);
+    else if (n <= 8) d1_sort_task<KT, 8>(sm, t);
+    else if (n <= 16) d1_sort_task<KT, 16>(sm, t);
+    else if (n <= 32) d1_sort_task<KT, 32>(sm, t);
+    else d1_sort_task<KT, 64>(sm, t);
+}
+
+// Element keys of the footprint: the order key (value mode) or the record
+// key << IB | footprint index (argmedian mode: equal keys then order by
+// footprint row-major position, i.e. by window slot for every pixel).
+template <int DT, class KT, bool ARG>
+struct D1Key {
+    static constexpr int IB = sizeof(KT) == 8 ? 32 : 16;
+    static __device__ __forceinline__ KT make(uint32_t key, int fidx) {
+        if (ARG) return (KT)(((unsigned long long)key << IB) | (unsigned long long)fidx);
+        return (KT)key;
+    }
+};
+
+template <class KT, int DT, bool ARG>
+__global__ void __launch_bounds__(D1_NT) d1_kernel(ImgArgs a, D1Dev p) {
+    extern __shared__ __align__(16) unsigned char d1_smem[];
+    KT *sm = reinterpret_cast<KT *>(d1_smem);
+    typedef typename Dt<DT>::E E;
+    const int tid = threadIdx.x;
+    const int T = p.T, FW = p.FW, R = (p.k - 1) / 2;
+    const int x0 = blockIdx.x * T, y0 = blockIdx.y * T;
+    const char *src = a.src + (size_t)blockIdx.z * a.plane;
+
+    // footprint, clamped to the image
+    for (int i = tid; i < FW * FW; i += D1_NT) {
+        const int fy = i / FW, fx = i - fy * FW;
+        const int y = clampi(y0 - R + fy, 0, a.H - 1);
+        const int x = clampi(x0 - R + fx, 0, a.W - 1);
+        sm[i] = D1Key<DT, KT, ARG>::make(Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, x)), i);
+    }
+    __syncthreads();
+
+    for (int ph = 0; ph < p.nphases; ph++) {
+        const int wb = p.phase_begin[ph], we = p.phase_begin[ph + 1];
+        for (int w = wb + tid; w < we; w += D1_NT) {
+            const uint32_t item = p.work[w];
+            const D1Task t = p.tasks[item >> 12];
+            if (t.type == D1_SORT) d1_sort_any<KT>(sm, t);
+            else d1_merge_chunk<KT>(sm, t, (int)(item & 4095u));
+        }
+        __syncthreads();
+    }
+
+    char *dst = a.dst ? a.dst + (size_t)blockIdx.z * a.plane : nullptr;
+    char *idx = a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)blockIdx.z * a.idx_plane : nullptr;
+    for (int i = tid; i < T * T; i += D1_NT) {
+        const int py = i / T, px = i - py * T;
+        const int y = y0 + py, x = x0 + px;
+        if (y >= a.H || x >= a.W) continue;
+        const KT v = sm[p.out_off[i]];
+        if (!ARG) {
+            reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val((uint32_t)v);
+        } else {
+            constexpr int IB = D1Key<DT, KT, ARG>::IB;
+            const int fidx = (int)((unsigned long long)v & ((1ull << IB) - 1));
+            const uint32_t key = (uint32_t)((unsigned long long)v >> IB);
+            const int fy = fidx / FW, fx = fidx - fy * FW;
+            const int ys = clampi(y0 - R + fy, 0, a.H - 1), xs = clampi(x0 - R + fx, 0, a.W - 1);
+            if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
+            if (idx) reinterpret_cast<int32_t *>(idx + (size_t)y * a.idx_pitch)[x] = ys * a.W + xs;
+        }
+    }
+}
+
+// ------------------------------------------------------------ host side
+struct D1Cached {
+    D1Plan plan;
+    D1Dev dev;
+    void *mem = nullptr;
+};
+
+static std::mutex g_d1_mu;
+// host plans by (k, T); device copies by (k, T, device)
+static std::map<std::pair<int, int>, D1Plan *> *g_plans = new std::map<std::pair<int, int>, D1Plan *>();
+static std::map<std::tuple<int, int, int>, D1Cached *> *g_d1 = new std::map<std::tuple<int, int, int>, D1Cached *>();
+
+static size_t key_bytes(int dtype, bool arg) {
+    const bool wide = dtype == MF_U32 || dtype == MF_F32;
+    if (arg) return wide ? 8 : 4;
+    return wide ? 4 : 2;
+}
+
+// Host plan for (k, T); nullptr if none exists.  No device work.
+static const D1Plan *host_plan(int k, int T) {
+    std::lock_guard<std::mutex> lk(g_d1_mu);
+    auto key = std::make_pair(k, T);
+    auto it = g_plans->find(key);
+    if (it != g_plans->end()) return it->second;
+    D1Plan *pl = new D1Plan();
+    if (!d1_build_plan(k, T, pl)) {
+        delete pl;
+        pl = nullptr;
+    }
+    (*g_plans)[key] = pl;
+    return pl;
+}
+
+// Plan for (k, T) uploaded to the current device (once per device).
+static D1Cached *get_plan(int k, int T) {
+    const D1Plan *hp = host_plan(k, T);
+    if (!hp) return nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_d1_mu);
+    auto key = std::make_tuple(k, T, dev);
+    auto it = g_d1->find(key);
+    if (it != g_d1->end()) return it->second;
+    D1Cached *c = new D1Cached();
+    c->plan = *hp;
+    const D1Plan &pl = c->plan;
+    const size_t bt = pl.tasks.size() * sizeof(D1Task), bw = pl.work.size() * 4,
+                 bp = pl.phase_begin.size() * 4, bo = pl.out_off.size() * 4;
+    const size_t total = bt + bw + bp + bo + 64;
+    if (cudaMalloc(&c->mem, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return nullptr;
+    }
+    char *m = (char *)c->mem;
+    if (cudaMemcpy(m, pl.tasks.data(), bt, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m + bt, pl.work.data(), bw, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m + bt + bw, pl.phase_begin.data(), bp, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m + bt + bw + bp, pl.out_off.data(), bo, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->mem);
+        delete c;
+        return nullptr;
+    }
+    c->dev.tasks = (const D1Task *)m;
+    c->dev.work = (const uint32_t *)(m + bt);
+    c->dev.phase_begin = (const int32_t *)(m + bt + bw);
+    c->dev.out_off = (const int32_t *)(m + bt + bw + bp);
+    c->dev.nphases = (int)pl.phase_begin.size() - 1;
+    c->dev.k = k;
+    c->dev.T = T;
+    c->dev.FW = pl.FW;
+    (*g_d1)[key] = c;
+    return c;
+}
+
+int d1_supported_tile(int k, int dtype, bool arg, int T) {
+    if (k < 3 || k > 75 || !(k & 1) || T < 2 || T > 32 || (T & (T - 1)) || T > k) return 0;
+    const D1Plan *p = host_plan(k, T);
+    if (!p) return 0;
+    return (size_t)p->smem_elems * key_bytes(dtype, arg) <= D1_SMEM_BUDGET;
+}
+
+int d1_default_tile(int k, int dtype, bool arg) {
+    const int tuned = tune_tile(k, dtype, arg);
+    if (tuned && d1_supported_tile(k, dtype, arg, tuned)) return tuned;
+    // root-tile heuristic t(k) = 2^(floor(log2 k) - 1) (paper Sec. 4.2), at
+    // least 2 and at most 16, lowered until the tree's state fits in shared
+    // memory
+    int t = 1;
+    while (t * 4 <= k) t *= 2;
+    if (t < 2) t = 2;
+    if (t > 16) t = 16;
+    for (; t >= 2; t /= 2)
+        if (d1_supported_tile(k, dtype, arg, t)) return t;
+    return 0;
+}
+
+int d1_supported(int k, int dtype, bool arg) { return d1_default_tile(k, dtype, arg) != 0; }
+
+template <class KT, int DT, bool ARG>
+static int d1_launch_t(const ImgArgs &a, int C, const D1Cached *c, cudaStream_t s) {
+    const size_t smem = (size_t)c->plan.smem_elems * sizeof(KT);
+    auto kern = d1_kernel<KT, DT, ARG>;
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM_BUDGET) !=
+            cudaSuccess)
+            return MF_ERR_CUDA;
+        configured = true;
+    }
+    dim3 grid((a.W + c->plan.T - 1) / c->plan.T, (a.H + c->plan.T - 1) / c->plan.T, C);
+    kern<<<grid, D1_NT, smem, s>>>(a, c->dev);
+    count_launch();
+    return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;
+}
+
+int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s) {
+    const bool arg = a.idx != nullptr;
+    if (T == 0) T = d1_default_tile(k, dtype, arg);
+    if (!d1_supported_tile(k, dtype, arg, T)) {
+        set_error("no data-aware plan for k=%d tile=%d", k, T);
+        return MF_ERR_UNSUPPORTED;
+    }
+    const D1Cached *c = get_plan(k, T);
+    if (!c) {
+        set_error("cannot upload the data-aware plan for k=%d tile=%d", k, T);
+        return MF_ERR_CUDA;
+    }
+    int rc;
+    switch (dtype * 2 + (arg ? 1 : 0)) {
+        case MF_U8 * 2: rc = d1_launch_t<uint16_t, MF_U8, false>(a, C, c, s); break;
+        case MF_U16 * 2: rc = d1_launch_t<uint16_t, MF_U16, false>(a, C, c, s); break;
+        case MF_U32 * 2: rc = d1_launch_t<uint32_t, MF_U32, false>(a, C, c, s); break;
+        case MF_F32 * 2: rc = d1_launch_t<uint32_t, MF_F32, false>(a, C, c, s); break;
+        case MF_U8 * 2 + 1: rc = d1_launch_t<uint32_t, MF_U8, true>(a, C, c, s); break;
+        case MF_U16 * 2 + 1: rc = d1_launch_t<uint32_t, MF_U16, true>(a, C, c, s); break;
+        case MF_U32 * 2 + 1: rc = d1_launch_t<unsigned long long, MF_U32, true>(a, C, c, s); break;
+        case MF_F32 * 2 + 1: rc = d1_launch_t<unsigned long long, MF_F32, true>(a, C, c, s); break;
+        default: set_error("bad dtype"); return MF_ERR_DTYPE;
+    }
+    if (rc == MF_ERR_CUDA) set_error("data-aware kernel: %s", cudaGetErrorString(cudaGetLastError()));
+    return rc;
+}
+
+int d1_describe(int k, int dtype, bool arg, int T, char *buf, size_t n) {
+    const D1Plan *p = T ? host_plan(k, T) : nullptr;
+    if (!p) {
+        snprintf(buf, n, "data-aware k=%d (no plan)", k);
+        return MF_OK;
+    }
+    snprintf(buf, n, "data-aware k=%d tile=%dx%d block=%d smem=%zuB phases=%d tasks=%zu merged/px=%.1f sorted/px=%.1f",
+             k, T, T, D1_NT, (size_t)p->smem_elems * key_bytes(dtype, arg), (int)p->phase_begin.size() - 1,
+             p->tasks.size(), (double)p->merge_outputs / (T * T), (double)p->sort_elems / (T * T));
     return MF_OK;
 }
+
+void d1_release_all() {
+    std::lock_guard<std::mutex> lk(g_d1_mu);
+    for (auto &kv : *g_d1)
+        if (kv.second) {
+            cudaFree(kv.second->mem);
+            delete kv.second;
+        }
+    g_d1->clear();
+}
+
 }  // namespace mf

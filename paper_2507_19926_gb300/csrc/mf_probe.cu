@@ -11,19 +11,23 @@ namespace mf {
 template <int KIND>
 __device__ __forceinline__ uint32_t pmin(uint32_t a, uint32_t b) {
     uint32_t d;
-    if (KIND == 0) d = umin(a, b);
+    if (KIND == 0) asm("min.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     if (KIND == 1) asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     if (KIND == 2) d = __float_as_uint(fminf(__uint_as_float(a), __uint_as_float(b)));
     if (KIND == 3) asm("min.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    if (KIND == 4) asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    if (KIND == 5) asm("min.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     return d;
 }
 template <int KIND>
 __device__ __forceinline__ uint32_t pmax(uint32_t a, uint32_t b) {
     uint32_t d;
-    if (KIND == 0) d = umax(a, b);
+    if (KIND == 0) asm("max.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     if (KIND == 1) asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     if (KIND == 2) d = __float_as_uint(fmaxf(__uint_as_float(a), __uint_as_float(b)));
     if (KIND == 3) asm("max.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    if (KIND == 4) asm("max.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    if (KIND == 5) d = __float_as_uint(fmaxf(__uint_as_float(a), __uint_as_float(b)));
     return d;
 }
 
@@ -53,11 +57,12 @@ __global__ void __launch_bounds__(256) probe_kernel(const uint32_t *in, uint32_t
 
 using namespace mf;
 
-// kind: 0 u32 min/max, 1 u16x2 min/max, 2 f32 min/max, 3 f16x2 min/max.
+// kind: 0 u32 min/max, 1 u16x2 min/max, 2 f32 min/max, 3 f16x2 min/max,
+// 4 u16x2 min interleaved with f16x2 max, 5 u32 min interleaved with f32 max.
 // Writes min/max instructions per second (per warp-lane instruction) and
 // the elapsed milliseconds; buffers are allocated and freed here.
 extern "C" int mf_probe_minmax(int kind, int iters, double *instr_per_s, double *ms_out) {
-    if (kind < 0 || kind > 3 || iters < 1 || !instr_per_s) { set_error("bad probe arguments"); return MF_ERR_ARG; }
+    if (kind < 0 || kind > 5 || iters < 1 || !instr_per_s) { set_error("bad probe arguments"); return MF_ERR_ARG; }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -71,7 +76,8 @@ extern "C" int mf_probe_minmax(int kind, int iters, double *instr_per_s, double 
     }
     cudaMemset(in, 0x5a, 1024 * 4);
     void (*kern)(const uint32_t *, uint32_t *, int) =
-        kind == 0 ? probe_kernel<0> : kind == 1 ? probe_kernel<1> : kind == 2 ? probe_kernel<2> : probe_kernel<3>;
+        kind == 0 ? probe_kernel<0> : kind == 1 ? probe_kernel<1> : kind == 2 ? probe_kernel<2>
+        : kind == 3 ? probe_kernel<3> : kind == 4 ? probe_kernel<4> : probe_kernel<5>;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

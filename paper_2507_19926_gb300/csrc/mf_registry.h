@@ -29,6 +29,7 @@ int d1_launch(const ImgArgs &a, int channels, int k, int dtype, int tile, cudaSt
 int d1_default_tile(int k, int dtype, bool arg);
 int d1_supported_tile(int k, int dtype, bool arg, int tile);
 int d1_describe(int k, int dtype, bool arg, int tile, char *buf, size_t n);
+void d1_release_all();
 
 // Identity argmedian for k = 1 and small helpers (mf_api.cu).
 int launch_identity_idx(const ImgArgs &a, int channels, cudaStream_t s);

@@ -1,0 +1,63 @@
+"""The data-aware schedule (host side, no GPU): for each (k, root tile) the
+planned sorts and merges, run on the CPU with the same merge code the kernel
+uses, must give the oracle's medians for a root tile's footprint."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_19926_gb300 as mf
+from paper_2507_19926_gb300 import build, synth
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    mf.load_library()
+
+
+CASES = [(3, 2), (5, 2), (5, 4), (7, 4), (9, 2), (9, 8), (11, 4), (13, 8), (17, 8), (17, 16),
+         (21, 8), (25, 16), (31, 16), (45, 16), (61, 16), (75, 16), (75, 8), (33, 32)]
+
+
+@pytest.mark.parametrize("k,T", CASES)
+def test_plan_matches_oracle(k, T):
+    FW = T + k - 1
+    r = k // 2
+    for s in range(2):
+        gen = synth.levels16 if s else synth.uniform
+        img = gen((FW, FW), "u16", 7 * k + T + s)
+        st, med = mf.mf_d1_plan_check(k, T, img.astype(np.uint64).ravel())
+        want = oracle.median_filter(img, k)[r:r + T, r:r + T].ravel()
+        assert np.array_equal(med.astype(np.uint16), want), (k, T, s)
+    assert st["phases"] >= 3 and st["max_sort"] <= 64
+
+
+def test_plan_argmedian_records():
+    # 64-bit records key << 32 | footprint index: the winner's index is the
+    # oracle's argmedian (lowest value, then lowest row-major window slot)
+    k, T = 9, 4
+    FW = T + k - 1
+    r = k // 2
+    img = synth.levels16((FW, FW), "u8", 3).astype(np.uint64)
+    rec = (img.ravel() << np.uint64(32)) | np.arange(FW * FW, dtype=np.uint64)
+    _, med = mf.mf_d1_plan_check(k, T, rec)
+    _, idx = oracle.median_filter(img.astype(np.uint8), k, with_idx=True)
+    want = idx[r:r + T, r:r + T].ravel()
+    got = (med & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    assert np.array_equal(got, want)
+
+
+def test_plan_rejects_bad_tiles():
+    with pytest.raises(mf.MedianFilterError):
+        mf.mf_d1_plan_check(5, 8)
+    with pytest.raises(mf.MedianFilterError):
+        mf.mf_d1_plan_check(9, 3)
+
+
+def test_work_per_pixel_linear_in_k():
+    # data-aware recursion: merged elements per pixel grow about linearly in k (Sec. 5.2)
+    per = []
+    for k in (17, 33, 65):
+        st, _ = mf.mf_d1_plan_check(k, 16)
+        per.append(st["merged"] / 256 / k)
+    assert max(per) / min(per) < 2.0
