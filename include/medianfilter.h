@@ -160,14 +160,16 @@ int mf_describe(int H, int W, int channels, mf_dtype dtype, int k, mf_variant va
 int mf_probe_minmax(int kind, int iters, double *instr_per_s, double *ms);
 
 /* Host-side check of the data-aware schedule (paper Sec. 5 method, as
- * planned by this library): builds the plan for a k x k kernel and a
- * tile x tile root tile and, if footprint and medians are non-NULL, runs
- * it on the CPU for one footprint of (tile + k - 1)^2 order keys (row-major,
- * 64-bit, clamped by the caller), writing the tile*tile medians (row-major).
- * stats (NULL or 7 ints): shared-memory list elements, phases, tasks, work
- * items, merged elements, sorted elements, longest sort.  No GPU is used.
- * Returns MF_ERR_UNSUPPORTED when no plan exists for (k, tile). */
-int mf_d1_plan_check(int k, int tile, const uint64_t *footprint, uint64_t *medians, int *stats);
+ * planned by this library): builds the plan for a k x k kernel and a strip
+ * of `strip` root tiles of tile x tile pixels side by side and, if
+ * footprint and medians are non-NULL, runs it on the CPU for one footprint
+ * of (tile + k - 1) rows x (strip*tile + k - 1) columns of 64-bit order keys
+ * (row-major, clamped by the caller), writing the tile x strip*tile medians
+ * (row-major).  stats (NULL or 7 ints): shared-memory list elements, phases,
+ * tasks, work items, merged elements, sorted elements, longest sort.  No GPU
+ * is used.  Returns MF_ERR_UNSUPPORTED when no plan exists. */
+int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,
+                     int *stats);
 
 /* Number of CUDA kernels this library launched since load (all threads). */
 uint64_t mf_kernel_launch_count(void);

@@ -70,7 +70,7 @@ def load_library(path=LIB_PATH):
         lib.mf_describe.argtypes = [i, i, i, i, i, i, ctypes.c_char_p, sz]
         lib.mf_kernel_launch_count.restype = u64
         lib.mf_probe_minmax.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
-        lib.mf_d1_plan_check.argtypes = [i, i, vp, vp, vp]
+        lib.mf_d1_plan_check.argtypes = [i, i, i, vp, vp, vp]
         lib.mf_status_string.argtypes = [i]
         lib.mf_status_string.restype = ctypes.c_char_p
         lib.mf_last_error.restype = ctypes.c_char_p
@@ -155,18 +155,18 @@ def mf_probe_minmax(kind, iters=4096):
     return rate.value, ms.value
 
 
-def mf_d1_plan_check(k, tile, footprint=None):
-    """Builds the data-aware schedule for (k, tile); with a (tile+k-1)^2
-    uint64 footprint of keys also runs it on the CPU.  Returns (stats dict,
-    medians or None)."""
+def mf_d1_plan_check(k, tile, footprint=None, strip=1):
+    """Builds the data-aware schedule for (k, tile, strip); with a uint64
+    footprint of keys ((tile+k-1) x (strip*tile+k-1)) also runs it on the
+    CPU.  Returns (stats dict, tile x strip*tile medians or None)."""
     import numpy as np
     st = np.zeros(7, np.int32)
     med = None
     fp = None
     if footprint is not None:
         fp = np.ascontiguousarray(footprint, dtype=np.uint64)
-        med = np.zeros(tile * tile, np.uint64)
-    _check(load_library().mf_d1_plan_check(k, tile, fp.ctypes.data if fp is not None else None,
+        med = np.zeros(tile * tile * strip, np.uint64)
+    _check(load_library().mf_d1_plan_check(k, tile, strip, fp.ctypes.data if fp is not None else None,
                                            med.ctypes.data if med is not None else None, st.ctypes.data))
     names = ["smem_elems", "phases", "tasks", "work_items", "merged", "sorted", "max_sort"]
     return dict(zip(names, [int(v) for v in st])), med

@@ -158,23 +158,29 @@ static void keep_range(int k, int c, int d, int n_held, int *lo, int *hi) {
 
 }  // namespace
 
-bool d1_build_plan(int k, int T, D1Plan *plan) {
-    if (k < 3 || (k & 1) == 0 || T < 2 || (T & (T - 1)) || T > k || T > 32) return false;
+bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt) {
+    if (k < 3 || (k & 1) == 0 || T < 2 || (T & (T - 1)) || T > k || T > 32 || NB < 1 || NB > 64) return false;
     Builder B;
     B.k = k;
     B.T = T;
-    B.FW = T + k - 1;
-    const int FW = B.FW;
-    auto F = [&](int fy, int fx) { return fy * FW + fx; };
+    B.FW = NB * T + k - 1;
+    const int FW = B.FW, FH = T + k - 1;
+    // sorted column segments over the root core rows, for every footprint
+    // column of the strip: horizontally adjacent root tiles share them
+    std::map<int, Ref> col_strip;
+    for (int fx = 0; fx < FW; fx++) col_strip[fx] = B.sort_gather((T - 1) * FW + fx, FW, k - T + 1);
+    std::vector<Ref> outs(NB * T * T);
+    for (int tb = 0; tb < NB; tb++) {
+    const int bx = tb * T;  // strip column of this root tile's footprint
+    auto F = [&](int fy, int fx) { return fy * FW + bx + fx; };
 
     // ---------------------------------------------------------- initialisation
     int tw = T, th = T;
-    // sorted column segments over the root core rows, for every footprint column
     std::map<int, Ref> col0;
-    for (int fx = 0; fx < FW; fx++) col0[fx] = B.sort_gather(F(T - 1, fx), FW, k - T + 1);
+    for (int fx = 0; fx < T + k - 1; fx++) col0[fx] = col_strip[bx + fx];
     // sorted extra rows over the root core columns
     std::map<int, Ref> row0;
-    for (int fy = 0; fy < FW; fy++)
+    for (int fy = 0; fy < FH; fy++)
         if (fy < T - 1 || fy > k - 1) row0[fy] = B.sort_gather(F(fy, T - 1), 1, k - T + 1);
     // root core: multi-way merge of the core columns
     std::vector<Ref> cc;
@@ -252,10 +258,11 @@ bool d1_build_plan(int k, int T, D1Plan *plan) {
         d += lo;
     }
 
-    // ---------------------------------------------------------- liveness
-    std::vector<Ref> outs(T * T);
     for (int j = 0; j < T; j++)
-        for (int i = 0; i < T; i++) outs[j * T + i] = core[j][i];
+        for (int i = 0; i < T; i++) outs[j * NB * T + bx + i] = core[j][i];
+    }  // root tiles of the strip
+
+    // ---------------------------------------------------------- liveness
     for (const Ref &r : outs) {
         if (r.len != 1) return false;
         if (r.list >= 0) B.lists[r.list].needed = true;
@@ -295,7 +302,7 @@ bool d1_build_plan(int k, int T, D1Plan *plan) {
 
     // ---------------------------------------------------------- allocation
     // first fit over a free list, phase by phase; the footprint sits at 0
-    const int base = FW * FW;
+    const int base = FW * FH;
     std::vector<std::pair<int, int>> freel;  // (off, len), sorted by off
     int top = base;
     std::vector<std::vector<int>> prod(nph + 1), dies(nph + 2);
@@ -344,7 +351,10 @@ bool d1_build_plan(int k, int T, D1Plan *plan) {
     // ---------------------------------------------------------- emit
     plan->k = k;
     plan->T = T;
+    plan->B = NB;
     plan->FW = FW;
+    plan->FH = FH;
+    plan->nt = nt;
     plan->smem_elems = top;
     plan->tasks.clear();
     plan->work.clear();
@@ -355,13 +365,13 @@ bool d1_build_plan(int k, int T, D1Plan *plan) {
     std::vector<std::vector<int>> by_phase(nph);
     for (size_t ti = 0; ti < B.tasks.size(); ti++)
         if (keep[ti]) by_phase[task_phase[ti]].push_back((int)ti);
-    const int NT = 256;
     for (int p = 0; p < nph; p++) {
         plan->phase_begin.push_back((int)plan->work.size());
         long long outs_p = 0;
         for (int ti : by_phase[p])
             if (B.tasks[ti].type == D1_MERGE) outs_p += B.tasks[ti].hi - B.tasks[ti].lo + 1;
-        int chunk = (int)std::min<long long>(32, std::max<long long>(8, outs_p / NT));
+        // about two chunks per thread, each 4..32 outputs long
+        int chunk = (int)std::min<long long>(32, std::max<long long>(4, outs_p / (2 * nt)));
         // sorts first, grouped by size class, then merges
         std::vector<int> order = by_phase[p];
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -399,14 +409,14 @@ bool d1_build_plan(int k, int T, D1Plan *plan) {
         }
     }
     plan->phase_begin.push_back((int)plan->work.size());
-    plan->out_off.resize(T * T);
-    for (int i = 0; i < T * T; i++) plan->out_off[i] = resolve(outs[i]);
+    plan->out_off.resize(NB * T * T);
+    for (int i = 0; i < NB * T * T; i++) plan->out_off[i] = resolve(outs[i]);
     return plan->tasks.size() < (1u << 20);
 }
 
 void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *medians) {
     std::vector<uint64_t> sm(plan.smem_elems, 0xdeadbeefdeadbeefull);
-    std::copy(footprint, footprint + plan.FW * plan.FW, sm.begin());
+    std::copy(footprint, footprint + plan.FW * plan.FH, sm.begin());
     const int nph = (int)plan.phase_begin.size() - 1;
     for (int p = 0; p < nph; p++) {
         for (int w = plan.phase_begin[p]; w < plan.phase_begin[p + 1]; w++) {
@@ -422,16 +432,16 @@ void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *m
             }
         }
     }
-    for (int i = 0; i < plan.T * plan.T; i++) medians[i] = sm[plan.out_off[i]];
+    for (int i = 0; i < plan.B * plan.T * plan.T; i++) medians[i] = sm[plan.out_off[i]];
 }
 
 }  // namespace mf
 
 // Host check of the data-aware schedule (declared in medianfilter.h).
-extern "C" int mf_d1_plan_check(int k, int tile, const uint64_t *footprint, uint64_t *medians,
+extern "C" int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,
                                 int *stats) {
     mf::D1Plan plan;
-    if (!mf::d1_build_plan(k, tile, &plan)) return MF_ERR_UNSUPPORTED;
+    if (!mf::d1_build_plan(k, tile, &plan, strip)) return MF_ERR_UNSUPPORTED;
     if (stats) {
         stats[0] = plan.smem_elems;
         stats[1] = (int)plan.phase_begin.size() - 1;

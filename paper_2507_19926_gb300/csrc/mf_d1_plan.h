@@ -30,24 +30,29 @@ struct D1Task {
 
 struct D1Plan {
     int k = 0, T = 0;
-    int FW = 0;                      // footprint side T + k - 1 (footprint at offset 0, row-major)
+    int B = 1;                       // root tiles per strip (side by side horizontally)
+    int FW = 0;                      // footprint width B*T + k - 1 (footprint at offset 0, row-major)
+    int FH = 0;                      // footprint height T + k - 1
+    int nt = 256;                    // threads per block the chunking targets
     int smem_elems = 0;              // shared-memory list elements needed (footprint included)
     std::vector<D1Task> tasks;
     std::vector<uint32_t> work;      // task << 12 | chunk, grouped by phase
     std::vector<int32_t> phase_begin;  // phases + 1 entries into work
-    std::vector<int32_t> out_off;    // T*T: offset of each pixel's median (row-major in tile)
+    std::vector<int32_t> out_off;    // T * B*T: offset of each pixel's median (row-major in the strip)
     int max_sort = 0;                // longest SORT task
     long long merge_outputs = 0;     // total merged elements (work measure)
     long long sort_elems = 0;
 };
 
-// Builds the plan for a k x k kernel and a T x T root tile (T a power of
-// two, 2 <= T <= min(k, 32)).  Returns false if the parameters are outside
-// that range.
-bool d1_build_plan(int k, int T, D1Plan *plan);
+// Builds the plan for a k x k kernel and a strip of B root tiles of T x T
+// (T a power of two, 2 <= T <= min(k, 32); B >= 1), chunking merges for
+// blocks of nt threads.  The strip's footprint columns are sorted once and
+// shared by its tiles (paper Sec. 3.3).  Returns false outside that range.
+bool d1_build_plan(int k, int T, D1Plan *plan, int B = 1, int nt = 256);
 
-// Runs a plan on the host for one footprint of keys (FW*FW, row-major),
-// writing the T*T medians.  Used by tests to check the schedule itself.
+// Runs a plan on the host for one footprint of keys (FH*FW, row-major),
+// writing the T * B*T medians (row-major).  Used by tests to check the
+// schedule itself.
 void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *medians);
 
 }  // namespace mf

@@ -21,8 +21,11 @@
 
 namespace mf {
 
-constexpr int D1_NT = 256;
+constexpr int D1_NT_MAX = 512;
 constexpr size_t D1_SMEM_BUDGET = 200 * 1024;
+// A strip whose state fits in this much shared memory runs with 256
+// threads, several blocks per SM; bigger ones run alone with 512 threads.
+constexpr size_t D1_SMEM_SMALL = 56 * 1024;
 
 struct D1Dev {
     const D1Task *tasks;
@@ -30,7 +33,7 @@ struct D1Dev {
     const int32_t *phase_begin;
     const int32_t *out_off;
     int nphases;
-    int k, T, FW;
+    int k, T, B, FW, FH;
 };
 
 template <class KT, int N>
@@ -45,15 +48,18 @@ __device__ __forceinline__ void d1_sort_task(KT *sm, const D1Task &t) {
         if (i < t.a_len) sm[t.out_off + i] = v[i];
 }
 
-template <class KT>
+// NMAX: the longest sort of the plan, rounded up to a power of two; the
+// kernel is instantiated per NMAX so that short plans do not pay for the
+// registers of a 64-element network.
+template <class KT, int NMAX>
 __device__ __forceinline__ void d1_sort_any(KT *sm, const D1Task &t) {
     const int n = t.a_len;
     if (n <= 2) d1_sort_task<KT, 2>(sm, t);
     else if (n <= 4) d1_sort_task<KT, 4>(sm, t);
-    else if (n <= 8) d1_sort_task<KT, 8>(sm, t);
-    else if (n <= 16) d1_sort_task<KT, 16>(sm, t);
-    else if (n <= 32) d1_sort_task<KT, 32>(sm, t);
-    else d1_sort_task<KT, 64>(sm, t);
+    else if (NMAX <= 8 || n <= 8) d1_sort_task<KT, (NMAX < 8 ? NMAX : 8)>(sm, t);
+    else if (NMAX <= 16 || n <= 16) d1_sort_task<KT, (NMAX < 16 ? NMAX : 16)>(sm, t);
+    else if (NMAX <= 32 || n <= 32) d1_sort_task<KT, (NMAX < 32 ? NMAX : 32)>(sm, t);
+    else d1_sort_task<KT, NMAX>(sm, t);
 }
 
 // Element keys of the footprint: the order key (value mode) or the record
@@ -68,18 +74,18 @@ struct D1Key {
     }
 };
 
-template <class KT, int DT, bool ARG>
-__global__ void __launch_bounds__(D1_NT) d1_kernel(ImgArgs a, D1Dev p) {
+template <class KT, int DT, bool ARG, int NMAX>
+__global__ void __launch_bounds__(D1_NT_MAX) d1_kernel(ImgArgs a, D1Dev p) {
     extern __shared__ __align__(16) unsigned char d1_smem[];
     KT *sm = reinterpret_cast<KT *>(d1_smem);
     typedef typename Dt<DT>::E E;
-    const int tid = threadIdx.x;
-    const int T = p.T, FW = p.FW, R = (p.k - 1) / 2;
-    const int x0 = blockIdx.x * T, y0 = blockIdx.y * T;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int T = p.T, FW = p.FW, FH = p.FH, R = (p.k - 1) / 2, SW = p.B * p.T;
+    const int x0 = blockIdx.x * SW, y0 = blockIdx.y * T;
     const char *src = a.src + (size_t)blockIdx.z * a.plane;
 
-    // footprint, clamped to the image
-    for (int i = tid; i < FW * FW; i += D1_NT) {
+    // footprint of the strip, clamped to the image
+    for (int i = tid; i < FW * FH; i += NT) {
         const int fy = i / FW, fx = i - fy * FW;
         const int y = clampi(y0 - R + fy, 0, a.H - 1);
         const int x = clampi(x0 - R + fx, 0, a.W - 1);
@@ -89,10 +95,10 @@ __global__ void __launch_bounds__(D1_NT) d1_kernel(ImgArgs a, D1Dev p) {
 
     for (int ph = 0; ph < p.nphases; ph++) {
         const int wb = p.phase_begin[ph], we = p.phase_begin[ph + 1];
-        for (int w = wb + tid; w < we; w += D1_NT) {
+        for (int w = wb + tid; w < we; w += NT) {
             const uint32_t item = p.work[w];
             const D1Task t = p.tasks[item >> 12];
-            if (t.type == D1_SORT) d1_sort_any<KT>(sm, t);
+            if (t.type == D1_SORT) d1_sort_any<KT, NMAX>(sm, t);
             else d1_merge_chunk<KT>(sm, t, (int)(item & 4095u));
         }
         __syncthreads();
@@ -100,8 +106,8 @@ __global__ void __launch_bounds__(D1_NT) d1_kernel(ImgArgs a, D1Dev p) {
 
     char *dst = a.dst ? a.dst + (size_t)blockIdx.z * a.plane : nullptr;
     char *idx = a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)blockIdx.z * a.idx_plane : nullptr;
-    for (int i = tid; i < T * T; i += D1_NT) {
-        const int py = i / T, px = i - py * T;
+    for (int i = tid; i < T * SW; i += NT) {
+        const int py = i / SW, px = i - py * SW;
         const int y = y0 + py, x = x0 + px;
         if (y >= a.H || x >= a.W) continue;
         const KT v = sm[p.out_off[i]];
@@ -127,9 +133,10 @@ struct D1Cached {
 };
 
 static std::mutex g_d1_mu;
-// host plans by (k, T); device copies by (k, T, device)
-static std::map<std::pair<int, int>, D1Plan *> *g_plans = new std::map<std::pair<int, int>, D1Plan *>();
-static std::map<std::tuple<int, int, int>, D1Cached *> *g_d1 = new std::map<std::tuple<int, int, int>, D1Cached *>();
+typedef std::tuple<int, int, int, int> PlanKey;  // k, T, B, nt
+static std::map<PlanKey, D1Plan *> *g_plans = new std::map<PlanKey, D1Plan *>();
+static std::map<std::tuple<int, int, int, int, int>, D1Cached *> *g_d1 =
+    new std::map<std::tuple<int, int, int, int, int>, D1Cached *>();
 
 static size_t key_bytes(int dtype, bool arg) {
     const bool wide = dtype == MF_U32 || dtype == MF_F32;
@@ -137,14 +144,14 @@ static size_t key_bytes(int dtype, bool arg) {
     return wide ? 4 : 2;
 }
 
-// Host plan for (k, T); nullptr if none exists.  No device work.
-static const D1Plan *host_plan(int k, int T) {
+// Host plan; nullptr if none exists.  No device work.
+static const D1Plan *host_plan(int k, int T, int B, int nt) {
     std::lock_guard<std::mutex> lk(g_d1_mu);
-    auto key = std::make_pair(k, T);
+    const PlanKey key(k, T, B, nt);
     auto it = g_plans->find(key);
     if (it != g_plans->end()) return it->second;
     D1Plan *pl = new D1Plan();
-    if (!d1_build_plan(k, T, pl)) {
+    if (!d1_build_plan(k, T, pl, B, nt)) {
         delete pl;
         pl = nullptr;
     }
@@ -152,9 +159,32 @@ static const D1Plan *host_plan(int k, int T) {
     return pl;
 }
 
-// Plan for (k, T) uploaded to the current device (once per device).
-static D1Cached *get_plan(int k, int T) {
-    const D1Plan *hp = host_plan(k, T);
+// Strip width and block size for a root tile: the widest strip (sharing the
+// most column sorts) whose state fits the small budget runs with 256 threads
+// and several blocks per SM; otherwise one tile with 512 threads.
+static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt) {
+    if (k < 3 || k > 75 || !(k & 1) || T < 2 || T > 32 || (T & (T - 1)) || T > k) return false;
+    const size_t kb = key_bytes(dtype, arg);
+    for (int b = 8; b >= 1; b /= 2) {
+        const D1Plan *p = host_plan(k, T, b, 256);
+        if (p && (size_t)p->smem_elems * kb <= D1_SMEM_SMALL) {
+            *B = b;
+            *nt = 256;
+            return true;
+        }
+    }
+    const D1Plan *p = host_plan(k, T, 1, 512);
+    if (p && (size_t)p->smem_elems * kb <= D1_SMEM_BUDGET) {
+        *B = 1;
+        *nt = 512;
+        return true;
+    }
+    return false;
+}
+
+// Plan uploaded to the current device (once per device).
+static D1Cached *get_plan(int k, int T, int B, int nt) {
+    const D1Plan *hp = host_plan(k, T, B, nt);
     if (!hp) return nullptr;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -162,7 +192,7 @@ static D1Cached *get_plan(int k, int T) {
         return nullptr;
     }
     std::lock_guard<std::mutex> lk(g_d1_mu);
-    auto key = std::make_tuple(k, T, dev);
+    auto key = std::make_tuple(k, T, B, nt, dev);
     auto it = g_d1->find(key);
     if (it != g_d1->end()) return it->second;
     D1Cached *c = new D1Cached();
@@ -193,16 +223,16 @@ static D1Cached *get_plan(int k, int T) {
     c->dev.nphases = (int)pl.phase_begin.size() - 1;
     c->dev.k = k;
     c->dev.T = T;
+    c->dev.B = B;
     c->dev.FW = pl.FW;
+    c->dev.FH = pl.FH;
     (*g_d1)[key] = c;
     return c;
 }
 
 int d1_supported_tile(int k, int dtype, bool arg, int T) {
-    if (k < 3 || k > 75 || !(k & 1) || T < 2 || T > 32 || (T & (T - 1)) || T > k) return 0;
-    const D1Plan *p = host_plan(k, T);
-    if (!p) return 0;
-    return (size_t)p->smem_elems * key_bytes(dtype, arg) <= D1_SMEM_BUDGET;
+    int B, nt;
+    return choose_config(k, dtype, arg, T, &B, &nt) ? 1 : 0;
 }
 
 int d1_default_tile(int k, int dtype, bool arg) {
@@ -222,10 +252,10 @@ int d1_default_tile(int k, int dtype, bool arg) {
 
 int d1_supported(int k, int dtype, bool arg) { return d1_default_tile(k, dtype, arg) != 0; }
 
-template <class KT, int DT, bool ARG>
-static int d1_launch_t(const ImgArgs &a, int C, const D1Cached *c, cudaStream_t s) {
+template <class KT, int DT, bool ARG, int NMAX>
+static int d1_launch_n(const ImgArgs &a, int C, const D1Cached *c, int nt, cudaStream_t s) {
     const size_t smem = (size_t)c->plan.smem_elems * sizeof(KT);
-    auto kern = d1_kernel<KT, DT, ARG>;
+    auto kern = d1_kernel<KT, DT, ARG, NMAX>;
     static bool configured = false;
     if (!configured) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM_BUDGET) !=
@@ -233,34 +263,45 @@ static int d1_launch_t(const ImgArgs &a, int C, const D1Cached *c, cudaStream_t 
             return MF_ERR_CUDA;
         configured = true;
     }
-    dim3 grid((a.W + c->plan.T - 1) / c->plan.T, (a.H + c->plan.T - 1) / c->plan.T, C);
-    kern<<<grid, D1_NT, smem, s>>>(a, c->dev);
+    const int SW = c->plan.B * c->plan.T;
+    dim3 grid((a.W + SW - 1) / SW, (a.H + c->plan.T - 1) / c->plan.T, C);
+    kern<<<grid, nt, smem, s>>>(a, c->dev);
     count_launch();
     return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;
+}
+
+template <class KT, int DT, bool ARG>
+static int d1_launch_t(const ImgArgs &a, int C, const D1Cached *c, int nt, cudaStream_t s) {
+    const int ms = c->plan.max_sort;
+    if (ms <= 8) return d1_launch_n<KT, DT, ARG, 8>(a, C, c, nt, s);
+    if (ms <= 16) return d1_launch_n<KT, DT, ARG, 16>(a, C, c, nt, s);
+    if (ms <= 32) return d1_launch_n<KT, DT, ARG, 32>(a, C, c, nt, s);
+    return d1_launch_n<KT, DT, ARG, 64>(a, C, c, nt, s);
 }
 
 int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s) {
     const bool arg = a.idx != nullptr;
     if (T == 0) T = d1_default_tile(k, dtype, arg);
-    if (!d1_supported_tile(k, dtype, arg, T)) {
+    int B, nt;
+    if (!choose_config(k, dtype, arg, T, &B, &nt)) {
         set_error("no data-aware plan for k=%d tile=%d", k, T);
         return MF_ERR_UNSUPPORTED;
     }
-    const D1Cached *c = get_plan(k, T);
+    const D1Cached *c = get_plan(k, T, B, nt);
     if (!c) {
         set_error("cannot upload the data-aware plan for k=%d tile=%d", k, T);
         return MF_ERR_CUDA;
     }
     int rc;
     switch (dtype * 2 + (arg ? 1 : 0)) {
-        case MF_U8 * 2: rc = d1_launch_t<uint16_t, MF_U8, false>(a, C, c, s); break;
-        case MF_U16 * 2: rc = d1_launch_t<uint16_t, MF_U16, false>(a, C, c, s); break;
-        case MF_U32 * 2: rc = d1_launch_t<uint32_t, MF_U32, false>(a, C, c, s); break;
-        case MF_F32 * 2: rc = d1_launch_t<uint32_t, MF_F32, false>(a, C, c, s); break;
-        case MF_U8 * 2 + 1: rc = d1_launch_t<uint32_t, MF_U8, true>(a, C, c, s); break;
-        case MF_U16 * 2 + 1: rc = d1_launch_t<uint32_t, MF_U16, true>(a, C, c, s); break;
-        case MF_U32 * 2 + 1: rc = d1_launch_t<unsigned long long, MF_U32, true>(a, C, c, s); break;
-        case MF_F32 * 2 + 1: rc = d1_launch_t<unsigned long long, MF_F32, true>(a, C, c, s); break;
+        case MF_U8 * 2: rc = d1_launch_t<uint16_t, MF_U8, false>(a, C, c, nt, s); break;
+        case MF_U16 * 2: rc = d1_launch_t<uint16_t, MF_U16, false>(a, C, c, nt, s); break;
+        case MF_U32 * 2: rc = d1_launch_t<uint32_t, MF_U32, false>(a, C, c, nt, s); break;
+        case MF_F32 * 2: rc = d1_launch_t<uint32_t, MF_F32, false>(a, C, c, nt, s); break;
+        case MF_U8 * 2 + 1: rc = d1_launch_t<uint32_t, MF_U8, true>(a, C, c, nt, s); break;
+        case MF_U16 * 2 + 1: rc = d1_launch_t<uint32_t, MF_U16, true>(a, C, c, nt, s); break;
+        case MF_U32 * 2 + 1: rc = d1_launch_t<unsigned long long, MF_U32, true>(a, C, c, nt, s); break;
+        case MF_F32 * 2 + 1: rc = d1_launch_t<unsigned long long, MF_F32, true>(a, C, c, nt, s); break;
         default: set_error("bad dtype"); return MF_ERR_DTYPE;
     }
     if (rc == MF_ERR_CUDA) set_error("data-aware kernel: %s", cudaGetErrorString(cudaGetLastError()));
@@ -268,14 +309,16 @@ int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s) 
 }
 
 int d1_describe(int k, int dtype, bool arg, int T, char *buf, size_t n) {
-    const D1Plan *p = T ? host_plan(k, T) : nullptr;
+    int B = 0, nt = 0;
+    const D1Plan *p = T && choose_config(k, dtype, arg, T, &B, &nt) ? host_plan(k, T, B, nt) : nullptr;
     if (!p) {
         snprintf(buf, n, "data-aware k=%d (no plan)", k);
         return MF_OK;
     }
-    snprintf(buf, n, "data-aware k=%d tile=%dx%d block=%d smem=%zuB phases=%d tasks=%zu merged/px=%.1f sorted/px=%.1f",
-             k, T, T, D1_NT, (size_t)p->smem_elems * key_bytes(dtype, arg), (int)p->phase_begin.size() - 1,
-             p->tasks.size(), (double)p->merge_outputs / (T * T), (double)p->sort_elems / (T * T));
+    const double px = (double)B * T * T;
+    snprintf(buf, n, "data-aware k=%d tile=%dx%d strip=%d block=%d smem=%zuB phases=%d tasks=%zu merged/px=%.1f sorted/px=%.1f",
+             k, T, T, B, nt, (size_t)p->smem_elems * key_bytes(dtype, arg), (int)p->phase_begin.size() - 1,
+             p->tasks.size(), p->merge_outputs / px, p->sort_elems / px);
     return MF_OK;
 }
 

@@ -32,6 +32,19 @@ def test_plan_matches_oracle(k, T):
     assert st["phases"] >= 3 and st["max_sort"] <= 64
 
 
+@pytest.mark.parametrize("k,T,B", [(3, 2, 8), (9, 4, 3), (17, 8, 4), (21, 8, 2), (31, 8, 2)])
+def test_strip_plan_matches_oracle(k, T, B):
+    """A strip of B root tiles sharing its column sorts (Sec. 3.3)."""
+    FH, FW = T + k - 1, B * T + k - 1
+    r = k // 2
+    img = synth.levels16((FH, FW), "u8", 11 * k + B)
+    st, med = mf.mf_d1_plan_check(k, T, img.astype(np.uint64).ravel(), strip=B)
+    want = oracle.median_filter(img, k)[r:r + T, r:r + B * T].ravel()
+    assert np.array_equal(med.astype(np.uint8), want)
+    single, _ = mf.mf_d1_plan_check(k, T)
+    assert st["sorted"] < B * single["sorted"]  # column sorts are shared
+
+
 def test_plan_argmedian_records():
     # 64-bit records key << 32 | footprint index: the winner's index is the
     # oracle's argmedian (lowest value, then lowest row-major window slot)
