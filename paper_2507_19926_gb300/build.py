@@ -39,6 +39,9 @@ O1_ARG64 = {k: v for k, v in O1_VALUE.items() if k <= 9}
 
 DT_NAMES = {0: "MF_U8", 1: "MF_U16", 2: "MF_U32", 3: "MF_F32"}
 
+# Barrier spacing (min/max ops) inside long per-thread networks.
+O1_SYNC_EVERY = int(os.environ.get("MF_O1_SYNC_EVERY", "0"))
+
 
 def _o1_instances():
     """(k, tw, th, bx, by, dtype, ko, arg, ib) for every O1 kernel built."""
@@ -73,7 +76,9 @@ def generate():
         nets = sorted({(i[1], i[2]) for i in lst})
         sorts = sorted({k - th + 1 for (_, th) in nets})
         for tw, th in nets:
-            parts.append(codegen.emit_network(netgen.build(k, tw, th), codegen.net_name(k, tw, th)))
+            net = netgen.build(k, tw, th)
+            sync = O1_SYNC_EVERY if O1_SYNC_EVERY and len(net.ops) > 4 * O1_SYNC_EVERY else 0
+            parts.append(codegen.emit_network(net, codegen.net_name(k, tw, th), sync))
         for n in sorts:
             parts.append(codegen.emit_colsort(n))
         for (k_, tw, th, bx, by, dt, ko, arg, ib) in lst:

@@ -24,7 +24,11 @@ def sort_name(n):
     return "ColSort_%d" % n
 
 
-def emit_network(net, name):
+def emit_network(net, name, sync_every=0):
+    """sync_every > 0 inserts a block barrier after every that many ops: all
+    threads of a block run this same branch-free code, so the barrier only
+    keeps the block's warps within one window of the (very long) program,
+    which the instruction cache can then hold."""
     lines = []
     w = lines.append
     w("struct %s {" % name)
@@ -47,9 +51,11 @@ def emit_network(net, name):
             loaded[v] = True
         return "v%d" % v
 
-    for kind, a, b, v in net.ops:
+    for n, (kind, a, b, v) in enumerate(net.ops):
         ra, rb = ref(a), ref(b)
         w("    const T v%d = KO::%s(%s, %s);" % (v, "mn" if kind == "min" else "mx", ra, rb))
+        if sync_every and n % sync_every == sync_every - 1:
+            w("    __syncthreads();")
     for i, v in enumerate(net.outputs):
         w("    o[%d] = %s;" % (i, ref(v)))
     w("  }")

@@ -27,6 +27,29 @@ __host__ __device__ __forceinline__ KT d1_sentinel() {
     return (KT)~(KT)0;
 }
 
+// 16-byte device form of a task (one 128-bit load):
+//   x = a_off | type << 17 | (a_stride == FW) << 18 | chunk << 19
+//   y = b_off | a_len << 17,  z = out_off | b_len << 17,  w = lo | hi << 13
+// Offsets < 2^17 list elements, lengths and ranks < 2^13, chunk < 64.
+struct D1Packed {
+    uint32_t x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ D1Task d1_unpack(const D1Packed &p, int FW) {
+    D1Task t;
+    t.a_off = (int)(p.x & 0x1ffffu);
+    t.type = (int)((p.x >> 17) & 1u);
+    t.a_stride = ((p.x >> 18) & 1u) ? FW : 1;
+    t.chunk = (int)(p.x >> 19);
+    t.b_off = (int)(p.y & 0x1ffffu);
+    t.a_len = (int)(p.y >> 17);
+    t.out_off = (int)(p.z & 0x1ffffu);
+    t.b_len = (int)(p.z >> 17);
+    t.lo = (int)(p.w & 0x1fffu);
+    t.hi = (int)(p.w >> 13);
+    return t;
+}
+
 // Outputs lo + chunk*t.chunk ... (up to t.chunk of them, not past hi) of
 // merge(A, B) into out[(p - lo)].
 template <class KT>
@@ -48,16 +71,19 @@ __host__ __device__ __forceinline__ void d1_merge_chunk(KT *sm, const D1Task &t,
     }
     int i = lo, j = p0 - lo;
     KT *out = sm + t.out_off + (p0 - t.lo);
-    const KT S = d1_sentinel<KT>();
-    KT a = i < na ? A[i] : S;
-    KT b = j < nb ? B[j] : S;
+    // branch-free: the index of an exhausted list is clamped to its last
+    // element and never chosen again (ta is forced by the length tests)
+    const int ia = na - 1, jb = nb - 1;
+    KT a = A[i < ia ? i : ia];
+    KT b = B[j < jb ? j : jb];
+#pragma unroll 4
     for (int n = 0; n < cnt; n++) {
-        const bool ta = (j >= nb) || (i < na && a <= b);
+        const bool ta = (j > jb) || (i <= ia && a <= b);
         out[n] = ta ? a : b;
-        i += ta ? 1 : 0;
-        j += ta ? 0 : 1;
-        a = i < na ? A[i] : S;
-        b = j < nb ? B[j] : S;
+        i += ta;
+        j += !ta;
+        a = A[i < ia ? i : ia];
+        b = B[j < jb ? j : jb];
     }
 }
 

@@ -370,8 +370,8 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt) {
         long long outs_p = 0;
         for (int ti : by_phase[p])
             if (B.tasks[ti].type == D1_MERGE) outs_p += B.tasks[ti].hi - B.tasks[ti].lo + 1;
-        // about two chunks per thread, each 4..32 outputs long
-        int chunk = (int)std::min<long long>(32, std::max<long long>(4, outs_p / (2 * nt)));
+        // about two chunks per thread, each 16..32 outputs long
+        int chunk = (int)std::min<long long>(32, std::max<long long>(16, outs_p / (2 * nt)));
         // sorts first, grouped by size class, then merges
         std::vector<int> order = by_phase[p];
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -411,16 +411,37 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt) {
     plan->phase_begin.push_back((int)plan->work.size());
     plan->out_off.resize(NB * T * T);
     for (int i = 0; i < NB * T * T; i++) plan->out_off[i] = resolve(outs[i]);
+    // limits of the packed device form
+    for (const D1Task &t : plan->tasks)
+        if (t.a_off >= (1 << 17) || t.b_off >= (1 << 17) || t.out_off >= (1 << 17) || t.a_len >= (1 << 13) ||
+            t.b_len >= (1 << 13) || t.lo >= (1 << 13) || t.hi >= (1 << 13) || t.chunk >= 64 ||
+            (t.type == D1_SORT && t.a_stride != 1 && t.a_stride != FW))
+            return false;
     return plan->tasks.size() < (1u << 20);
+}
+
+void d1_pack_tasks(const D1Plan &plan, std::vector<D1Packed> *out) {
+    out->resize(plan.tasks.size());
+    for (size_t i = 0; i < plan.tasks.size(); i++) {
+        const D1Task &t = plan.tasks[i];
+        D1Packed &p = (*out)[i];
+        p.x = (uint32_t)t.a_off | (uint32_t)t.type << 17 | (uint32_t)(t.type == D1_SORT && t.a_stride == plan.FW) << 18 |
+              (uint32_t)t.chunk << 19;
+        p.y = (uint32_t)t.b_off | (uint32_t)t.a_len << 17;
+        p.z = (uint32_t)t.out_off | (uint32_t)t.b_len << 17;
+        p.w = (uint32_t)t.lo | (uint32_t)t.hi << 13;
+    }
 }
 
 void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *medians) {
     std::vector<uint64_t> sm(plan.smem_elems, 0xdeadbeefdeadbeefull);
     std::copy(footprint, footprint + plan.FW * plan.FH, sm.begin());
     const int nph = (int)plan.phase_begin.size() - 1;
+    std::vector<D1Packed> packed;
+    d1_pack_tasks(plan, &packed);
     for (int p = 0; p < nph; p++) {
         for (int w = plan.phase_begin[p]; w < plan.phase_begin[p + 1]; w++) {
-            const D1Task &t = plan.tasks[plan.work[w] >> 12];
+            const D1Task t = d1_unpack(packed[plan.work[w] >> 12], plan.FW);
             const int chunk = plan.work[w] & 4095;
             if (t.type == D1_SORT) {
                 std::vector<uint64_t> v(t.a_len);

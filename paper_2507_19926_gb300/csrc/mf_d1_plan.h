@@ -35,7 +35,7 @@ struct D1Plan {
     int FH = 0;                      // footprint height T + k - 1
     int nt = 256;                    // threads per block the chunking targets
     int smem_elems = 0;              // shared-memory list elements needed (footprint included)
-    std::vector<D1Task> tasks;
+    std::vector<D1Task> tasks;       // host form; the device gets them packed (D1Packed)
     std::vector<uint32_t> work;      // task << 12 | chunk, grouped by phase
     std::vector<int32_t> phase_begin;  // phases + 1 entries into work
     std::vector<int32_t> out_off;    // T * B*T: offset of each pixel's median (row-major in the strip)
@@ -49,6 +49,10 @@ struct D1Plan {
 // blocks of nt threads.  The strip's footprint columns are sorted once and
 // shared by its tiles (paper Sec. 3.3).  Returns false outside that range.
 bool d1_build_plan(int k, int T, D1Plan *plan, int B = 1, int nt = 256);
+
+struct D1Packed;
+// The 16-byte device form of every task (layout in mf_d1_ops.cuh).
+void d1_pack_tasks(const D1Plan &plan, std::vector<D1Packed> *out);
 
 // Runs a plan on the host for one footprint of keys (FH*FW, row-major),
 // writing the T * B*T medians (row-major).  Used by tests to check the

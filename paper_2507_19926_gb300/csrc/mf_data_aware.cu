@@ -28,7 +28,7 @@ constexpr size_t D1_SMEM_BUDGET = 200 * 1024;
 constexpr size_t D1_SMEM_SMALL = 56 * 1024;
 
 struct D1Dev {
-    const D1Task *tasks;
+    const D1Packed *tasks;
     const uint32_t *work;
     const int32_t *phase_begin;
     const int32_t *out_off;
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(D1_NT_MAX) d1_kernel(ImgArgs a, D1Dev p) {
         const int wb = p.phase_begin[ph], we = p.phase_begin[ph + 1];
         for (int w = wb + tid; w < we; w += NT) {
             const uint32_t item = p.work[w];
-            const D1Task t = p.tasks[item >> 12];
+            const D1Task t = d1_unpack(p.tasks[item >> 12], FW);
             if (t.type == D1_SORT) d1_sort_any<KT, NMAX>(sm, t);
             else d1_merge_chunk<KT>(sm, t, (int)(item & 4095u));
         }
@@ -198,7 +198,9 @@ static D1Cached *get_plan(int k, int T, int B, int nt) {
     D1Cached *c = new D1Cached();
     c->plan = *hp;
     const D1Plan &pl = c->plan;
-    const size_t bt = pl.tasks.size() * sizeof(D1Task), bw = pl.work.size() * 4,
+    std::vector<D1Packed> packed;
+    d1_pack_tasks(pl, &packed);
+    const size_t bt = packed.size() * sizeof(D1Packed), bw = pl.work.size() * 4,
                  bp = pl.phase_begin.size() * 4, bo = pl.out_off.size() * 4;
     const size_t total = bt + bw + bp + bo + 64;
     if (cudaMalloc(&c->mem, total) != cudaSuccess) {
@@ -207,7 +209,7 @@ static D1Cached *get_plan(int k, int T, int B, int nt) {
         return nullptr;
     }
     char *m = (char *)c->mem;
-    if (cudaMemcpy(m, pl.tasks.data(), bt, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(m, packed.data(), bt, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(m + bt, pl.work.data(), bw, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(m + bt + bw, pl.phase_begin.data(), bp, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(m + bt + bw + bp, pl.out_off.data(), bo, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -216,7 +218,7 @@ static D1Cached *get_plan(int k, int T, int B, int nt) {
         delete c;
         return nullptr;
     }
-    c->dev.tasks = (const D1Task *)m;
+    c->dev.tasks = (const D1Packed *)m;
     c->dev.work = (const uint32_t *)(m + bt);
     c->dev.phase_begin = (const int32_t *)(m + bt + bw);
     c->dev.out_off = (const int32_t *)(m + bt + bw + bp);

@@ -283,7 +283,7 @@ def build(k, tw, th=None):
 
     recurse(0, 0, tw, th, core, d, cols, rows)
     net.outputs = [outputs[(y, x)] for y in range(th) for x in range(tw)]
-    return prune(net)
+    return schedule(prune(net), leaf_order(tw, th))
 
 
 def prune(net):
@@ -310,6 +310,58 @@ def prune(net):
     out.ops = new_ops
     out.outputs = [order[v] for v in net.outputs]
     out._memo = {d: order[net._memo[d]] for d in new_inputs}
+    return out
+
+
+def leaf_order(tw, th):
+    """Pixels (row-major index in the tile) in the order the recursion
+    reaches them (depth-first, first child first)."""
+    out = []
+
+    def rec(x0, y0, w, h):
+        if w == 1 and h == 1:
+            out.append(y0 * tw + x0)
+            return
+        if w >= h:
+            rec(x0, y0, w // 2, h)
+            rec(x0 + w // 2, y0, w // 2, h)
+        else:
+            rec(x0, y0, w, h // 2)
+            rec(x0, y0 + h // 2, w, h // 2)
+
+    rec(0, 0, tw, th)
+    return out
+
+
+def schedule(net, out_order):
+    """Reorders the ops of a pruned network into demand-driven post-order
+    (each output's dependencies just before it, outputs in out_order), which
+    keeps values live for shorter spans: fewer registers for the same ops."""
+    n_in = len(net.inputs)
+    op_of = {v: i for i, (kind, a, b, v) in enumerate(net.ops)}
+    done = set(range(n_in))
+    order = []
+    for o in out_order:
+        stack = [(net.outputs[o], False)]
+        while stack:
+            v, expanded = stack.pop()
+            if v in done:
+                continue
+            if expanded:
+                done.add(v)
+                order.append(net.ops[op_of[v]])
+                continue
+            stack.append((v, True))
+            _, a, b, _ = net.ops[op_of[v]]
+            for x in (b, a):
+                if x not in done:
+                    stack.append((x, False))
+    assert len(order) == len(net.ops)
+    out = Network(net.k, net.tw, net.th)
+    out.inputs = net.inputs
+    out.ops = order
+    out.outputs = net.outputs
+    out._memo = net._memo
     return out
 
 

@@ -16,7 +16,7 @@ def lib():
 
 
 CASES = [(3, 2), (5, 2), (5, 4), (7, 4), (9, 2), (9, 8), (11, 4), (13, 8), (17, 8), (17, 16),
-         (21, 8), (25, 16), (31, 16), (45, 16), (61, 16), (75, 16), (75, 8), (33, 32)]
+         (21, 8), (25, 16), (31, 16), (45, 16), (61, 16), (75, 16), (75, 8), (33, 16)]
 
 
 @pytest.mark.parametrize("k,T", CASES)
