@@ -125,15 +125,21 @@ typedef struct {
 
 typedef struct mf_batch_plan mf_batch_plan;
 
-/* Plans many images of uneven sizes, dtypes and k for one persistent launch
- * with a device-side work queue, ordered by predicted cost.  The plan owns
- * its device memory (work list and queue counter) until destroyed.  The
- * descriptors are copied; the image buffers they point to must stay valid
- * while the plan is run. */
+/* Plans many images of uneven sizes, dtypes and k (odd, 1..31) for one
+ * CUDA-graph launch.  Images are grouped by the kernel the plain entry point
+ * would run for them; each group gets one persistent kernel whose blocks
+ * claim (image, block, plane) work items from a device-side queue, largest
+ * images first; the groups run as concurrent branches of the graph.  The
+ * plan owns its device memory (image table, work lists, queue counters),
+ * streams and graph until destroyed.  The descriptors are copied; the image
+ * buffers they point to must stay valid while the plan is run.  Must be
+ * called outside any stream capture. */
 int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_plan **out);
 /* Runs a plan on `stream` (one CUDA graph launch: queue reset + kernel). */
 int mf_batch_run(mf_batch_plan *plan, mf_stream_t stream);
 int mf_batch_plan_destroy(mf_batch_plan *plan);
+/* Kernel launches per run (one per kernel class) and work items of a plan. */
+int mf_batch_describe(const mf_batch_plan *plan, int *kernels, long long *items);
 
 /* ---- tuning and introspection ------------------------------------------ */
 

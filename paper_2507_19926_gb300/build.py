@@ -83,15 +83,23 @@ def generate():
             parts.append(codegen.emit_colsort(n))
         for (k_, tw, th, bx, by, dt, ko, arg, ib) in lst:
             fn = "o1_launch_k%d_%dx%d_%s_%s%s" % (k, tw, th, DT_NAMES[dt], ko, "_arg" if arg else "")
-            parts.append(
-                "int %s(const ImgArgs &a, int c, cudaStream_t s) {\n"
-                "  return launch_o1<%d, %d, %d, %d, %d, %s, %s, %s, %d, %s, %s>(a, c, s);\n}"
-                % (fn, k, tw, th, bx, by, DT_NAMES[dt], ko, "true" if arg else "false", ib,
-                   codegen.net_name(k, tw, th), codegen.sort_name(k - th + 1)))
+            targs = "%d, %d, %d, %d, %d, %s, %s, %s, %d, %s, %s" % (
+                k, tw, th, bx, by, DT_NAMES[dt], ko, "true" if arg else "false", ib,
+                codegen.net_name(k, tw, th), codegen.sort_name(k - th + 1))
+            parts.append("int %s(const ImgArgs &a, int c, cudaStream_t s) {\n"
+                         "  return launch_o1<%s>(a, c, s);\n}" % (fn, targs))
+            pfn = "NULL"
+            if not arg:
+                pfn = fn.replace("o1_launch", "o1_persist")
+                parts.append("int %s(const ImgArgs *i, const int4 *w, int n, unsigned *q, int b, int sms, "
+                             "cudaStream_t s, int *g) {\n  return persist_o1<%s>(i, w, n, q, b, sms, s, g);\n}"
+                             % (pfn, targs))
+                decls.append("int %s(const ImgArgs *i, const int4 *w, int n, unsigned *q, int b, int sms, "
+                             "cudaStream_t s, int *g);" % pfn)
             decls.append("int %s(const ImgArgs &a, int c, cudaStream_t s);" % fn)
-            entries.append("  {%d, %s, %d, %d, %d, %d, %d, %d, %s, \"%s\"}," %
+            entries.append("  {%d, %s, %d, %d, %d, %d, %d, %d, %s, %s, \"%s\"}," %
                            (k, DT_NAMES[dt], 1 if arg else 0, tw, th, bx, by,
-                            netgen.build(k, tw, th).ops.__len__(), fn, fn))
+                            netgen.build(k, tw, th).ops.__len__(), fn, pfn, fn))
         parts.append("}  // namespace mf")
         path = os.path.join(GEN, "o1_k%d.cu" % k)
         codegen.write_if_changed(path, "\n".join(parts) + "\n")

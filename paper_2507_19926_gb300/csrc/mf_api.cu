@@ -125,6 +125,14 @@ static int resolve(int k, int dtype, bool arg, int variant, Plan *p) {
     return MF_ERR_ARG;
 }
 
+int resolve_variant(int k, int dtype, bool arg, int variant, const O1Entry **o1) {
+    Plan p;
+    int rc = resolve(k, dtype, arg, variant, &p);
+    if (rc) return rc;
+    if (o1) *o1 = p.o1;
+    return p.variant;
+}
+
 static int run_filter(const void *src, void *dst, int H, int W, size_t pitch, int C, int dtype, int k,
                       int variant, int32_t *idx, size_t idx_pitch, cudaStream_t s) {
     ImgArgs a;

@@ -74,15 +74,16 @@ struct D1Key {
     }
 };
 
+// One block's work: the strip at (bxi, byi) of plane z.
 template <class KT, int DT, bool ARG, int NMAX>
-__global__ void __launch_bounds__(D1_NT_MAX) d1_kernel(ImgArgs a, D1Dev p) {
+__device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int bxi, int byi, int z) {
     extern __shared__ __align__(16) unsigned char d1_smem[];
     KT *sm = reinterpret_cast<KT *>(d1_smem);
     typedef typename Dt<DT>::E E;
     const int tid = threadIdx.x, NT = blockDim.x;
     const int T = p.T, FW = p.FW, FH = p.FH, R = (p.k - 1) / 2, SW = p.B * p.T;
-    const int x0 = blockIdx.x * SW, y0 = blockIdx.y * T;
-    const char *src = a.src + (size_t)blockIdx.z * a.plane;
+    const int x0 = bxi * SW, y0 = byi * T;
+    const char *src = a.src + (size_t)z * a.plane;
 
     // footprint of the strip, clamped to the image
     for (int i = tid; i < FW * FH; i += NT) {
@@ -104,8 +105,8 @@ __global__ void __launch_bounds__(D1_NT_MAX) d1_kernel(ImgArgs a, D1Dev p) {
         __syncthreads();
     }
 
-    char *dst = a.dst ? a.dst + (size_t)blockIdx.z * a.plane : nullptr;
-    char *idx = a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)blockIdx.z * a.idx_plane : nullptr;
+    char *dst = a.dst ? a.dst + (size_t)z * a.plane : nullptr;
+    char *idx = a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)z * a.idx_plane : nullptr;
     for (int i = tid; i < T * SW; i += NT) {
         const int py = i / SW, px = i - py * SW;
         const int y = y0 + py, x = x0 + px;
@@ -122,6 +123,28 @@ __global__ void __launch_bounds__(D1_NT_MAX) d1_kernel(ImgArgs a, D1Dev p) {
             if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
             if (idx) reinterpret_cast<int32_t *>(idx + (size_t)y * a.idx_pitch)[x] = ys * a.W + xs;
         }
+    }
+}
+
+template <class KT, int DT, bool ARG, int NMAX>
+__global__ void __launch_bounds__(D1_NT_MAX) d1_kernel(ImgArgs a, D1Dev p) {
+    d1_block<KT, DT, ARG, NMAX>(a, p, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Persistent form for batches (see o1_persistent): blocks claim work items
+// (image, strip x, strip y, plane) from a device counter.
+template <class KT, int DT, bool ARG, int NMAX>
+__global__ void __launch_bounds__(D1_NT_MAX) d1_persistent(const ImgArgs *imgs, const int4 *items, int n_items,
+                                                         unsigned *counter, D1Dev p) {
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int4 w = items[it];
+        d1_block<KT, DT, ARG, NMAX>(imgs[w.x], p, w.y, w.z, w.w);
+        __syncthreads();
     }
 }
 
@@ -308,6 +331,65 @@ int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s) 
     }
     if (rc == MF_ERR_CUDA) set_error("data-aware kernel: %s", cudaGetErrorString(cudaGetLastError()));
     return rc;
+}
+
+template <class KT, int DT, int NMAX>
+static int d1_persist_n(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter,
+                        const D1Cached *c, int nt, int sms, cudaStream_t s, int *grid_out) {
+    const size_t smem = (size_t)c->plan.smem_elems * sizeof(KT);
+    auto kern = d1_persistent<KT, DT, false, NMAX>;
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM_BUDGET) !=
+            cudaSuccess)
+            return MF_ERR_CUDA;
+        configured = true;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, smem) != cudaSuccess) return MF_ERR_CUDA;
+    if (occ < 1) occ = 1;
+    int grid = occ * sms;
+    if (grid > n_items) grid = n_items;
+    if (grid < 1) grid = 1;
+    *grid_out = grid;
+    kern<<<grid, nt, smem, s>>>(imgs, items, n_items, counter, c->dev);
+    count_launch();
+    return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;
+}
+
+template <class KT, int DT>
+static int d1_persist_t(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter,
+                        const D1Cached *c, int nt, int sms, cudaStream_t s, int *grid_out) {
+    const int ms = c->plan.max_sort;
+    if (ms <= 8) return d1_persist_n<KT, DT, 8>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
+    if (ms <= 16) return d1_persist_n<KT, DT, 16>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
+    if (ms <= 32) return d1_persist_n<KT, DT, 32>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
+    return d1_persist_n<KT, DT, 64>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
+}
+
+int d1_geometry(int k, int dtype, bool arg, int *tile, int *strip, int *threads) {
+    const int T = d1_default_tile(k, dtype, arg);
+    int B, nt;
+    if (!T || !choose_config(k, dtype, arg, T, &B, &nt)) return MF_ERR_UNSUPPORTED;
+    *tile = T;
+    *strip = B;
+    *threads = nt;
+    return MF_OK;
+}
+
+int d1_persist(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter, int k, int dtype,
+               int sms, cudaStream_t s, int *grid_out) {
+    int T, B, nt;
+    if (d1_geometry(k, dtype, false, &T, &B, &nt)) return MF_ERR_UNSUPPORTED;
+    const D1Cached *c = get_plan(k, T, B, nt);
+    if (!c) return MF_ERR_CUDA;
+    switch (dtype) {
+        case MF_U8: return d1_persist_t<uint16_t, MF_U8>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
+        case MF_U16: return d1_persist_t<uint16_t, MF_U16>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
+        case MF_U32: return d1_persist_t<uint32_t, MF_U32>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
+        case MF_F32: return d1_persist_t<uint32_t, MF_F32>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
+        default: return MF_ERR_DTYPE;
+    }
 }
 
 int d1_describe(int k, int dtype, bool arg, int T, char *buf, size_t n) {

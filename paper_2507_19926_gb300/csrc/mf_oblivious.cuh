@@ -106,9 +106,10 @@ struct O1Words<DT, KoU64, true, IB> {  // 32-bit argmedian: key << 32 | index
     }
 };
 
+// One block's work: the block of tiles at (bxi, byi) of plane z.
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
           class CSORT>
-__global__ void __launch_bounds__(BX *BY) o1_kernel(ImgArgs a) {
+__device__ __forceinline__ void o1_block(const ImgArgs &a, int bxi, int byi, int z) {
     typedef O1Layout<K, TW, TH, BX, BY> L;
     typedef typename KO::T T;
     typedef typename Dt<DT>::E E;
@@ -119,9 +120,9 @@ __global__ void __launch_bounds__(BX *BY) o1_kernel(ImgArgs a) {
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
-    const int bx0 = blockIdx.x * (P * BX * TW);
-    const int by0 = blockIdx.y * (BY * TH);
-    const char *src = a.src + (size_t)blockIdx.z * a.plane;
+    const int bx0 = bxi * (P * BX * TW);
+    const int by0 = byi * (BY * TH);
+    const char *src = a.src + (size_t)z * a.plane;
 
     // 1. block footprint -> shared memory (clamp to edge)
     for (int i = tid; i < L::FH * L::FW; i += NT) {
@@ -151,8 +152,8 @@ __global__ void __launch_bounds__(BX *BY) o1_kernel(ImgArgs a) {
     NET::template run<KO, L>(sm + L::CSB + ty * L::CSTY + tx, sm + ty * TH * L::RS + tx, o);
 
     // 4. results
-    char *dst = a.dst ? a.dst + (size_t)blockIdx.z * a.plane : nullptr;
-    char *idx = a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)blockIdx.z * a.idx_plane : nullptr;
+    char *dst = a.dst ? a.dst + (size_t)z * a.plane : nullptr;
+    char *idx = a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)z * a.idx_plane : nullptr;
 #pragma unroll
     for (int py = 0; py < TH; py++) {
         const int y = by0 + ty * TH + py;
@@ -179,6 +180,58 @@ __global__ void __launch_bounds__(BX *BY) o1_kernel(ImgArgs a) {
             }
         }
     }
+}
+
+template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
+          class CSORT>
+__global__ void __launch_bounds__(BX *BY) o1_kernel(ImgArgs a) {
+    o1_block<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Persistent form for batches: each block repeatedly claims the next work
+// item (image, block x, block y, plane) from a device counter until the
+// list is exhausted.  Claims are atomic increments -- no block ever waits
+// on another.
+template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
+          class CSORT>
+__global__ void __launch_bounds__(BX *BY) o1_persistent(const ImgArgs *imgs, const int4 *items, int n_items,
+                                                        unsigned *counter) {
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int4 w = items[it];
+        o1_block<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT>(imgs[w.x], w.y, w.z, w.w);
+        __syncthreads();  // shared memory is reused by the next item
+    }
+}
+
+template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
+          class CSORT>
+int persist_o1(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter, int blocks_per_sm,
+               int sms, cudaStream_t s, int *grid_out) {
+    typedef O1Layout<K, TW, TH, BX, BY> L;
+    constexpr size_t smem = sizeof(typename KO::T) * (size_t)L::WORDS;
+    auto kern = o1_persistent<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT>;
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return MF_ERR_CUDA;
+        configured = true;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BX * BY, smem) != cudaSuccess) return MF_ERR_CUDA;
+    if (occ < 1) occ = 1;
+    if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
+    int grid = occ * sms;
+    if (grid > n_items) grid = n_items;
+    if (grid < 1) grid = 1;
+    *grid_out = grid;
+    kern<<<grid, BX * BY, smem, s>>>(imgs, items, n_items, counter);
+    count_launch();
+    return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;
 }
 
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,

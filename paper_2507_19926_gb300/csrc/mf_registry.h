@@ -5,6 +5,9 @@
 namespace mf {
 
 typedef int (*ImgLaunchFn)(const ImgArgs &a, int channels, cudaStream_t s);
+// Persistent launch over a device work list (see o1_persistent).
+typedef int (*PersistFn)(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter,
+                         int blocks_per_sm, int sms, cudaStream_t s, int *grid_out);
 
 // One data-oblivious kernel instantiation (generated list).
 struct O1Entry {
@@ -15,6 +18,7 @@ struct O1Entry {
     int bx, by;     // threads per block (x, y)
     int net_ops;    // min/max ops of one root tile's network (excl. column sort)
     ImgLaunchFn launch;
+    PersistFn persist;
     const char *name;
 };
 
@@ -30,6 +34,11 @@ int d1_default_tile(int k, int dtype, bool arg);
 int d1_supported_tile(int k, int dtype, bool arg, int tile);
 int d1_describe(int k, int dtype, bool arg, int tile, char *buf, size_t n);
 void d1_release_all();
+// Persistent data-aware launch over a device work list for (k, dtype); the
+// block geometry is the plan d1_geometry reports.
+int d1_geometry(int k, int dtype, bool arg, int *tile, int *strip, int *threads);
+int d1_persist(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter, int k, int dtype,
+               int sms, cudaStream_t s, int *grid_out);
 
 // Identity argmedian for k = 1 and small helpers (mf_api.cu).
 int launch_identity_idx(const ImgArgs &a, int channels, cudaStream_t s);
@@ -41,5 +50,9 @@ int bwd_gather(const float *g, const int32_t *idx, float *gi, int H, int W, size
                size_t idx_pitch, int C, int k, cudaStream_t s);
 
 void set_error(const char *fmt, ...);
+
+// Variant the plain entry point would run for (k, dtype): MF_OBLIVIOUS (and
+// its entry) or MF_DATA_AWARE; negative status if neither exists.
+int resolve_variant(int k, int dtype, bool arg, int variant, const O1Entry **o1);
 
 }  // namespace mf

@@ -64,3 +64,15 @@ def test_describe_dispatch(lib):
     d = mf.mf_describe(480, 640, 1, mf.MF_U8, 5)
     assert "oblivious" in d and "k=5" in d
     assert mf.mf_describe(10, 10, 1, mf.MF_F32, 1) == "identity copy"
+
+
+def test_batch_rejects_bad_descriptors(lib):
+    d = mf.ImageDesc(0x1000, 0x900000, 8, 8, 8, 1, mf.MF_U8, 33)  # k > 31
+    with pytest.raises(mf.MedianFilterError):
+        mf.mf_batch_plan_create([d])
+    d = mf.ImageDesc(0x1000, 0x1000, 8, 8, 8, 1, mf.MF_U8, 3)  # aliasing
+    with pytest.raises(mf.MedianFilterError):
+        mf.mf_batch_plan_create([d])
+    d = mf.ImageDesc(0x1000, 0x900000, 8, 8, 4, 1, mf.MF_U8, 3)  # pitch < W
+    with pytest.raises(mf.MedianFilterError):
+        mf.mf_batch_plan_create([d])
