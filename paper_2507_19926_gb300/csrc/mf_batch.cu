@@ -42,6 +42,7 @@ struct BatchClass {
     const O1Entry *o1;
     int k, dtype;
     int rw, rh;  // pixels covered by one work item (block region)
+    int bps;     // resident blocks per SM of its persistent kernel
     std::vector<int4> items;
 };
 
@@ -170,6 +171,22 @@ extern "C" int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_
     }
     p->items = (long long)nitems;
 
+    // prepare every class outside the capture: plan uploads, kernel
+    // attributes and occupancy are not stream work
+    for (auto &kv : classes) {
+        BatchClass &c = kv.second;
+        int bps = 0, rc0;
+        if (c.variant == MF_OBLIVIOUS) rc0 = c.o1->persist(nullptr, nullptr, 0, nullptr, 0, sms, nullptr, &bps);
+        else rc0 = d1_persist(nullptr, nullptr, 0, nullptr, c.k, c.dtype, 0, sms, nullptr, &bps);
+        if (rc0 != MF_OK) {
+            set_error("preparing the persistent kernel for k=%d dtype=%d: %s", c.k, c.dtype,
+                      cudaGetErrorString(cudaGetLastError()));
+            destroy_plan(p);
+            return rc0;
+        }
+        c.bps = bps;
+    }
+
     // capture: one branch per class (counter reset + persistent kernel),
     // plus device-to-device copies for k = 1 images
     cudaStream_t s0;
@@ -198,9 +215,12 @@ extern "C" int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_
         int grid = 0;
         if (rc == MF_OK) {
             if (c.variant == MF_OBLIVIOUS)
-                rc = c.o1->persist((const ImgArgs *)dm, items, (int)c.items.size(), cnt, 0, sms, si, &grid);
+                rc = c.o1->persist((const ImgArgs *)dm, items, (int)c.items.size(), cnt, c.bps, sms, si, &grid);
             else
-                rc = d1_persist((const ImgArgs *)dm, items, (int)c.items.size(), cnt, c.k, c.dtype, sms, si, &grid);
+                rc = d1_persist((const ImgArgs *)dm, items, (int)c.items.size(), cnt, c.k, c.dtype, c.bps, sms, si,
+                                &grid);
+            if (rc != MF_OK)
+                set_error("persistent launch for k=%d dtype=%d: %s", c.k, c.dtype, cudaGetErrorString(cudaGetLastError()));
         }
         p->kernels++;
         cudaEventRecord(join, si);

@@ -335,7 +335,7 @@ int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s) 
 
 template <class KT, int DT, int NMAX>
 static int d1_persist_n(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter,
-                        const D1Cached *c, int nt, int sms, cudaStream_t s, int *grid_out) {
+                        const D1Cached *c, int nt, int blocks_per_sm, int sms, cudaStream_t s, int *grid_out) {
     const size_t smem = (size_t)c->plan.smem_elems * sizeof(KT);
     auto kern = d1_persistent<KT, DT, false, NMAX>;
     static bool configured = false;
@@ -345,26 +345,29 @@ static int d1_persist_n(const ImgArgs *imgs, const int4 *items, int n_items, uns
             return MF_ERR_CUDA;
         configured = true;
     }
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, smem) != cudaSuccess) return MF_ERR_CUDA;
-    if (occ < 1) occ = 1;
+    if (n_items == 0) {  // prepare only (see persist_o1)
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, smem) != cudaSuccess) return MF_ERR_CUDA;
+        *grid_out = occ < 1 ? 1 : occ;
+        return MF_OK;
+    }
+    const int occ = blocks_per_sm > 0 ? blocks_per_sm : 1;
     int grid = occ * sms;
     if (grid > n_items) grid = n_items;
     if (grid < 1) grid = 1;
     *grid_out = grid;
     kern<<<grid, nt, smem, s>>>(imgs, items, n_items, counter, c->dev);
-    count_launch();
     return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;
 }
 
 template <class KT, int DT>
 static int d1_persist_t(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter,
-                        const D1Cached *c, int nt, int sms, cudaStream_t s, int *grid_out) {
+                        const D1Cached *c, int nt, int bps, int sms, cudaStream_t s, int *grid_out) {
     const int ms = c->plan.max_sort;
-    if (ms <= 8) return d1_persist_n<KT, DT, 8>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
-    if (ms <= 16) return d1_persist_n<KT, DT, 16>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
-    if (ms <= 32) return d1_persist_n<KT, DT, 32>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
-    return d1_persist_n<KT, DT, 64>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
+    if (ms <= 8) return d1_persist_n<KT, DT, 8>(imgs, items, n_items, counter, c, nt, bps, sms, s, grid_out);
+    if (ms <= 16) return d1_persist_n<KT, DT, 16>(imgs, items, n_items, counter, c, nt, bps, sms, s, grid_out);
+    if (ms <= 32) return d1_persist_n<KT, DT, 32>(imgs, items, n_items, counter, c, nt, bps, sms, s, grid_out);
+    return d1_persist_n<KT, DT, 64>(imgs, items, n_items, counter, c, nt, bps, sms, s, grid_out);
 }
 
 int d1_geometry(int k, int dtype, bool arg, int *tile, int *strip, int *threads) {
@@ -378,16 +381,19 @@ int d1_geometry(int k, int dtype, bool arg, int *tile, int *strip, int *threads)
 }
 
 int d1_persist(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter, int k, int dtype,
-               int sms, cudaStream_t s, int *grid_out) {
+               int blocks_per_sm, int sms, cudaStream_t s, int *grid_out) {
     int T, B, nt;
     if (d1_geometry(k, dtype, false, &T, &B, &nt)) return MF_ERR_UNSUPPORTED;
+    // the plan upload (synchronous copies) happens in the prepare call,
+    // before any stream capture
     const D1Cached *c = get_plan(k, T, B, nt);
     if (!c) return MF_ERR_CUDA;
+    const int b = blocks_per_sm;
     switch (dtype) {
-        case MF_U8: return d1_persist_t<uint16_t, MF_U8>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
-        case MF_U16: return d1_persist_t<uint16_t, MF_U16>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
-        case MF_U32: return d1_persist_t<uint32_t, MF_U32>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
-        case MF_F32: return d1_persist_t<uint32_t, MF_F32>(imgs, items, n_items, counter, c, nt, sms, s, grid_out);
+        case MF_U8: return d1_persist_t<uint16_t, MF_U8>(imgs, items, n_items, counter, c, nt, b, sms, s, grid_out);
+        case MF_U16: return d1_persist_t<uint16_t, MF_U16>(imgs, items, n_items, counter, c, nt, b, sms, s, grid_out);
+        case MF_U32: return d1_persist_t<uint32_t, MF_U32>(imgs, items, n_items, counter, c, nt, b, sms, s, grid_out);
+        case MF_F32: return d1_persist_t<uint32_t, MF_F32>(imgs, items, n_items, counter, c, nt, b, sms, s, grid_out);
         default: return MF_ERR_DTYPE;
     }
 }

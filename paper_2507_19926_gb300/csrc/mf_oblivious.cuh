@@ -221,16 +221,21 @@ int persist_o1(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *co
             return MF_ERR_CUDA;
         configured = true;
     }
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BX * BY, smem) != cudaSuccess) return MF_ERR_CUDA;
-    if (occ < 1) occ = 1;
-    if (blocks_per_sm > 0 && blocks_per_sm < occ) occ = blocks_per_sm;
+    // n_items == 0: prepare only (attributes, occupancy -> *grid_out as
+    // blocks per SM); call this outside stream capture
+    if (n_items == 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BX * BY, smem) != cudaSuccess)
+            return MF_ERR_CUDA;
+        *grid_out = occ < 1 ? 1 : occ;
+        return MF_OK;
+    }
+    const int occ = blocks_per_sm > 0 ? blocks_per_sm : 1;
     int grid = occ * sms;
     if (grid > n_items) grid = n_items;
     if (grid < 1) grid = 1;
     *grid_out = grid;
     kern<<<grid, BX * BY, smem, s>>>(imgs, items, n_items, counter);
-    count_launch();
     return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;
 }
 

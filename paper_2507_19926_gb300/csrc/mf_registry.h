@@ -37,8 +37,10 @@ void d1_release_all();
 // Persistent data-aware launch over a device work list for (k, dtype); the
 // block geometry is the plan d1_geometry reports.
 int d1_geometry(int k, int dtype, bool arg, int *tile, int *strip, int *threads);
+// n_items == 0 prepares (plan upload, attributes) and returns the blocks
+// per SM in *grid_out; call that outside stream capture.
 int d1_persist(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter, int k, int dtype,
-               int sms, cudaStream_t s, int *grid_out);
+               int blocks_per_sm, int sms, cudaStream_t s, int *grid_out);
 
 // Identity argmedian for k = 1 and small helpers (mf_api.cu).
 int launch_identity_idx(const ImgArgs &a, int channels, cudaStream_t s);
