@@ -141,6 +141,30 @@ int mf_batch_plan_destroy(mf_batch_plan *plan);
 /* Kernel launches per run (one per kernel class) and work items of a plan. */
 int mf_batch_describe(const mf_batch_plan *plan, int *kernels, long long *items);
 
+/* Batched filter that allocates nothing (the paper has no counterpart: this
+ * serves callers that must not allocate device memory when they filter --
+ * e.g. code running while another framework's caching allocator owns the
+ * device, loops that must never wait inside an allocator, or deployments
+ * with a device memory budget fixed in advance).  Filters each image of
+ * descs (device buffers, as for mf_batch_plan_create) with the persistent
+ * data-oblivious kernels, taking its work queues from one fixed array of
+ * 2 MiB that the library's module holds on every device where it is used,
+ * until the library is unloaded.  Limits: at most 256 images, k = 1 or an
+ * odd k from 3 to 17, and at most 126,976 work items (one item is one
+ * block of pixels: 128 x 8 for k = 3, 5 and 8/16-bit data, 64 x 8 for 32-bit
+ * data, 256 x 16 / 128 x 16 for larger k); beyond them it returns MF_ERR_ARG
+ * or MF_ERR_UNSUPPORTED with a message, before touching the device.
+ * Nothing is allocated (no cudaMalloc, cudaFree or allocating library
+ * call): the image table and work records are copied from the stack, the
+ * queue counters are cleared on every call.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents, so calls whose
+ * work overlaps on the GPU (different streams, or devices sharing the
+ * module) race; calls issued in order on one stream are safe.  Work is
+ * enqueued on `stream`; the call returns without waiting for it. */
+int mf_batch_run_static(const mf_image_desc *descs, int n, mf_stream_t stream);
+
 /* ---- tuning and introspection ------------------------------------------ */
 
 /* Times the instantiated candidates for one (k, dtype, H, W) on the current

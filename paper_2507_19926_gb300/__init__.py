@@ -27,7 +27,7 @@ GRAD_MODES = {"atomic": MF_GRAD_ATOMIC, "deterministic": MF_GRAD_DETERMINISTIC}
 # C symbols declared in include/medianfilter.h
 EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_tile", "mf_median_filter_bwd",
            "mf_median_filter_host", "mf_batch_plan_create", "mf_batch_run",
-           "mf_batch_plan_destroy", "mf_batch_describe", "mf_autotune", "mf_describe", "mf_kernel_launch_count",
+           "mf_batch_plan_destroy", "mf_batch_describe", "mf_batch_run_static", "mf_autotune", "mf_describe", "mf_kernel_launch_count",
            "mf_status_string", "mf_last_error", "mf_version", "mf_shutdown", "mf_probe_minmax",
            "mf_d1_plan_check"]
 
@@ -66,6 +66,7 @@ def load_library(path=LIB_PATH):
         lib.mf_batch_plan_create.argtypes = [ctypes.POINTER(ImageDesc), i, ctypes.POINTER(vp)]
         lib.mf_batch_run.argtypes = [vp, vp]
         lib.mf_batch_plan_destroy.argtypes = [vp]
+        lib.mf_batch_run_static.argtypes = [ctypes.POINTER(ImageDesc), i, vp]
         lib.mf_batch_describe.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]
         lib.mf_autotune.argtypes = [vp, vp, i, i, sz, i, i, i, vp]
         lib.mf_describe.argtypes = [i, i, i, i, i, i, ctypes.c_char_p, sz]
@@ -133,6 +134,13 @@ def mf_batch_run(plan, stream=None):
 
 def mf_batch_plan_destroy(plan):
     return _check(load_library().mf_batch_plan_destroy(plan))
+
+
+def mf_batch_run_static(descs, stream=None):
+    """Filters a batch without allocating: work queues live in the library's
+    fixed device array (see include/medianfilter.h for the limits)."""
+    arr = (ImageDesc * len(descs))(*descs)
+    return _check(load_library().mf_batch_run_static(arr, len(descs), stream))
 
 
 def mf_batch_describe(plan):

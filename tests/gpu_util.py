@@ -40,7 +40,8 @@ def to_host(t, dtype):
         return t.view(torch.int16).cpu().numpy().view(np.uint16)
     if t.dtype == torch.uint32:
         return t.view(torch.int32).cpu().numpy().view(np.uint32)
-    return t.cpu().numpy().astype(dtype, copy=False)
+    out = t.cpu().numpy()
+    return out if dtype is None else out.astype(dtype, copy=False)
 
 
 def gpu_filter(a, k, variant="auto", return_idx=False):
