@@ -207,6 +207,119 @@ def run_reference(args):
     }))
 
 
+def _time_ms(fn, stream, reps, flush=None):
+    """Median of per-call CUDA-event times on `stream` (L2 flushed before each)."""
+    import torch
+    ts = []
+    for i in range(reps):
+        if flush is not None:
+            flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def bench_batched(dev, stream, flush, reps=5):
+    """64 images of uneven sizes/dtypes/k: one graph launch vs 64 plain calls."""
+    import torch
+    import paper_2507_19926_gb300 as mf
+    from paper_2507_19926_gb300 import synth
+    codes = {"u8": mf.MF_U8, "u16": mf.MF_U16, "f32": mf.MF_F32}
+    descs, bufs, px = [], [], 0
+    for d in synth.batch_descs():
+        x = to_device(synth.uniform((1, d["H"], d["W"]), d["dtype"], d["seed"]), dev)
+        y = torch.empty_like(x)
+        bufs.append((x, y, d))
+        descs.append(mf.ImageDesc(x.data_ptr(), y.data_ptr(), d["H"], d["W"], d["W"] * x.element_size(), 1,
+                                  codes[d["dtype"]], d["k"]))
+        px += d["H"] * d["W"]
+    plan = mf.mf_batch_plan_create(descs)
+    sptr = stream.cuda_stream
+    try:
+        kernels, items = mf.mf_batch_describe(plan)
+        run = lambda: mf.mf_batch_run(plan, sptr)
+        for _ in range(2):
+            run()
+        t_batch = _time_ms(run, stream, reps, flush)
+
+        def plain():
+            for x, y, d in bufs:
+                mf.mf_median_filter(x.data_ptr(), y.data_ptr(), d["H"], d["W"], d["W"] * x.element_size(), 1,
+                                    codes[d["dtype"]], d["k"], mf.MF_BORDER_CLAMP, sptr)
+        plain()
+        t_plain = _time_ms(plain, stream, reps, flush)
+    finally:
+        mf.mf_batch_plan_destroy(plan)
+    return {"workload": "64 images, log-uniform 256x256..4096x3072, u8/u16/f32, odd k 3..31",
+            "pixels": px, "graph_kernels": kernels, "work_items": items,
+            "batched_ms": t_batch, "plain_ms": t_plain, "batched_mpix_s": px / t_batch / 1e3,
+            "plain_mpix_s": px / t_plain / 1e3, "speedup": t_plain / t_batch}
+
+
+def bench_fwd_bwd(dev, stream, flush, reps=5):
+    """f32 16x1x1024x1024, k = 9 and 25: forward, forward + argmedian, and
+    forward + argmedian + backward (atomic and deterministic)."""
+    import torch
+    import paper_2507_19926_gb300 as mf
+    from paper_2507_19926_gb300 import synth
+    N, H, W = 16, 1024, 1024
+    x = torch.from_numpy(synth.normal_f32((N, 1, H, W), synth.SEED_BASE + 4)).to(dev)
+    g = torch.from_numpy(synth.normal_f32((N, 1, H, W), synth.SEED_BASE + 5)).to(dev)
+    y = torch.empty_like(x)
+    idx = torch.empty(x.shape, dtype=torch.int32, device=dev)
+    gi = torch.empty_like(x)
+    sptr = stream.cuda_stream
+    out = {}
+    for k in (9, 25):
+        fwd = lambda: mf.mf_median_filter_ex(x.data_ptr(), y.data_ptr(), H, W, 4 * W, N, mf.MF_F32, k,
+                                             mf.MF_BORDER_CLAMP, mf.MF_AUTO, None, 0, sptr)
+        fwd_idx = lambda: mf.mf_median_filter_ex(x.data_ptr(), y.data_ptr(), H, W, 4 * W, N, mf.MF_F32, k,
+                                                 mf.MF_BORDER_CLAMP, mf.MF_AUTO, idx.data_ptr(), 4 * W, sptr)
+        bwd_a = lambda: mf.mf_median_filter_bwd(g.data_ptr(), idx.data_ptr(), gi.data_ptr(), H, W, 4 * W, 4 * W, N, k,
+                                                mf.MF_GRAD_ATOMIC, sptr)
+        bwd_d = lambda: mf.mf_median_filter_bwd(g.data_ptr(), idx.data_ptr(), gi.data_ptr(), H, W, 4 * W, 4 * W, N, k,
+                                                mf.MF_GRAD_DETERMINISTIC, sptr)
+        for f in (fwd, fwd_idx, bwd_a, bwd_d):
+            f()
+        t_f = _time_ms(fwd, stream, reps, flush)
+        t_fi = _time_ms(fwd_idx, stream, reps, flush)
+        t_a = _time_ms(bwd_a, stream, reps, flush)
+        t_d = _time_ms(bwd_d, stream, reps, flush)
+        px = N * H * W
+        out["k%d" % k] = {"fwd_ms": t_f, "fwd_argmedian_ms": t_fi, "bwd_atomic_ms": t_a,
+                          "bwd_deterministic_ms": t_d, "fwd_mpix_s": px / t_f / 1e3,
+                          "fwd_bwd_atomic_mpix_s": px / (t_fi + t_a) / 1e3,
+                          "fwd_bwd_deterministic_mpix_s": px / (t_fi + t_d) / 1e3,
+                          "fwd_plan": mf.mf_describe(H, W, N, mf.MF_F32, k)}
+    return out
+
+
+def bench_sweep(dev, stream, flush, reps=3, ks=(3, 5, 9, 15, 21, 31, 45, 75), dts=("u8", "u16", "u32", "f32")):
+    """4096 x 4096 single-plane images, uniform values, auto variant."""
+    import torch
+    import paper_2507_19926_gb300 as mf
+    from paper_2507_19926_gb300 import synth
+    codes = {"u8": mf.MF_U8, "u16": mf.MF_U16, "u32": mf.MF_U32, "f32": mf.MF_F32}
+    res = []
+    sptr = stream.cuda_stream
+    for dt in dts:
+        x = to_device(synth.uniform((1, 4096, 4096), dt, synth.SEED_BASE + 2), dev)
+        y = torch.empty_like(x)
+        pitch = 4096 * x.element_size()
+        for k in ks:
+            f = lambda: mf.mf_median_filter(x.data_ptr(), y.data_ptr(), 4096, 4096, pitch, 1, codes[dt], k,
+                                            mf.MF_BORDER_CLAMP, sptr)
+            f()
+            ms = _time_ms(f, stream, reps, flush)
+            res.append({"dtype": dt, "k": k, "ms": round(ms, 4), "mpix_s": round(4096 * 4096 / ms / 1e3, 1),
+                        "plan": mf.mf_describe(4096, 4096, 1, codes[dt], k).split(" kernel=")[0]})
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -320,6 +433,10 @@ def run_ours(args):
         v, npx, secs = cpu_sample(x_np, k, args.cpu_seconds)
         cpu = {"value": v, "unit": "Mpix/s", "cores": oracle.max_threads(), "kind": "oracle",
                "sample": "%d output channel-pixels on random full rows of the same image (%.1f s)" % (npx, secs)}
+    if ws == 1 and not args.no_extras:
+        extra["batched_vs_plain"] = bench_batched(dev, stream, flush)
+        extra["fwd_bwd_vs_fwd"] = bench_fwd_bwd(dev, stream, flush)
+        extra["sweep_4096"] = bench_sweep(dev, stream, flush)
     out = {
         "metric": "median filter throughput (output channel-pixels per second)",
         "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -352,6 +469,7 @@ def main():
     ap.add_argument("--variant", default="auto", choices=["auto", "oblivious", "data_aware"])
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched, fwd+bwd and sweep extras")
     ap.add_argument("--ref-rows", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
