@@ -207,6 +207,19 @@ def run_reference(args):
     }))
 
 
+def aggregate(total_ms, px_per_step, steps, world_size, device=None):
+    """Whole-job throughput over replicas: every rank filtered px_per_step
+    pixels per step; the job took as long as the slowest rank.  Returns
+    (Mpix/s, slowest rank's ms)."""
+    if world_size > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world_size * px_per_step * steps / (total_ms * 1e-3) / 1e6, total_ms
+
+
 def _time_ms(fn, stream, reps, flush=None):
     """Median of per-call CUDA-event times on `stream` (L2 flushed before each)."""
     import torch
@@ -371,13 +384,10 @@ def run_ours(args):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
     px_per_step = C * H * W
-    value = ws * px_per_step * args.steps / (total_ms * 1e-3) / 1e6
+    value, total_ms = aggregate(total_ms, px_per_step, args.steps, ws, dev)
+    if ws > 1:
+        torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
 
     # end to end through the host-buffer entry point (pinned host memory)

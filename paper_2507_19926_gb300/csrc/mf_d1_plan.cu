@@ -8,7 +8,7 @@
 //     discarded (forgetfulness, Sec. 2.2); all cores of a level have the
 //     same length and the same count d of values dropped below the median;
 //   - rows[i][fy]: sorted extra row fy over the core columns of node column
-//     i -- shared by every node of that column (Sec. 5.2: sorted rows are
+//     i -- shared by every node of that column (Sec. 5.3: sorted rows are
 //     shared between vertically contiguous tiles);
 //   - cols[j][fx]: sorted extra column fx over the core rows of node row j,
 //     shared by the nodes of that row.

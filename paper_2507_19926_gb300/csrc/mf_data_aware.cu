@@ -2,7 +2,7 @@
 //
 // The paper runs the recursion as a multi-pass pipeline of seven kernels
 // over three streams with the per-level state in global memory (up to two
-// orders of magnitude above the image size, Sec. 5.2 / 6.1).  Here one
+// orders of magnitude above the image size, Sec. 5.3 and 7.1).  Here one
 // thread block owns one T x T root tile and keeps the whole state of its
 // tree -- footprint, sorted columns, rows, cores -- in shared memory; the
 // statically planned phases (mf_d1_plan.cu) replace the kernel boundaries
