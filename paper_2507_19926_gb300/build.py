@@ -27,17 +27,34 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I" + INCLUDE, "-I" + CSRC, "-I" + GEN]
 
-# Data-oblivious instantiations: k -> (tile w, tile h, block x, block y).
+# Data-oblivious instantiations: k -> list of (tile w, tile h, block x,
+# block y, U); the first entry is the default, the autotuner may pick
+# another.  U is the number of tree levels emitted unrolled: deeper levels
+# are loop-rolled (rolled.py), U = -1 is the straight-line network.
 # Root tiles follow t(k) = 2^(floor(log2 k) - 1) (paper Sec. 4.2) up to
 # k = 7 and stay at 4x4 above: an 8x8 root tile's network no longer fits
 # the 255 registers of one thread (the paper's own limit, Sec. 4.3).
-O1_VALUE = {3: (2, 2, 32, 4), 5: (2, 2, 32, 4), 7: (4, 4, 32, 4), 9: (4, 4, 32, 4),
-            11: (4, 4, 32, 4), 13: (4, 4, 32, 4), 15: (4, 4, 32, 4), 17: (4, 4, 32, 4)}
+# Measured on GB300 (4096^2 u8/u32): straight-line is fastest up to k = 15,
+# the fully rolled tree at k = 17 (13-15% faster than straight-line there,
+# where the straight-line code no longer stays in the instruction cache).
+O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1)], 9: [(4, 4, 32, 4, -1)],
+            11: [(4, 4, 32, 4, -1)], 13: [(4, 4, 32, 4, -1)], 15: [(4, 4, 32, 4, -1)],
+            17: [(4, 4, 32, 4, 0)], 19: [(4, 4, 32, 4, 0)], 21: [(4, 4, 32, 4, 0)], 23: [(4, 4, 32, 4, 0)],
+            25: [(4, 4, 32, 4, 0)]}
+# extra configurations for timing (comma list "k:tw:th:bx:by:U" in MF_O1_EXTRA)
+for _spec in filter(None, os.environ.get("MF_O1_EXTRA", "").split(",")):
+    _v = [int(v) for v in _spec.split(":")]
+    O1_VALUE.setdefault(_v[0], []).append(tuple(_v[1:6]) if len(_v) > 5 else tuple(_v[1:5]) + (0,))
 # argmedian with 32-bit records (8/16-bit data) and 64-bit records (32-bit data)
-O1_ARG32 = {k: v for k, v in O1_VALUE.items()}
-O1_ARG64 = {k: v for k, v in O1_VALUE.items() if k <= 9}
+O1_ARG32 = {k: v[0] for k, v in O1_VALUE.items()}
+O1_ARG64 = {k: v[0] for k, v in O1_VALUE.items() if k <= 9}
+
 
 DT_NAMES = {0: "MF_U8", 1: "MF_U16", 2: "MF_U32", 3: "MF_F32"}
+
+# Loop-rolled networks (one child per split emitted, run twice): same ops,
+# roughly half the code per tree level.
+O1_ROLLED = os.environ.get("MF_O1_ROLLED", "1") == "1"
 
 # Barrier spacing (min/max ops) inside long per-thread networks.
 O1_SYNC_EVERY = int(os.environ.get("MF_O1_SYNC_EVERY", "0"))
@@ -46,46 +63,60 @@ O1_SYNC_EVERY = int(os.environ.get("MF_O1_SYNC_EVERY", "0"))
 def _o1_instances():
     """(k, tw, th, bx, by, dtype, ko, arg, ib) for every O1 kernel built."""
     out = []
-    for k, (tw, th, bx, by) in sorted(O1_VALUE.items()):
-        for dt in (0, 1):
-            out.append((k, tw, th, bx, by, dt, "KoU16x2", False, 0))
+    for k, cfgs in sorted(O1_VALUE.items()):
+        for (tw, th, bx, by, u) in cfgs:
+            for dt in (0, 1):
+                out.append((k, tw, th, bx, by, u, dt, "KoU16x2", False, 0))
+            for dt in (2, 3):
+                out.append((k, tw, th, bx, by, u, dt, "KoU32", False, 0))
+    for k, (tw, th, bx, by, u) in sorted(O1_ARG32.items()):
+        out.append((k, tw, th, bx, by, u, 0, "KoU32", True, 24))
+        out.append((k, tw, th, bx, by, u, 1, "KoU32", True, 16))
+    for k, (tw, th, bx, by, u) in sorted(O1_ARG64.items()):
         for dt in (2, 3):
-            out.append((k, tw, th, bx, by, dt, "KoU32", False, 0))
-    for k, (tw, th, bx, by) in sorted(O1_ARG32.items()):
-        out.append((k, tw, th, bx, by, 0, "KoU32", True, 24))
-        out.append((k, tw, th, bx, by, 1, "KoU32", True, 16))
-    for k, (tw, th, bx, by) in sorted(O1_ARG64.items()):
-        for dt in (2, 3):
-            out.append((k, tw, th, bx, by, dt, "KoU64", True, 32))
+            out.append((k, tw, th, bx, by, u, dt, "KoU64", True, 32))
     return out
 
 
 def generate():
     os.makedirs(GEN, exist_ok=True)
+    for name in os.listdir(GEN):
+        if name.startswith("o1_k") and name.endswith(".cu"):
+            os.remove(os.path.join(GEN, name))
     codegen.write_if_changed(os.path.join(GEN, "d1_sortnets.cuh"), codegen.emit_d1_sortnets())
     insts = _o1_instances()
     by_k = {}
-    for inst in insts:
-        by_k.setdefault(inst[0], []).append(inst)
+    for inst in insts:  # one translation unit per instantiation (parallel build)
+        by_k.setdefault(inst[:6] + (inst[7], inst[8], inst[6]), []).append(inst)
     tus = []
     decls = []
     entries = []
-    for k, lst in sorted(by_k.items()):
+
+    def cfg_rank(key):  # each k's configurations in their listed order (default first)
+        cfgs = O1_VALUE.get(key[0], [])
+        return (key[0], cfgs.index(key[1:6]) if key[1:6] in cfgs else len(cfgs))
+
+    for key, lst in sorted(by_k.items(), key=lambda kv: cfg_rank(kv[0])):
+        k = key[0]
         parts = ['// generated by codegen/build.py -- do not edit', '#include "mf_oblivious.cuh"',
                  "namespace mf {"]
+        unroll = key[5]
         nets = sorted({(i[1], i[2]) for i in lst})
         sorts = sorted({k - th + 1 for (_, th) in nets})
         for tw, th in nets:
             net = netgen.build(k, tw, th)
             sync = O1_SYNC_EVERY if O1_SYNC_EVERY and len(net.ops) > 4 * O1_SYNC_EVERY else 0
-            parts.append(codegen.emit_network(net, codegen.net_name(k, tw, th), sync))
+            u_eff = unroll if O1_ROLLED else -1
+            src, _ = codegen.emit_network_auto(net, codegen.net_name(k, tw, th, u_eff), sync, u_eff)
+            parts.append(src)
         for n in sorts:
             parts.append(codegen.emit_colsort(n))
-        for (k_, tw, th, bx, by, dt, ko, arg, ib) in lst:
-            fn = "o1_launch_k%d_%dx%d_%s_%s%s" % (k, tw, th, DT_NAMES[dt], ko, "_arg" if arg else "")
+        for (k_, tw, th, bx, by, u, dt, ko, arg, ib) in lst:
+            fn = "o1_launch_k%d_%dx%d_b%dx%d_u%s_%s_%s%s" % (k, tw, th, bx, by, "m1" if u < 0 else u,
+                                                          DT_NAMES[dt], ko, "_arg" if arg else "")
             targs = "%d, %d, %d, %d, %d, %s, %s, %s, %d, %s, %s" % (
                 k, tw, th, bx, by, DT_NAMES[dt], ko, "true" if arg else "false", ib,
-                codegen.net_name(k, tw, th), codegen.sort_name(k - th + 1))
+                codegen.net_name(k, tw, th, u if O1_ROLLED else -1), codegen.sort_name(k - th + 1))
             parts.append("int %s(const ImgArgs &a, int c, cudaStream_t s) {\n"
                          "  return launch_o1<%s>(a, c, s);\n}" % (fn, targs))
             pfn = "NULL"
@@ -101,7 +132,8 @@ def generate():
                            (k, DT_NAMES[dt], 1 if arg else 0, tw, th, bx, by,
                             netgen.build(k, tw, th).ops.__len__(), fn, pfn, fn))
         parts.append("}  // namespace mf")
-        path = os.path.join(GEN, "o1_k%d.cu" % k)
+        path = os.path.join(GEN, "o1_k%d_%dx%d_b%dx%d_u%s_%s%s_%s.cu" % (
+            key[:5] + ("m1" if key[5] < 0 else key[5], key[6], "_arg" if key[7] else "", DT_NAMES[key[8]])))
         codegen.write_if_changed(path, "\n".join(parts) + "\n")
         tus.append(path)
     reg = ['// generated -- do not edit', '#include "mf_registry.h"', "namespace mf {"]

@@ -16,8 +16,13 @@ import os
 from . import netgen
 
 
-def net_name(k, tw, th):
-    return "Net_k%d_%dx%d" % (k, tw, th)
+def net_name(k, tw, th, unroll=None):
+    """Struct name of one generated network; distinct per emission form so
+    that no two translation units define the same kernel differently."""
+    base = "Net_k%d_%dx%d" % (k, tw, th)
+    if unroll is None:
+        return base
+    return base + ("_flat" if unroll < 0 else "_u%d" % unroll)
 
 
 def sort_name(n):
@@ -33,10 +38,9 @@ def emit_network(net, name, sync_every=0):
     w = lines.append
     w("struct %s {" % name)
     w("  static constexpr int n_ops = %d;" % len(net.ops))
-    w("  template <class KO, class L>")
+    w("  template <class KO, class L, class OUT>")
     w("  static __device__ __forceinline__ void run(const typename KO::T *__restrict__ cs,")
-    w("                                            const typename KO::T *__restrict__ rw,")
-    w("                                            typename KO::T *o) {")
+    w("                                            const typename KO::T *__restrict__ rw, OUT &out) {")
     w("    typedef typename KO::T T;")
     n_in = len(net.inputs)
     loaded = [False] * n_in
@@ -57,10 +61,23 @@ def emit_network(net, name, sync_every=0):
         if sync_every and n % sync_every == sync_every - 1:
             w("    __syncthreads();")
     for i, v in enumerate(net.outputs):
-        w("    o[%d] = %s;" % (i, ref(v)))
+        w("    out(%d, %s);" % (i, ref(v)))
     w("  }")
     w("};")
     return "\n".join(lines) + "\n"
+
+
+def emit_network_auto(net, name, sync_every=0, unroll_levels=0):
+    """The loop-rolled form (rolled.py) when the tree's children pair up,
+    else the straight-line form.  unroll_levels < 0 forces straight-line."""
+    from . import rolled
+    if unroll_levels >= 0:
+        try:
+            ir, _ = rolled.build_ir(net)
+            return rolled.emit(net, ir, name, unroll_levels=unroll_levels), True
+        except rolled.RollError:
+            pass
+    return emit_network(net, name, sync_every), False
 
 
 def emit_colsort(n):

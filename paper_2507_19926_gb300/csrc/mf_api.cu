@@ -27,11 +27,19 @@ void set_error(const char *fmt, ...) {
 
 void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-const O1Entry *find_o1(int k, int dtype, bool arg) {
+// The nth (0-based) instantiated configuration for (k, dtype, arg); the
+// first one is the default.
+const O1Entry *find_o1_nth(int k, int dtype, bool arg, int nth) {
     for (int i = 0; i < kO1Count; i++)
         if (kO1Entries[i].k == k && kO1Entries[i].dtype == dtype && kO1Entries[i].arg == (arg ? 1 : 0))
-            return &kO1Entries[i];
+            if (nth-- == 0) return &kO1Entries[i];
     return nullptr;
+}
+
+const O1Entry *find_o1(int k, int dtype, bool arg) {
+    const int tuned = tune_lookup(k, dtype, arg) == MF_OBLIVIOUS ? tune_tile(k, dtype, arg) : 0;
+    const O1Entry *e = tuned ? find_o1_nth(k, dtype, arg, tuned) : nullptr;
+    return e ? e : find_o1_nth(k, dtype, arg, 0);
 }
 
 static int esize(int dtype) {

@@ -261,7 +261,7 @@ int d1_supported_tile(int k, int dtype, bool arg, int T) {
 }
 
 int d1_default_tile(int k, int dtype, bool arg) {
-    const int tuned = tune_tile(k, dtype, arg);
+    const int tuned = tune_lookup(k, dtype, arg) == MF_DATA_AWARE ? tune_tile(k, dtype, arg) : 0;
     if (tuned && d1_supported_tile(k, dtype, arg, tuned)) return tuned;
     // root-tile heuristic t(k) = 2^(floor(log2 k) - 1) (paper Sec. 4.2), at
     // least 2 and at most 16, lowered until the tree's state fits in shared

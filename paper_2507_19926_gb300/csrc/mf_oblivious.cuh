@@ -106,6 +106,43 @@ struct O1Words<DT, KoU64, true, IB> {  // 32-bit argmedian: key << 32 | index
     }
 };
 
+// Writes the median of tile pixel `pix` (row-major in the TW x TH tile) of
+// every lane: the value, or in argmedian mode the value and the source index
+// recovered from the composite record.
+template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB>
+struct O1Store {
+    typedef O1Layout<K, TW, TH, BX, BY> L;
+    typedef typename KO::T T;
+    typedef typename Dt<DT>::E E;
+    const ImgArgs &a;
+    char *dst;
+    char *idx;
+    int bx0, by0, tx, ty;
+    __device__ __forceinline__ void operator()(int pix, T w) const {
+        constexpr int P = KO::lanes;
+        const int py = pix / TW, px = pix - py * TW;
+        const int y = by0 + ty * TH + py;
+        if (y >= a.H) return;
+#pragma unroll
+        for (int l = 0; l < P; l++) {
+            const int x = bx0 + l * BX * TW + tx * TW + px;
+            if (x >= a.W) continue;
+            if (!ARG) {
+                const uint32_t key = P == 2 ? (uint32_t)((w >> (16 * l)) & 0xffffu) : (uint32_t)w;
+                if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
+            } else {
+                const uint32_t fidx = (uint32_t)(w & ((1ull << IB) - 1));
+                const uint32_t key = (uint32_t)(w >> IB);
+                const int fy = fidx / L::FW, gx = fidx - fy * L::FW;
+                const int ys = clampi(by0 - L::R + fy, 0, a.H - 1);
+                const int xs = clampi(bx0 - L::R + gx, 0, a.W - 1);
+                if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
+                if (idx) reinterpret_cast<int32_t *>(idx + (size_t)y * a.idx_pitch)[x] = ys * a.W + xs;
+            }
+        }
+    }
+};
+
 // One block's work: the block of tiles at (bxi, byi) of plane z.
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
           class CSORT>
@@ -147,39 +184,12 @@ __device__ __forceinline__ void o1_block(const ImgArgs &a, int bxi, int byi, int
     }
     __syncthreads();
 
-    // 3. the tile's hierarchical network
-    T o[TW * TH];
-    NET::template run<KO, L>(sm + L::CSB + ty * L::CSTY + tx, sm + ty * TH * L::RS + tx, o);
-
-    // 4. results
-    char *dst = a.dst ? a.dst + (size_t)z * a.plane : nullptr;
-    char *idx = a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)z * a.idx_plane : nullptr;
-#pragma unroll
-    for (int py = 0; py < TH; py++) {
-        const int y = by0 + ty * TH + py;
-        if (y >= a.H) break;
-#pragma unroll
-        for (int l = 0; l < P; l++) {
-#pragma unroll
-            for (int px = 0; px < TW; px++) {
-                const int x = bx0 + l * BX * TW + tx * TW + px;
-                if (x >= a.W) break;
-                const T w = o[py * TW + px];
-                if (!ARG) {
-                    const uint32_t key = P == 2 ? (uint32_t)((w >> (16 * l)) & 0xffffu) : (uint32_t)w;
-                    if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
-                } else {
-                    const uint32_t fidx = (uint32_t)(w & ((1ull << IB) - 1));
-                    const uint32_t key = (uint32_t)(w >> IB);
-                    const int fy = fidx / L::FW, gx = fidx - fy * L::FW;
-                    const int ys = clampi(by0 - L::R + fy, 0, a.H - 1);
-                    const int xs = clampi(bx0 - L::R + gx, 0, a.W - 1);
-                    if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
-                    if (idx) reinterpret_cast<int32_t *>(idx + (size_t)y * a.idx_pitch)[x] = ys * a.W + xs;
-                }
-            }
-        }
-    }
+    // 3. the tile's hierarchical network; each median goes straight to
+    //    the store functor as the recursion reaches its leaf
+    O1Store<K, TW, TH, BX, BY, DT, KO, ARG, IB> out{a, a.dst ? a.dst + (size_t)z * a.plane : nullptr,
+                                                     a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)z * a.idx_plane : nullptr,
+                                                     bx0, by0, tx, ty};
+    NET::template run<KO, L>(sm + L::CSB + ty * L::CSTY + tx, sm + ty * TH * L::RS + tx, out);
 }
 
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,

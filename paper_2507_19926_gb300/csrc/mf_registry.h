@@ -25,7 +25,9 @@ struct O1Entry {
 extern const O1Entry kO1Entries[];
 extern const int kO1Count;
 
+// The configuration the tuning table selects (else the default).
 const O1Entry *find_o1(int k, int dtype, bool arg);
+const O1Entry *find_o1_nth(int k, int dtype, bool arg, int nth);
 
 // Data-aware variant (mf_data_aware.cu).
 int d1_supported(int k, int dtype, bool arg);

@@ -145,12 +145,15 @@ extern "C" int mf_autotune(const void *src, void *dst, int H, int W, size_t pitc
     cudaStream_t s = (cudaStream_t)stream;
     float best = 1e30f;
     int best_var = 0, best_tile = 0;
-    const O1Entry *o1 = find_o1(k, dtype, false);
-    if (o1) {
+    const bool verbose = getenv("MF_TUNE_VERBOSE") != nullptr;
+    for (int nth = 0;; nth++) {
+        const O1Entry *o1 = find_o1_nth(k, dtype, false, nth);
+        if (!o1) break;
         Cand c{&a, channels, k, dtype, 0, o1, s};
         int rc;
         float ms = time_ms(run_cand, &c, s, &rc);
-        if (rc == MF_OK && ms < best) { best = ms; best_var = MF_OBLIVIOUS; best_tile = 0; }
+        if (verbose) fprintf(stderr, "mf_autotune k=%d dtype=%d %s: %.4f ms (rc %d)\n", k, (int)dtype, o1->name, ms, rc);
+        if (rc == MF_OK && ms < best) { best = ms; best_var = MF_OBLIVIOUS; best_tile = nth; }
     }
     if (d1_supported(k, dtype, false)) {
         for (int tile = 2; tile <= 32; tile *= 2) {
@@ -158,6 +161,7 @@ extern "C" int mf_autotune(const void *src, void *dst, int H, int W, size_t pitc
             Cand c{&a, channels, k, dtype, tile, nullptr, s};
             int rc;
             float ms = time_ms(run_cand, &c, s, &rc);
+            if (verbose) fprintf(stderr, "mf_autotune k=%d dtype=%d data-aware tile %d: %.4f ms (rc %d)\n", k, (int)dtype, tile, ms, rc);
             if (rc == MF_OK && ms < best) { best = ms; best_var = MF_DATA_AWARE; best_tile = tile; }
         }
     }

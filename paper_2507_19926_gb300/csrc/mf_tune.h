@@ -6,7 +6,8 @@ namespace mf {
 
 // MF_AUTO when nothing is recorded.
 int tune_lookup(int k, int dtype, bool arg);
-// 0 when nothing is recorded.
+// Data-aware: the root tile; data-oblivious: the configuration index
+// (0 = default).  0 when nothing is recorded.
 int tune_tile(int k, int dtype, bool arg);
 void tune_record(int k, int dtype, bool arg, int variant, int tile, float ms);
 

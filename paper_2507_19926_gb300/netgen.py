@@ -64,11 +64,15 @@ class Network:
 
     def __post_init__(self):
         self._kind = []  # value id -> ("in", desc) | ("op", index)
+        self.cur_path = ()   # tree path (child index per split) of ops being created
+        self.op_path = {}    # value id -> tree path
+        self.leaf_pixel = {}  # leaf tree path -> row-major pixel index in the tile
 
     def _op(self, kind, a, b):
         v = len(self._kind)
         self.ops.append((kind, a, b, v))
         self._kind.append(("op", len(self.ops) - 1))
+        self.op_path[v] = self.cur_path
         return v
 
     def vmin(self, a, b):
@@ -238,15 +242,17 @@ def build(k, tw, th=None):
 
     outputs = {}
 
-    def recurse(x0, y0, tw_, th_, core, d, cols, rows):
+    def recurse(x0, y0, tw_, th_, core, d, cols, rows, path=()):
         if tw_ == 1 and th_ == 1:
             assert len(core) == 1
             outputs[(y0, x0)] = core[0]
+            net.leaf_pixel[path] = y0 * tw + x0
             return
         (cx0, cx1), (cy0, cy1) = node_core_rect(x0, y0, tw_, th_)
         if tw_ >= th_:  # horizontal split: halve the width
             h = tw_ // 2
-            for cx in (x0, x0 + h):
+            for si, cx in enumerate((x0, x0 + h)):
+                net.cur_path = path + (si,)
                 ncx0, ncx1 = cx + h - 1, cx + k - 1
                 new = [fx for fx in range(ncx0, ncx1 + 1) if not (cx0 <= fx <= cx1)]
                 c = (ncx1 - ncx0 + 1) * (cy1 - cy0 + 1)
@@ -262,10 +268,12 @@ def build(k, tw, th=None):
                     if y0 <= fy <= y0 + th_ + k - 2:
                         corners = net.sort([px(fy, fx) for fx in new])
                         nrows[fy] = net.merge(r, corners)
-                recurse(cx, y0, h, th_, ncore, d + lo, ncols, nrows)
+                recurse(cx, y0, h, th_, ncore, d + lo, ncols, nrows, path + (si,))
+                net.cur_path = path
         else:  # vertical split: halve the height
             h = th_ // 2
-            for cy in (y0, y0 + h):
+            for si, cy in enumerate((y0, y0 + h)):
+                net.cur_path = path + (si,)
                 ncy0, ncy1 = cy + h - 1, cy + k - 1
                 new = [fy for fy in range(ncy0, ncy1 + 1) if not (cy0 <= fy <= cy1)]
                 c = (cx1 - cx0 + 1) * (ncy1 - ncy0 + 1)
@@ -279,7 +287,8 @@ def build(k, tw, th=None):
                     if x0 <= fx <= x0 + tw_ + k - 2:
                         corners = net.sort([px(fy, fx) for fy in new])
                         ncols[fx] = net.merge(cl, corners)
-                recurse(x0, cy, tw_, h, ncore, d + lo, ncols, nrows)
+                recurse(x0, cy, tw_, h, ncore, d + lo, ncols, nrows, path + (si,))
+                net.cur_path = path
 
     recurse(0, 0, tw, th, core, d, cols, rows)
     net.outputs = [outputs[(y, x)] for y in range(th) for x in range(tw)]
@@ -310,6 +319,8 @@ def prune(net):
     out.ops = new_ops
     out.outputs = [order[v] for v in net.outputs]
     out._memo = {d: order[net._memo[d]] for d in new_inputs}
+    out.op_path = {order[v]: p for v, p in net.op_path.items() if v in order}
+    out.leaf_pixel = dict(net.leaf_pixel)
     return out
 
 
@@ -362,6 +373,8 @@ def schedule(net, out_order):
     out.ops = order
     out.outputs = net.outputs
     out._memo = net._memo
+    out.op_path = net.op_path
+    out.leaf_pixel = net.leaf_pixel
     return out
 
 
