@@ -39,15 +39,21 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # where the straight-line code no longer stays in the instruction cache).
 O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1)], 9: [(4, 4, 32, 4, -1)],
             11: [(4, 4, 32, 4, -1)], 13: [(4, 4, 32, 4, -1)], 15: [(4, 4, 32, 4, -1)],
-            17: [(4, 4, 32, 4, 0)], 19: [(4, 4, 32, 4, 0)], 21: [(4, 4, 32, 4, 0)], 23: [(4, 4, 32, 4, 0)],
+            17: [(4, 4, 32, 4, 0)], 19: [(4, 4, 32, 4, 0, 1)], 21: [(4, 4, 32, 4, 0)], 23: [(4, 4, 32, 4, 0)],
             25: [(4, 4, 32, 4, 0)]}
-# extra configurations for timing (comma list "k:tw:th:bx:by:U" in MF_O1_EXTRA)
+# extra configurations for timing (comma list "k:tw:th:bx:by:U[:R]" in
+# MF_O1_EXTRA); R = 1: the root extra rows are sorted into shared memory
+# by a stage of their own (netgen.build rows_smem)
 for _spec in filter(None, os.environ.get("MF_O1_EXTRA", "").split(",")):
     _v = [int(v) for v in _spec.split(":")]
-    O1_VALUE.setdefault(_v[0], []).append(tuple(_v[1:6]) if len(_v) > 5 else tuple(_v[1:5]) + (0,))
+    O1_VALUE.setdefault(_v[0], []).append(tuple((_v + [0, 0])[1:7]))
+O1_VALUE = {k: [tuple(c) + (0,) * (6 - len(c)) for c in v] for k, v in O1_VALUE.items()}
 # argmedian with 32-bit records (8/16-bit data) and 64-bit records (32-bit data)
 O1_ARG32 = {k: v[0] for k, v in O1_VALUE.items()}
-O1_ARG64 = {k: v[0] for k, v in O1_VALUE.items() if k <= 9}
+# 32-bit data: the argmedian comes from the value kernel plus the recovery
+# pass (mf_argmedian.cu), which beats 64-bit records (1.33 vs ~0.4 ms at
+# k = 9, f32 16 x 1024^2); no 64-bit-record networks are built.
+O1_ARG64 = {}
 
 
 DT_NAMES = {0: "MF_U8", 1: "MF_U16", 2: "MF_U32", 3: "MF_F32"}
@@ -64,17 +70,17 @@ def _o1_instances():
     """(k, tw, th, bx, by, dtype, ko, arg, ib) for every O1 kernel built."""
     out = []
     for k, cfgs in sorted(O1_VALUE.items()):
-        for (tw, th, bx, by, u) in cfgs:
+        for (tw, th, bx, by, u, rs) in cfgs:
             for dt in (0, 1):
-                out.append((k, tw, th, bx, by, u, dt, "KoU16x2", False, 0))
+                out.append((k, tw, th, bx, by, (u, rs), dt, "KoU16x2", False, 0))
             for dt in (2, 3):
-                out.append((k, tw, th, bx, by, u, dt, "KoU32", False, 0))
-    for k, (tw, th, bx, by, u) in sorted(O1_ARG32.items()):
-        out.append((k, tw, th, bx, by, u, 0, "KoU32", True, 24))
-        out.append((k, tw, th, bx, by, u, 1, "KoU32", True, 16))
-    for k, (tw, th, bx, by, u) in sorted(O1_ARG64.items()):
+                out.append((k, tw, th, bx, by, (u, rs), dt, "KoU32", False, 0))
+    for k, (tw, th, bx, by, u, rs) in sorted(O1_ARG32.items()):
+        out.append((k, tw, th, bx, by, (u, rs), 0, "KoU32", True, 24))
+        out.append((k, tw, th, bx, by, (u, rs), 1, "KoU32", True, 16))
+    for k, (tw, th, bx, by, u, rs) in sorted(O1_ARG64.items()):
         for dt in (2, 3):
-            out.append((k, tw, th, bx, by, u, dt, "KoU64", True, 32))
+            out.append((k, tw, th, bx, by, (u, rs), dt, "KoU64", True, 32))
     return out
 
 
@@ -94,29 +100,32 @@ def generate():
 
     def cfg_rank(key):  # each k's configurations in their listed order (default first)
         cfgs = O1_VALUE.get(key[0], [])
-        return (key[0], cfgs.index(key[1:6]) if key[1:6] in cfgs else len(cfgs))
+        c = key[1:5] + key[5]
+        return (key[0], cfgs.index(c) if c in cfgs else len(cfgs))
 
     for key, lst in sorted(by_k.items(), key=lambda kv: cfg_rank(kv[0])):
         k = key[0]
         parts = ['// generated by codegen/build.py -- do not edit', '#include "mf_oblivious.cuh"',
                  "namespace mf {"]
-        unroll = key[5]
+        unroll, rsm = key[5]
         nets = sorted({(i[1], i[2]) for i in lst})
-        sorts = sorted({k - th + 1 for (_, th) in nets})
+        sorts = sorted({k - th + 1 for (_, th) in nets} | {k - tw + 1 for (tw, _) in nets})
         for tw, th in nets:
-            net = netgen.build(k, tw, th)
+            net = netgen.build(k, tw, th, rows_smem=bool(rsm))
             sync = O1_SYNC_EVERY if O1_SYNC_EVERY and len(net.ops) > 4 * O1_SYNC_EVERY else 0
             u_eff = unroll if O1_ROLLED else -1
-            src, _ = codegen.emit_network_auto(net, codegen.net_name(k, tw, th, u_eff), sync, u_eff)
+            src, _ = codegen.emit_network_auto(net, codegen.net_name(k, tw, th, u_eff, bool(rsm)), sync, u_eff)
             parts.append(src)
         for n in sorts:
             parts.append(codegen.emit_colsort(n))
-        for (k_, tw, th, bx, by, u, dt, ko, arg, ib) in lst:
-            fn = "o1_launch_k%d_%dx%d_b%dx%d_u%s_%s_%s%s" % (k, tw, th, bx, by, "m1" if u < 0 else u,
-                                                          DT_NAMES[dt], ko, "_arg" if arg else "")
-            targs = "%d, %d, %d, %d, %d, %s, %s, %s, %d, %s, %s" % (
+        for (k_, tw, th, bx, by, (u, rsm), dt, ko, arg, ib) in lst:
+            fn = "o1_launch_k%d_%dx%d_b%dx%d_u%s%s_%s_%s%s" % (k, tw, th, bx, by, "m1" if u < 0 else u,
+                                                            "_rs" if rsm else "", DT_NAMES[dt], ko,
+                                                            "_arg" if arg else "")
+            targs = "%d, %d, %d, %d, %d, %s, %s, %s, %d, %s, %s, %s" % (
                 k, tw, th, bx, by, DT_NAMES[dt], ko, "true" if arg else "false", ib,
-                codegen.net_name(k, tw, th, u if O1_ROLLED else -1), codegen.sort_name(k - th + 1))
+                codegen.net_name(k, tw, th, u if O1_ROLLED else -1, bool(rsm)), codegen.sort_name(k - th + 1),
+                codegen.sort_name(k - tw + 1))
             parts.append("int %s(const ImgArgs &a, int c, cudaStream_t s) {\n"
                          "  return launch_o1<%s>(a, c, s);\n}" % (fn, targs))
             pfn = "NULL"
@@ -132,8 +141,9 @@ def generate():
                            (k, DT_NAMES[dt], 1 if arg else 0, tw, th, bx, by,
                             netgen.build(k, tw, th).ops.__len__(), fn, pfn, fn))
         parts.append("}  // namespace mf")
-        path = os.path.join(GEN, "o1_k%d_%dx%d_b%dx%d_u%s_%s%s_%s.cu" % (
-            key[:5] + ("m1" if key[5] < 0 else key[5], key[6], "_arg" if key[7] else "", DT_NAMES[key[8]])))
+        path = os.path.join(GEN, "o1_k%d_%dx%d_b%dx%d_u%s%s_%s%s_%s.cu" % (
+            key[:5] + ("m1" if key[5][0] < 0 else key[5][0], "_rs" if key[5][1] else "", key[6],
+                       "_arg" if key[7] else "", DT_NAMES[key[8]])))
         codegen.write_if_changed(path, "\n".join(parts) + "\n")
         tus.append(path)
     reg = ['// generated -- do not edit', '#include "mf_registry.h"', "namespace mf {"]

@@ -16,13 +16,13 @@ import os
 from . import netgen
 
 
-def net_name(k, tw, th, unroll=None):
+def net_name(k, tw, th, unroll=None, rows_smem=False):
     """Struct name of one generated network; distinct per emission form so
     that no two translation units define the same kernel differently."""
     base = "Net_k%d_%dx%d" % (k, tw, th)
     if unroll is None:
         return base
-    return base + ("_flat" if unroll < 0 else "_u%d" % unroll)
+    return base + ("_flat" if unroll < 0 else "_u%d" % unroll) + ("_rs" if rows_smem else "")
 
 
 def sort_name(n):
@@ -38,9 +38,11 @@ def emit_network(net, name, sync_every=0):
     w = lines.append
     w("struct %s {" % name)
     w("  static constexpr int n_ops = %d;" % len(net.ops))
+    w("  static constexpr bool rows_smem = %s;" % ("true" if any(d[0] == "row" for d in net.inputs) else "false"))
     w("  template <class KO, class L, class OUT>")
     w("  static __device__ __forceinline__ void run(const typename KO::T *__restrict__ cs,")
-    w("                                            const typename KO::T *__restrict__ rw, OUT &out) {")
+    w("                                            const typename KO::T *__restrict__ rw,")
+    w("                                            const typename KO::T *__restrict__ rs, OUT &out) {")
     w("    typedef typename KO::T T;")
     n_in = len(net.inputs)
     loaded = [False] * n_in
@@ -50,6 +52,8 @@ def emit_network(net, name, sync_every=0):
             desc = net.inputs[v]
             if desc[0] == "col":
                 w("    const T v%d = cs[L::col(%d, %d)];" % (v, desc[1], desc[2]))
+            elif desc[0] == "row":
+                w("    const T v%d = rs[L::row(%d, %d)];" % (v, desc[1], desc[2]))
             else:
                 w("    const T v%d = rw[L::px(%d, %d)];" % (v, desc[1], desc[2]))
             loaded[v] = True

@@ -161,6 +161,15 @@ static int run_filter(const void *src, void *dst, int H, int W, size_t pitch, in
         }
         return idx ? launch_identity_idx(a, C, s) : MF_OK;
     }
+    // Argmedian where no record-carrying network is instantiated for (k,
+    // dtype): compute the medians with the value kernel, then recover each
+    // median's source from the window (mf_argmedian.cu).
+    if (idx && dst && variant != MF_DATA_AWARE && !find_o1(k, dtype, true) &&
+        (variant == MF_AUTO || find_o1(k, dtype, false))) {
+        int rc = run_filter(src, dst, H, W, pitch, C, dtype, k, variant, nullptr, 0, s);
+        if (rc) return rc;
+        return launch_argmedian_from_values(a, C, k, dtype, s);
+    }
     Plan p;
     int rc = resolve(k, dtype, idx != nullptr, variant, &p);
     if (rc) return rc;

@@ -30,7 +30,7 @@
 
 namespace mf {
 
-template <int K, int TW, int TH, int BX, int BY>
+template <int K, int TW, int TH, int BX, int BY, bool ROWS = false>
 struct O1Layout {
     static constexpr int R = (K - 1) / 2;
     static constexpr int FW = BX * TW + K - 1;  // footprint width of one lane half
@@ -41,7 +41,13 @@ struct O1Layout {
     static constexpr int RS = TW * G;           // words per shared-memory row
     static constexpr int CSB = FH * RS;         // start of the sorted column segments
     static constexpr int CSTY = CH0 * RS;       // words per tile row of segments
-    static constexpr int WORDS = CSB + BY * CSTY;
+    // optional: each thread's root extra rows, sorted, in a slot of its own
+    // (odd stride: the 32 lanes of a warp hit 32 different banks)
+    static constexpr int CW0 = K - TW + 1;      // root core width
+    static constexpr int NRW = 2 * (TH - 1);    // extra rows per root tile
+    static constexpr int RSTRIDE = (NRW * CW0) | 1;
+    static constexpr int RSB = CSB + BY * CSTY;
+    static constexpr int WORDS = RSB + (ROWS ? BX * BY * RSTRIDE : 0);
     static __host__ __device__ constexpr int at(int fy, int gx) {
         return fy * RS + (gx % TW) * G + gx / TW;
     }
@@ -52,6 +58,10 @@ struct O1Layout {
     }
     static __host__ __device__ constexpr int col(int fx, int i) {
         return i * RS + (fx % TW) * G + fx / TW;
+    }
+    // element i of the sorted extra row fy (footprint row) in the thread's slot
+    static __host__ __device__ constexpr int row(int fy, int i) {
+        return (fy < TH - 1 ? fy : TH - 1 + fy - K) * CW0 + i;
     }
 };
 
@@ -111,7 +121,7 @@ struct O1Words<DT, KoU64, true, IB> {  // 32-bit argmedian: key << 32 | index
 // recovered from the composite record.
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB>
 struct O1Store {
-    typedef O1Layout<K, TW, TH, BX, BY> L;
+    typedef O1Layout<K, TW, TH, BX, BY> L;  // FW and R do not depend on ROWS
     typedef typename KO::T T;
     typedef typename Dt<DT>::E E;
     const ImgArgs &a;
@@ -145,9 +155,9 @@ struct O1Store {
 
 // One block's work: the block of tiles at (bxi, byi) of plane z.
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
-          class CSORT>
+          class CSORT, class RSORT>
 __device__ __forceinline__ void o1_block(const ImgArgs &a, int bxi, int byi, int z) {
-    typedef O1Layout<K, TW, TH, BX, BY> L;
+    typedef O1Layout<K, TW, TH, BX, BY, NET::rows_smem> L;
     typedef typename KO::T T;
     typedef typename Dt<DT>::E E;
     constexpr int P = KO::lanes;
@@ -184,18 +194,39 @@ __device__ __forceinline__ void o1_block(const ImgArgs &a, int bxi, int byi, int
     }
     __syncthreads();
 
+    // 2b. (networks that take their extra rows sorted) each thread sorts the
+    //     root extra rows of its own tile into its slot; the barrier makes the
+    //     network reload them where it uses them instead of holding them in
+    //     registers through the core initialisation
+    if (NET::rows_smem) {
+        const T *rwt = sm + ty * TH * L::RS + tx;
+        T *rst = sm + L::RSB + (ty * BX + tx) * L::RSTRIDE;
+#pragma unroll 1
+        for (int r = 0; r < L::NRW; r++) {
+            const int fy = r < TH - 1 ? r : K + r - (TH - 1);
+            T v[L::CW0];
+#pragma unroll
+            for (int j = 0; j < L::CW0; j++) v[j] = rwt[fy * L::RS + ((TW - 1 + j) % TW) * L::G + (TW - 1 + j) / TW];
+            RSORT::template run<KO>(v);
+#pragma unroll
+            for (int j = 0; j < L::CW0; j++) rst[r * L::CW0 + j] = v[j];
+        }
+        __syncthreads();
+    }
+
     // 3. the tile's hierarchical network; each median goes straight to
     //    the store functor as the recursion reaches its leaf
     O1Store<K, TW, TH, BX, BY, DT, KO, ARG, IB> out{a, a.dst ? a.dst + (size_t)z * a.plane : nullptr,
                                                      a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)z * a.idx_plane : nullptr,
                                                      bx0, by0, tx, ty};
-    NET::template run<KO, L>(sm + L::CSB + ty * L::CSTY + tx, sm + ty * TH * L::RS + tx, out);
+    NET::template run<KO, L>(sm + L::CSB + ty * L::CSTY + tx, sm + ty * TH * L::RS + tx,
+                             sm + L::RSB + (ty * BX + tx) * L::RSTRIDE, out);
 }
 
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
-          class CSORT>
+          class CSORT, class RSORT>
 __global__ void __launch_bounds__(BX *BY) o1_kernel(ImgArgs a) {
-    o1_block<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+    o1_block<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT, RSORT>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // Persistent form for batches: each block repeatedly claims the next work
@@ -203,7 +234,7 @@ __global__ void __launch_bounds__(BX *BY) o1_kernel(ImgArgs a) {
 // list is exhausted.  Claims are atomic increments -- no block ever waits
 // on another.
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
-          class CSORT>
+          class CSORT, class RSORT>
 __global__ void __launch_bounds__(BX *BY) o1_persistent(const ImgArgs *imgs, const int4 *items, int n_items,
                                                         unsigned *counter) {
     __shared__ int s_item;
@@ -213,18 +244,18 @@ __global__ void __launch_bounds__(BX *BY) o1_persistent(const ImgArgs *imgs, con
         const int it = s_item;
         if (it >= n_items) break;
         const int4 w = items[it];
-        o1_block<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT>(imgs[w.x], w.y, w.z, w.w);
+        o1_block<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT, RSORT>(imgs[w.x], w.y, w.z, w.w);
         __syncthreads();  // shared memory is reused by the next item
     }
 }
 
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
-          class CSORT>
+          class CSORT, class RSORT>
 int persist_o1(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter, int blocks_per_sm,
                int sms, cudaStream_t s, int *grid_out) {
-    typedef O1Layout<K, TW, TH, BX, BY> L;
+    typedef O1Layout<K, TW, TH, BX, BY, NET::rows_smem> L;
     constexpr size_t smem = sizeof(typename KO::T) * (size_t)L::WORDS;
-    auto kern = o1_persistent<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT>;
+    auto kern = o1_persistent<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT, RSORT>;
     static bool configured = false;
     if (!configured) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -250,17 +281,26 @@ int persist_o1(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *co
 }
 
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
-          class CSORT>
+          class CSORT, class RSORT>
 int launch_o1(const ImgArgs &a, int channels, cudaStream_t s) {
-    typedef O1Layout<K, TW, TH, BX, BY> L;
+    typedef O1Layout<K, TW, TH, BX, BY, NET::rows_smem> L;
     constexpr int P = KO::lanes;
     constexpr size_t smem = sizeof(typename KO::T) * (size_t)L::WORDS;
-    auto kern = o1_kernel<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT>;
+    auto kern = o1_kernel<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT, RSORT>;
     static bool configured = false;  // per instantiation; benign race: idempotent
     if (!configured) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return MF_ERR_CUDA;
+        // ask for no more shared memory than the resident blocks use: the rest
+        // of the SM's 256 KB stays L1, where register spills of the large
+        // networks hit
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, BX * BY, smem) == cudaSuccess && occ > 0) {
+            const int pct = (int)((occ * (smem + 1024) * 100 + 228 * 1024 - 1) / (228 * 1024));
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
+        }
+        cudaGetLastError();
         configured = true;
     }
     dim3 grid((a.W + P * BX * TW - 1) / (P * BX * TW), (a.H + BY * TH - 1) / (BY * TH), channels);

@@ -44,6 +44,9 @@ int d1_geometry(int k, int dtype, bool arg, int *tile, int *strip, int *threads)
 int d1_persist(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter, int k, int dtype,
                int blocks_per_sm, int sms, cudaStream_t s, int *grid_out);
 
+// Argmedian from medians already in a.dst (mf_argmedian.cu).
+int launch_argmedian_from_values(const ImgArgs &a, int channels, int k, int dtype, cudaStream_t s);
+
 // Identity argmedian for k = 1 and small helpers (mf_api.cu).
 int launch_identity_idx(const ImgArgs &a, int channels, cudaStream_t s);
 

@@ -205,8 +205,11 @@ def keep_range(k, c, d, n_held):
     return max(0, m - d - u), min(n_held - 1, m - d)
 
 
-def build(k, tw, th=None):
-    """The full network for one root tile of tw x th pixels."""
+def build(k, tw, th=None, rows_smem=False):
+    """The full network for one root tile of tw x th pixels.  rows_smem:
+    the root's extra rows arrive already sorted as inputs ("row", fy, i)
+    (the kernel sorts them in a stage of its own) instead of being sorted
+    inside the network -- same work, fewer values live in registers."""
     th = tw if th is None else th
     assert k % 2 == 1 and k >= 1
     assert tw >= 1 and th >= 1 and tw & (tw - 1) == 0 and th & (th - 1) == 0
@@ -237,8 +240,12 @@ def build(k, tw, th=None):
     # extra columns: footprint columns outside the core, over the core rows
     cols = {fx: col_seg(fx) for fx in range(0, k + tw - 1) if not (cx0 <= fx <= cx1)}
     # extra rows: footprint rows outside the core rows, over the core columns
-    rows = {fy: net.sort([px(fy, fx) for fx in range(cx0, cx1 + 1)])
-            for fy in range(0, k + th - 1) if not (cy0 <= fy <= cy1)}
+    if rows_smem:
+        rows = {fy: [net.inp(("row", fy, i)) for i in range(cx1 - cx0 + 1)]
+                for fy in range(0, k + th - 1) if not (cy0 <= fy <= cy1)}
+    else:
+        rows = {fy: net.sort([px(fy, fx) for fx in range(cx0, cx1 + 1)])
+                for fy in range(0, k + th - 1) if not (cy0 <= fy <= cy1)}
 
     outputs = {}
 
@@ -378,13 +385,15 @@ def schedule(net, out_order):
     return out
 
 
-def evaluate(net, col_fn, px_fn):
-    """Run the network on the host.  col_fn(fx, i) and px_fn(fy, fx) return
-    numpy arrays (one entry per tile instance); returns the outputs."""
+def evaluate(net, col_fn, px_fn, row_fn=None):
+    """Run the network on the host.  col_fn(fx, i), px_fn(fy, fx) and
+    row_fn(fy, i) return numpy arrays (one entry per tile instance);
+    returns the outputs."""
     import numpy as np
     vals = [None] * (len(net.inputs) + len(net.ops))
     for i, desc in enumerate(net.inputs):
-        vals[i] = col_fn(desc[1], desc[2]) if desc[0] == "col" else px_fn(desc[1], desc[2])
+        f = {"col": col_fn, "px": px_fn, "row": row_fn}[desc[0]]
+        vals[i] = f(desc[1], desc[2])
     for kind, a, b, v in net.ops:
         vals[v] = np.minimum(vals[a], vals[b]) if kind == "min" else np.maximum(vals[a], vals[b])
     return [vals[v] for v in net.outputs]

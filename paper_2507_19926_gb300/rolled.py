@@ -141,7 +141,7 @@ def _sel_value(opnd, svals, vals, inputs_fn):
     return _sel_value(sub[key], svals, vals, inputs_fn)
 
 
-def interpret(net, ir, col_fn, px_fn):
+def interpret(net, ir, col_fn, px_fn, row_fn=None):
     """Runs the rolled IR on the host (numpy arrays, one entry per tile);
     returns the outputs in row-major pixel order."""
     import numpy as np
@@ -150,7 +150,7 @@ def interpret(net, ir, col_fn, px_fn):
 
     def inputs_fn(i):
         desc = net.inputs[i]
-        return col_fn(desc[1], desc[2]) if desc[0] == "col" else px_fn(desc[1], desc[2])
+        return {"col": col_fn, "px": px_fn, "row": row_fn}[desc[0]](desc[1], desc[2])
 
     def run(blk, svals):
         for st in blk:
@@ -182,9 +182,11 @@ def emit(net, ir, name, max_sel_levels=4, unroll_levels=0):
     n_in = len(net.inputs)
     w("struct %s {" % name)
     w("  static constexpr int n_ops = %d;" % len(net.ops))
+    w("  static constexpr bool rows_smem = %s;" % ("true" if any(d[0] == "row" for d in net.inputs) else "false"))
     w("  template <class KO, class L, class OUT>")
     w("  static __device__ __forceinline__ void run(const typename KO::T *__restrict__ cs,")
-    w("                                            const typename KO::T *__restrict__ rw, OUT &out) {")
+    w("                                            const typename KO::T *__restrict__ rw,")
+    w("                                            const typename KO::T *__restrict__ rs, OUT &out) {")
     w("    typedef typename KO::T T;")
     counter = [0]
 
@@ -192,6 +194,8 @@ def emit(net, ir, name, max_sel_levels=4, unroll_levels=0):
         desc = net.inputs[i]
         if desc[0] == "col":
             return "cs", "L::col(%d, %d)" % (desc[1], desc[2])
+        if desc[0] == "row":
+            return "rs", "L::row(%d, %d)" % (desc[1], desc[2])
         return "rw", "L::px(%d, %d)" % (desc[1], desc[2])
 
     def sel_expr(levels, sub, leaf):

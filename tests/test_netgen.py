@@ -90,7 +90,7 @@ def test_default_tile_heuristic():
         [1, 2, 2, 4, 4, 8, 8, 16, 16, 32, 32]
 
 
-def _run_hierarchy(img, k, tw, th, net):
+def _run_hierarchy(img, k, tw, th, net, rolled_ir=None):
     H, W = img.shape
     r = k // 2
     nty, ntx = -(-H // th), -(-W // tw)
@@ -105,9 +105,17 @@ def _run_hierarchy(img, k, tw, th, net):
             cache[fx] = np.sort(np.stack(rows), axis=0)
         return cache[fx]
 
-    outs = netgen.evaluate(net, lambda fx, i: colseg(fx)[i],
-                           lambda fy, fx: img[np.clip(TY * th - r + fy, 0, H - 1),
-                                              np.clip(TX * tw - r + fx, 0, W - 1)])
+    px_fn = lambda fy, fx: img[np.clip(TY * th - r + fy, 0, H - 1), np.clip(TX * tw - r + fx, 0, W - 1)]
+
+    def row_fn(fy, i):  # sorted extra row fy over the root core columns
+        seg = np.stack([px_fn(fy, fx) for fx in range(tw - 1, k)])
+        return np.sort(seg, axis=0)[i]
+
+    if rolled_ir is not None:
+        from paper_2507_19926_gb300 import rolled
+        outs = rolled.interpret(net, rolled_ir, lambda fx, i: colseg(fx)[i], px_fn, row_fn)
+    else:
+        outs = netgen.evaluate(net, lambda fx, i: colseg(fx)[i], px_fn, row_fn)
     res = np.zeros((nty * th, ntx * tw), img.dtype)
     for i, (py, px) in enumerate([(y, x) for y in range(th) for x in range(tw)]):
         res[TY * th + py, TX * tw + px] = outs[i]
@@ -133,3 +141,21 @@ def test_op_counts_grow_like_k_log_k():
         per_px = len(net.ops) / (t * t) + len(cs.ops) / t
         ratios.append(per_px / (k * np.log2(k)))
     assert max(ratios) / min(ratios) < 3.0
+
+
+@pytest.mark.parametrize("k,tw,th", [(5, 2, 2), (9, 4, 4), (13, 4, 4), (17, 4, 4), (9, 8, 2), (7, 2, 4)])
+@pytest.mark.parametrize("rows_smem", [False, True])
+def test_rolled_network_matches_oracle(k, tw, th, rows_smem):
+    """The loop-rolled form (one child per split, run for both children)
+    computes exactly what the straight-line network does."""
+    from paper_2507_19926_gb300 import rolled
+    net = netgen.build(k, tw, th, rows_smem=rows_smem)
+    ir, depth = rolled.build_ir(net)
+    assert depth == (tw * th).bit_length() - 1
+    for s in range(2):
+        img = (synth.levels16 if s else synth.uniform)((19, 22), "u16", 90 * k + s)
+        want = oracle.median_filter(img, k)
+        assert np.array_equal(_run_hierarchy(img, k, tw, th, net, ir), want)
+        assert np.array_equal(_run_hierarchy(img, k, tw, th, net), want)
+    src = rolled.emit(net, ir, "T")
+    assert src.count("KO::m") < len(net.ops) or len(net.ops) < 100
