@@ -103,10 +103,13 @@ int mf_median_filter_bwd(const float *grad_out, const int32_t *argidx, float *gr
 
 /* The same filter on HOST buffers: copies src (pitch bytes per row) to the
  * device, filters, copies the result back into dst (host) and waits for
- * completion.  Host buffers are caller-owned; page-locked memory makes the
- * copies asynchronous DMA.  Device staging memory is owned by the library:
- * one pair of buffers per process, grown on demand, shared by calls under a
- * lock and released by mf_shutdown(). */
+ * completion.  Planes are pipelined over three internal streams -- the
+ * upload of one plane overlaps the filtering and download of the others --
+ * after whatever is already queued on `stream`.  Host buffers are
+ * caller-owned; page-locked memory makes the copies asynchronous DMA.
+ * Device staging memory and the streams are owned by the library: one set
+ * per process, grown on demand, shared by calls under a lock and released
+ * by mf_shutdown(). */
 int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, size_t pitch,
                           int channels, mf_dtype dtype, int k, mf_border border,
                           mf_variant variant, mf_stream_t stream);

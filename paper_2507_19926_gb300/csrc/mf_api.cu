@@ -231,11 +231,16 @@ int mf_median_filter_tile(const void *src, void *dst, int H, int W, size_t pitch
     return d1_launch(a, channels, k, dtype, tile, (cudaStream_t)stream);
 }
 
-// Device staging buffers of the host entry point (one pair per process,
-// grown on demand, serialised by a mutex, released by mf_shutdown).
+// Device staging buffers and streams of the host entry point (one set per
+// process, grown on demand, serialised by a mutex, released by
+// mf_shutdown).  Planes are independent, so the copies of one plane overlap
+// the filtering of its neighbours: plane c is uploaded on stream c % 3 while
+// earlier planes are filtered and downloaded.
 static std::mutex g_stage_mu;
 static void *g_stage_src = nullptr, *g_stage_dst = nullptr;
 static size_t g_stage_bytes = 0;
+static cudaStream_t g_stage_streams[3] = {nullptr, nullptr, nullptr};
+static cudaEvent_t g_stage_events[3] = {nullptr, nullptr, nullptr};
 
 int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, size_t pitch,
                           int channels, mf_dtype dtype, int k, mf_border border,
@@ -246,7 +251,8 @@ int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, si
     if (H < 1 || W < 1 || channels < 1) { set_error("bad shape"); return MF_ERR_ARG; }
     if (pitch < (size_t)W * es || pitch % es) { set_error("bad pitch"); return MF_ERR_PITCH; }
     const size_t dpitch = ((size_t)W * es + 255) & ~(size_t)255;
-    const size_t bytes = (size_t)channels * H * dpitch;
+    const size_t plane = (size_t)H * dpitch;
+    const size_t bytes = (size_t)channels * plane;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_stage_mu);
     if (g_stage_bytes < bytes) {
@@ -262,17 +268,38 @@ int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, si
         }
         g_stage_bytes = bytes;
     }
-    cudaError_t e = cudaMemcpy2DAsync(g_stage_src, dpitch, src_host, pitch, (size_t)W * es,
-                                      (size_t)channels * H, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
-    int rc = mf_median_filter_ex(g_stage_src, g_stage_dst, H, W, dpitch, channels, dtype, k, border,
-                                 variant, nullptr, 0, stream);
-    if (rc) return rc;
-    e = cudaMemcpy2DAsync(dst_host, pitch, g_stage_dst, dpitch, (size_t)W * es, (size_t)channels * H,
-                          cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    if (!g_stage_streams[0]) {
+        for (int i = 0; i < 3; i++) {
+            if (cudaStreamCreateWithFlags(&g_stage_streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&g_stage_events[i], cudaEventDisableTiming) != cudaSuccess) {
+                set_error("cannot create staging streams: %s", cudaGetErrorString(cudaGetLastError()));
+                return MF_ERR_CUDA;
+            }
+        }
+    }
+    // the pipeline starts after work already queued on the caller's stream
+    cudaError_t e = cudaEventRecord(g_stage_events[0], s);
+    for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaStreamWaitEvent(g_stage_streams[i], g_stage_events[0], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline start");
+    const char *hs = (const char *)src_host;
+    char *hd = (char *)dst_host;
+    for (int c = 0; c < channels; c++) {
+        cudaStream_t sc = g_stage_streams[c % 3];
+        char *ds = (char *)g_stage_src + c * plane, *dd = (char *)g_stage_dst + c * plane;
+        e = cudaMemcpy2DAsync(ds, dpitch, hs + (size_t)c * H * pitch, pitch, (size_t)W * es, H,
+                              cudaMemcpyHostToDevice, sc);
+        if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
+        int rc = mf_median_filter_ex(ds, dd, H, W, dpitch, 1, dtype, k, border, variant, nullptr, 0,
+                                     (mf_stream_t)sc);
+        if (rc) return rc;
+        e = cudaMemcpy2DAsync(hd + (size_t)c * H * pitch, pitch, dd, dpitch, (size_t)W * es, H,
+                              cudaMemcpyDeviceToHost, sc);
+        if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+    }
+    for (int i = 0; i < 3; i++) {
+        e = cudaStreamSynchronize(g_stage_streams[i]);
+        if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    }
     return MF_OK;
 }
 
@@ -342,6 +369,12 @@ int mf_shutdown(void) {
     if (g_stage_dst) cudaFree(g_stage_dst);
     g_stage_src = g_stage_dst = nullptr;
     g_stage_bytes = 0;
+    for (int i = 0; i < 3; i++) {
+        if (g_stage_streams[i]) cudaStreamDestroy(g_stage_streams[i]);
+        if (g_stage_events[i]) cudaEventDestroy(g_stage_events[i]);
+        g_stage_streams[i] = nullptr;
+        g_stage_events[i] = nullptr;
+    }
     d1_release_all();
     return MF_OK;
 }

@@ -15,8 +15,10 @@ namespace mf {
 
 enum { D1_SORT = 0, D1_MERGE = 1 };
 
-// Longest list one thread sorts with a register network.
-constexpr int D1_MAX_SORT = 64;
+// Longest list one thread sorts with a register network (longer runs are
+// sorted in pieces and merged): keeps the kernel within 64 registers so a
+// block can run 1024 threads.
+constexpr int D1_MAX_SORT = 32;
 
 // One task.  Offsets and lengths are in list elements of shared memory.
 struct D1Task {

@@ -21,10 +21,10 @@
 
 namespace mf {
 
-constexpr int D1_NT_MAX = 512;
+constexpr int D1_NT_MAX = 1024;
 constexpr size_t D1_SMEM_BUDGET = 200 * 1024;
 // A strip whose state fits in this much shared memory runs with 256
-// threads, several blocks per SM; bigger ones run alone with 512 threads.
+// threads, several blocks per SM; bigger ones run alone with 1024 threads.
 constexpr size_t D1_SMEM_SMALL = 56 * 1024;
 
 struct D1Dev {
@@ -58,8 +58,7 @@ __device__ __forceinline__ void d1_sort_any(KT *sm, const D1Task &t) {
     else if (n <= 4) d1_sort_task<KT, 4>(sm, t);
     else if (NMAX <= 8 || n <= 8) d1_sort_task<KT, (NMAX < 8 ? NMAX : 8)>(sm, t);
     else if (NMAX <= 16 || n <= 16) d1_sort_task<KT, (NMAX < 16 ? NMAX : 16)>(sm, t);
-    else if (NMAX <= 32 || n <= 32) d1_sort_task<KT, (NMAX < 32 ? NMAX : 32)>(sm, t);
-    else d1_sort_task<KT, NMAX>(sm, t);
+    else d1_sort_task<KT, (NMAX < 32 ? NMAX : 32)>(sm, t);
 }
 
 // Element keys of the footprint: the order key (value mode) or the record
@@ -196,10 +195,18 @@ static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt) {
             return true;
         }
     }
-    const D1Plan *p = host_plan(k, T, 1, 512);
-    if (p && (size_t)p->smem_elems * kb <= D1_SMEM_BUDGET) {
+    // one tile per block: 512 threads when two blocks share an SM, else
+    // 1024 threads (32 warps) in a block of its own
+    const D1Plan *p5 = host_plan(k, T, 1, 512);
+    if (p5 && 2 * ((size_t)p5->smem_elems * kb + 1024) <= 227 * 1024) {
         *B = 1;
         *nt = 512;
+        return true;
+    }
+    const D1Plan *p = host_plan(k, T, 1, 1024);
+    if (p && (size_t)p->smem_elems * kb <= D1_SMEM_BUDGET) {
+        *B = 1;
+        *nt = 1024;
         return true;
     }
     return false;
@@ -300,8 +307,7 @@ static int d1_launch_t(const ImgArgs &a, int C, const D1Cached *c, int nt, cudaS
     const int ms = c->plan.max_sort;
     if (ms <= 8) return d1_launch_n<KT, DT, ARG, 8>(a, C, c, nt, s);
     if (ms <= 16) return d1_launch_n<KT, DT, ARG, 16>(a, C, c, nt, s);
-    if (ms <= 32) return d1_launch_n<KT, DT, ARG, 32>(a, C, c, nt, s);
-    return d1_launch_n<KT, DT, ARG, 64>(a, C, c, nt, s);
+    return d1_launch_n<KT, DT, ARG, 32>(a, C, c, nt, s);
 }
 
 int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s) {
@@ -366,8 +372,7 @@ static int d1_persist_t(const ImgArgs *imgs, const int4 *items, int n_items, uns
     const int ms = c->plan.max_sort;
     if (ms <= 8) return d1_persist_n<KT, DT, 8>(imgs, items, n_items, counter, c, nt, bps, sms, s, grid_out);
     if (ms <= 16) return d1_persist_n<KT, DT, 16>(imgs, items, n_items, counter, c, nt, bps, sms, s, grid_out);
-    if (ms <= 32) return d1_persist_n<KT, DT, 32>(imgs, items, n_items, counter, c, nt, bps, sms, s, grid_out);
-    return d1_persist_n<KT, DT, 64>(imgs, items, n_items, counter, c, nt, bps, sms, s, grid_out);
+    return d1_persist_n<KT, DT, 32>(imgs, items, n_items, counter, c, nt, bps, sms, s, grid_out);
 }
 
 int d1_geometry(int k, int dtype, bool arg, int *tile, int *strip, int *threads) {
