@@ -29,7 +29,9 @@
  * Errors: every entry point returns MF_OK (0) or a negative mf_status;
  * arguments are checked before anything is launched, no error terminates
  * the process, and mf_last_error() gives a one-line description of the
- * calling thread's last failure.
+ * calling thread's last failure.  For testing error paths, the environment
+ * variable MF_FAULT_INJECT=alloc makes every device allocation the library
+ * itself makes fail (entry points then return MF_ERR_ALLOC).
  */
 #ifndef MEDIANFILTER_H
 #define MEDIANFILTER_H

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -26,6 +27,15 @@ void set_error(const char *fmt, ...) {
 }
 
 void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+    const char *f = getenv("MF_FAULT_INJECT");
+    if (f && strcmp(f, "alloc") == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
 
 // The nth (0-based) instantiated configuration for (k, dtype, arg); the
 // first one is the default.
@@ -259,7 +269,7 @@ int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, si
         if (g_stage_src) { cudaFree(g_stage_src); cudaFree(g_stage_dst); }
         g_stage_src = g_stage_dst = nullptr;
         g_stage_bytes = 0;
-        if (cudaMalloc(&g_stage_src, bytes) != cudaSuccess || cudaMalloc(&g_stage_dst, bytes) != cudaSuccess) {
+        if (dev_alloc(&g_stage_src, bytes) != cudaSuccess || dev_alloc(&g_stage_dst, bytes) != cudaSuccess) {
             cudaGetLastError();
             if (g_stage_src) cudaFree(g_stage_src);
             g_stage_src = g_stage_dst = nullptr;

@@ -134,7 +134,7 @@ extern "C" int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_
     const size_t off_cnt = ((size_t)n * sizeof(ImgArgs) + 255) & ~(size_t)255;
     const size_t off_items = (off_cnt + nclass * sizeof(unsigned) + 255) & ~(size_t)255;
     const size_t total = off_items + nitems * sizeof(int4) + 16;
-    if (cudaMalloc(&p->dmem, total) != cudaSuccess) {
+    if (dev_alloc(&p->dmem, total) != cudaSuccess) {
         cudaGetLastError();
         set_error("cannot allocate %zu bytes for the batch plan", total);
         destroy_plan(p);

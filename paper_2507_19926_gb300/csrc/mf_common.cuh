@@ -106,4 +106,10 @@ struct ImgArgs {
 // Kernel launch counter (host side, see mf_kernel_launch_count).
 void count_launch(unsigned n = 1);
 
+// Every device allocation of the library goes through here.  Setting the
+// environment variable MF_FAULT_INJECT=alloc makes it fail (as an
+// out-of-memory device would), so the error paths can be exercised on the
+// host without touching the GPU.
+cudaError_t dev_alloc(void **p, size_t bytes);
+
 }  // namespace mf

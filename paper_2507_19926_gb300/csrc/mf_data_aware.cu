@@ -233,7 +233,7 @@ static D1Cached *get_plan(int k, int T, int B, int nt) {
     const size_t bt = packed.size() * sizeof(D1Packed), bw = pl.work.size() * 4,
                  bp = pl.phase_begin.size() * 4, bo = pl.out_off.size() * 4;
     const size_t total = bt + bw + bp + bo + 64;
-    if (cudaMalloc(&c->mem, total) != cudaSuccess) {
+    if (dev_alloc(&c->mem, total) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return nullptr;
@@ -320,8 +320,8 @@ int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s) 
     }
     const D1Cached *c = get_plan(k, T, B, nt);
     if (!c) {
-        set_error("cannot upload the data-aware plan for k=%d tile=%d", k, T);
-        return MF_ERR_CUDA;
+        set_error("cannot allocate or upload the data-aware plan for k=%d tile=%d", k, T);
+        return MF_ERR_ALLOC;
     }
     int rc;
     switch (dtype * 2 + (arg ? 1 : 0)) {
