@@ -187,7 +187,8 @@ int mf_describe(int H, int W, int channels, mf_dtype dtype, int k, mf_variant va
 /* Min/max throughput microbenchmark (the denominator of the data-oblivious
  * kernels' ALU roofline; no counterpart in the paper).  kind: 0 = u32,
  * 1 = packed u16x2, 2 = f32, 3 = packed f16x2, 4 = u16x2 min interleaved
- * with f16x2 max, 5 = u32 min interleaved with f32 max.  Runs `iters`
+ * with f16x2 max, 5 = u32 min interleaved with f32 max, 6 = three-input
+ * u16x2 min/max, 7 = three-input u32 min/max.  Runs `iters`
  * iterations of 16 min/max per thread on 4 blocks of 256 threads per SM of
  * the current device (the library allocates and frees its own 8 KB-scale
  * buffers) and writes instructions per second (one per thread-instruction)

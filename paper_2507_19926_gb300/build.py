@@ -62,6 +62,9 @@ DT_NAMES = {0: "MF_U8", 1: "MF_U16", 2: "MF_U32", 3: "MF_F32"}
 # roughly half the code per tree level.
 O1_ROLLED = os.environ.get("MF_O1_ROLLED", "1") == "1"
 
+# Fuse min(min(a, b), c) chains into three-input min/max (one instruction).
+O1_FUSE3 = os.environ.get("MF_O1_FUSE3", "1") == "1"
+
 # Barrier spacing (min/max ops) inside long per-thread networks.
 O1_SYNC_EVERY = int(os.environ.get("MF_O1_SYNC_EVERY", "0"))
 
@@ -112,6 +115,8 @@ def generate():
         sorts = sorted({k - th + 1 for (_, th) in nets} | {k - tw + 1 for (tw, _) in nets})
         for tw, th in nets:
             net = netgen.build(k, tw, th, rows_smem=bool(rsm))
+            if O1_FUSE3:
+                net = netgen.fuse3(net)
             sync = O1_SYNC_EVERY if O1_SYNC_EVERY and len(net.ops) > 4 * O1_SYNC_EVERY else 0
             u_eff = unroll if O1_ROLLED else -1
             src, _ = codegen.emit_network_auto(net, codegen.net_name(k, tw, th, u_eff, bool(rsm)), sync, u_eff)

@@ -37,7 +37,7 @@ def emit_network(net, name, sync_every=0):
     lines = []
     w = lines.append
     w("struct %s {" % name)
-    w("  static constexpr int n_ops = %d;" % len(net.ops))
+    w("  static constexpr int n_ops = %d;" % netgen.n_minmax(net))
     w("  static constexpr bool rows_smem = %s;" % ("true" if any(d[0] == "row" for d in net.inputs) else "false"))
     w("  template <class KO, class L, class OUT>")
     w("  static __device__ __forceinline__ void run(const typename KO::T *__restrict__ cs,")
@@ -59,9 +59,14 @@ def emit_network(net, name, sync_every=0):
             loaded[v] = True
         return "v%d" % v
 
+    third = getattr(net, "third", {})
     for n, (kind, a, b, v) in enumerate(net.ops):
         ra, rb = ref(a), ref(b)
-        w("    const T v%d = KO::%s(%s, %s);" % (v, "mn" if kind == "min" else "mx", ra, rb))
+        fn = "mn" if kind.startswith("min") else "mx"
+        if kind.endswith("3"):
+            w("    const T v%d = KO::%s3(%s, %s, %s);" % (v, fn, ra, rb, ref(third[v])))
+        else:
+            w("    const T v%d = KO::%s(%s, %s);" % (v, fn, ra, rb))
         if sync_every and n % sync_every == sync_every - 1:
             w("    __syncthreads();")
     for i, v in enumerate(net.outputs):

@@ -18,11 +18,15 @@ namespace mf {
 // One 32-bit register holds one u32 key, or two u16 keys (two tiles run the
 // same data-oblivious network side by side, paper Sec. 4.3 packing idea:
 // the network is independent of the data, so lanes never diverge).
+// mn3 / mx3: three-input forms, one instruction on sm_100+ (measured at the
+// two-input rate by mf_probe_minmax kinds 6 and 7).
 struct KoU32 {
     typedef uint32_t T;
     static constexpr int lanes = 1;
     static __device__ __forceinline__ T mn(T a, T b) { return umin(a, b); }
     static __device__ __forceinline__ T mx(T a, T b) { return umax(a, b); }
+    static __device__ __forceinline__ T mn3(T a, T b, T c) { return __vimin3_u32(a, b, c); }
+    static __device__ __forceinline__ T mx3(T a, T b, T c) { return __vimax3_u32(a, b, c); }
 };
 
 struct KoU16x2 {
@@ -38,6 +42,8 @@ struct KoU16x2 {
         asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
         return d;
     }
+    static __device__ __forceinline__ T mn3(T a, T b, T c) { return __vimin3_u16x2(a, b, c); }
+    static __device__ __forceinline__ T mx3(T a, T b, T c) { return __vimax3_u16x2(a, b, c); }
 };
 
 // 64-bit composite records (key << 32 | position) for argmedian of 32-bit data.
@@ -46,6 +52,8 @@ struct KoU64 {
     static constexpr int lanes = 1;
     static __device__ __forceinline__ T mn(T a, T b) { return a < b ? a : b; }
     static __device__ __forceinline__ T mx(T a, T b) { return a < b ? b : a; }
+    static __device__ __forceinline__ T mn3(T a, T b, T c) { return mn(mn(a, b), c); }
+    static __device__ __forceinline__ T mx3(T a, T b, T c) { return mx(mx(a, b), c); }
 };
 
 // ------------------------------------------------------------ dtype traits

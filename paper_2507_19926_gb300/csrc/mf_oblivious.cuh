@@ -47,7 +47,7 @@ struct O1Layout {
     static constexpr int NRW = 2 * (TH - 1);    // extra rows per root tile
     static constexpr int RSTRIDE = (NRW * CW0) | 1;
     static constexpr int RSB = CSB + BY * CSTY;
-    static constexpr int WORDS = RSB + (ROWS ? BX * BY * RSTRIDE : 0);
+    static constexpr int WORDS = (RSB + (ROWS ? BX * BY * RSTRIDE : 0) + 3) & ~3;
     static __host__ __device__ constexpr int at(int fy, int gx) {
         return fy * RS + (gx % TW) * G + gx / TW;
     }
@@ -73,14 +73,13 @@ struct O1Layout {
 template <int DT, class KO, bool ARG, int IB>
 struct O1Words;
 
+// row: the clamped source row; xl0 / xl1: the clamped columns of lanes 0 / 1.
 template <int DT, int IB>
 struct O1Words<DT, KoU16x2, false, IB> {
     template <class L>
-    static __device__ __forceinline__ uint32_t make(const char *src, const ImgArgs &a, int y,
-                                                    int xl0, int xl1, int, int) {
-        typedef typename Dt<DT>::E E;
-        uint32_t k0 = Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, xl0));
-        uint32_t k1 = Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, xl1));
+    static __device__ __forceinline__ uint32_t make(const typename Dt<DT>::E *row, int xl0, int xl1, int, int) {
+        const uint32_t k0 = Dt<DT>::key(__ldg(row + xl0));
+        const uint32_t k1 = Dt<DT>::key(__ldg(row + xl1));
         return k0 | (k1 << 16);
     }
 };
@@ -88,31 +87,25 @@ struct O1Words<DT, KoU16x2, false, IB> {
 template <int DT, int IB>
 struct O1Words<DT, KoU32, false, IB> {
     template <class L>
-    static __device__ __forceinline__ uint32_t make(const char *src, const ImgArgs &a, int y,
-                                                    int xl0, int, int, int) {
-        typedef typename Dt<DT>::E E;
-        return Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, xl0));
+    static __device__ __forceinline__ uint32_t make(const typename Dt<DT>::E *row, int xl0, int, int, int) {
+        return Dt<DT>::key(__ldg(row + xl0));
     }
 };
 
 template <int DT, int IB>
 struct O1Words<DT, KoU32, true, IB> {  // 8/16-bit argmedian: key << IB | index
     template <class L>
-    static __device__ __forceinline__ uint32_t make(const char *src, const ImgArgs &a, int y,
-                                                    int xl0, int, int fy, int gx) {
-        typedef typename Dt<DT>::E E;
-        return (Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, xl0)) << IB) | (uint32_t)(fy * L::FW + gx);
+    static __device__ __forceinline__ uint32_t make(const typename Dt<DT>::E *row, int xl0, int, int fy, int gx) {
+        return (Dt<DT>::key(__ldg(row + xl0)) << IB) | (uint32_t)(fy * L::FW + gx);
     }
 };
 
 template <int DT, int IB>
 struct O1Words<DT, KoU64, true, IB> {  // 32-bit argmedian: key << 32 | index
     template <class L>
-    static __device__ __forceinline__ unsigned long long make(const char *src, const ImgArgs &a,
-                                                              int y, int xl0, int, int fy, int gx) {
-        typedef typename Dt<DT>::E E;
-        return ((unsigned long long)Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, xl0)) << 32) |
-               (unsigned long long)(fy * L::FW + gx);
+    static __device__ __forceinline__ unsigned long long make(const typename Dt<DT>::E *row, int xl0, int, int fy,
+                                                              int gx) {
+        return ((unsigned long long)Dt<DT>::key(__ldg(row + xl0)) << 32) | (unsigned long long)(fy * L::FW + gx);
     }
 };
 
@@ -124,23 +117,30 @@ struct O1Store {
     typedef O1Layout<K, TW, TH, BX, BY> L;  // FW and R do not depend on ROWS
     typedef typename KO::T T;
     typedef typename Dt<DT>::E E;
+    static constexpr int OW = KO::lanes * BX * TW;  // output tile width (elements)
     const ImgArgs &a;
     char *dst;
     char *idx;
     int bx0, by0, tx, ty;
+    E *otile;  // value mode: the block's output tile in shared memory
     __device__ __forceinline__ void operator()(int pix, T w) const {
         constexpr int P = KO::lanes;
         const int py = pix / TW, px = pix - py * TW;
+        if (!ARG) {  // into the shared output tile; written out coalesced later
+#pragma unroll
+            for (int l = 0; l < P; l++) {
+                const uint32_t key = P == 2 ? (uint32_t)((w >> (16 * l)) & 0xffffu) : (uint32_t)w;
+                otile[(ty * TH + py) * OW + l * BX * TW + tx * TW + px] = Dt<DT>::val(key);
+            }
+            return;
+        }
         const int y = by0 + ty * TH + py;
         if (y >= a.H) return;
 #pragma unroll
         for (int l = 0; l < P; l++) {
             const int x = bx0 + l * BX * TW + tx * TW + px;
             if (x >= a.W) continue;
-            if (!ARG) {
-                const uint32_t key = P == 2 ? (uint32_t)((w >> (16 * l)) & 0xffffu) : (uint32_t)w;
-                if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
-            } else {
+            {
                 const uint32_t fidx = (uint32_t)(w & ((1ull << IB) - 1));
                 const uint32_t key = (uint32_t)(w >> IB);
                 const int fy = fidx / L::FW, gx = fidx - fy * L::FW;
@@ -171,13 +171,23 @@ __device__ __forceinline__ void o1_block(const ImgArgs &a, int bxi, int byi, int
     const int by0 = byi * (BY * TH);
     const char *src = a.src + (size_t)z * a.plane;
 
-    // 1. block footprint -> shared memory (clamp to edge)
-    for (int i = tid; i < L::FH * L::FW; i += NT) {
-        const int fy = i / L::FW, gx = i - fy * L::FW;
-        const int y = clampi(by0 - L::R + fy, 0, a.H - 1);
+    // 1. block footprint -> shared memory (clamp to edge): one work item is
+    //    one footprint column over a group of 4 rows, so the column's
+    //    clamps and shared-memory offset are computed once per 4 elements
+    constexpr int RG = 4, NRG = (L::FH + RG - 1) / RG;
+    for (int i = tid; i < L::FW * NRG; i += NT) {
+        const int g = i / L::FW, gx = i - g * L::FW;
         const int x0 = clampi(bx0 - L::R + gx, 0, a.W - 1);
         const int x1 = clampi(bx0 + BX * TW - L::R + gx, 0, a.W - 1);
-        sm[L::at(fy, gx)] = O1Words<DT, KO, ARG, IB>::template make<L>(src, a, y, x0, x1, fy, gx);
+        const int sw = (gx % TW) * L::G + gx / TW;
+#pragma unroll
+        for (int j = 0; j < RG; j++) {
+            const int fy = g * RG + j;
+            if (RG * NRG != L::FH && fy >= L::FH) break;
+            const int y = clampi(by0 - L::R + fy, 0, a.H - 1);
+            const E *row = reinterpret_cast<const E *>(src + (size_t)y * a.pitch);
+            sm[fy * L::RS + sw] = O1Words<DT, KO, ARG, IB>::template make<L>(row, x0, x1, fy, gx);
+        }
     }
     __syncthreads();
 
@@ -216,11 +226,38 @@ __device__ __forceinline__ void o1_block(const ImgArgs &a, int bxi, int byi, int
 
     // 3. the tile's hierarchical network; each median goes straight to
     //    the store functor as the recursion reaches its leaf
-    O1Store<K, TW, TH, BX, BY, DT, KO, ARG, IB> out{a, a.dst ? a.dst + (size_t)z * a.plane : nullptr,
-                                                     a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)z * a.idx_plane : nullptr,
-                                                     bx0, by0, tx, ty};
+    typedef O1Store<K, TW, TH, BX, BY, DT, KO, ARG, IB> Store;
+    E *otile = reinterpret_cast<E *>(sm + L::WORDS);
+    Store out{a, a.dst ? a.dst + (size_t)z * a.plane : nullptr,
+              a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)z * a.idx_plane : nullptr, bx0, by0, tx, ty, otile};
     NET::template run<KO, L>(sm + L::CSB + ty * L::CSTY + tx, sm + ty * TH * L::RS + tx,
                              sm + L::RSB + (ty * BX + tx) * L::RSTRIDE, out);
+
+    // 4. value mode: the output tile goes out as full 16-byte rows where the
+    //    block lies inside the image and the row start is aligned, else
+    //    element by element
+    if (!ARG && a.dst) {
+        __syncthreads();
+        constexpr int OW = Store::OW, OH = BY * TH;
+        constexpr int VEC = 16 / (int)sizeof(E);  // elements per 16-byte store
+        char *dst = a.dst + (size_t)z * a.plane;
+        const bool full = bx0 + OW <= a.W && ((a.pitch | (size_t)dst | ((size_t)bx0 * sizeof(E))) & 15) == 0;
+        if (full && OW % VEC == 0) {
+            for (int i = tid; i < OH * (OW / VEC); i += NT) {
+                const int r = i / (OW / VEC), c = i - r * (OW / VEC);
+                const int y = by0 + r;
+                if (y >= a.H) continue;
+                const uint4 v = reinterpret_cast<const uint4 *>(otile + r * OW)[c];
+                reinterpret_cast<uint4 *>(dst + (size_t)y * a.pitch + (size_t)bx0 * sizeof(E))[c] = v;
+            }
+        } else {
+            for (int i = tid; i < OH * OW; i += NT) {
+                const int r = i / OW, c = i - r * OW;
+                const int y = by0 + r, x = bx0 + c;
+                if (y < a.H && x < a.W) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = otile[i];
+            }
+        }
+    }
 }
 
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
@@ -249,12 +286,21 @@ __global__ void __launch_bounds__(BX *BY) o1_persistent(const ImgArgs *imgs, con
     }
 }
 
+// Shared memory of one block: the layout's words plus, in value mode, the
+// output tile (16-byte aligned: the layout's word count is rounded up).
+template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, class NET>
+constexpr size_t o1_smem_bytes() {
+    typedef O1Layout<K, TW, TH, BX, BY, NET::rows_smem> L;
+    return sizeof(typename KO::T) * (size_t)L::WORDS +
+           (ARG ? 0 : (size_t)KO::lanes * BX * TW * BY * TH * sizeof(typename Dt<DT>::E));
+}
+
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
           class CSORT, class RSORT>
 int persist_o1(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter, int blocks_per_sm,
                int sms, cudaStream_t s, int *grid_out) {
     typedef O1Layout<K, TW, TH, BX, BY, NET::rows_smem> L;
-    constexpr size_t smem = sizeof(typename KO::T) * (size_t)L::WORDS;
+    constexpr size_t smem = o1_smem_bytes<K, TW, TH, BX, BY, DT, KO, ARG, NET>();
     auto kern = o1_persistent<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT, RSORT>;
     static bool configured = false;
     if (!configured) {
@@ -283,9 +329,8 @@ int persist_o1(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *co
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
           class CSORT, class RSORT>
 int launch_o1(const ImgArgs &a, int channels, cudaStream_t s) {
-    typedef O1Layout<K, TW, TH, BX, BY, NET::rows_smem> L;
     constexpr int P = KO::lanes;
-    constexpr size_t smem = sizeof(typename KO::T) * (size_t)L::WORDS;
+    constexpr size_t smem = o1_smem_bytes<K, TW, TH, BX, BY, DT, KO, ARG, NET>();
     auto kern = o1_kernel<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT, RSORT>;
     static bool configured = false;  // per instantiation; benign race: idempotent
     if (!configured) {

@@ -31,6 +31,40 @@ __device__ __forceinline__ uint32_t pmax(uint32_t a, uint32_t b) {
     return d;
 }
 
+// three-input forms: one instruction each where the hardware has them
+template <int KIND>
+__device__ __forceinline__ uint32_t pmin3(uint32_t a, uint32_t b, uint32_t c) {
+    if (KIND == 6) return __vimin3_u16x2(a, b, c);
+    return __vimin3_u32(a, b, c);
+}
+template <int KIND>
+__device__ __forceinline__ uint32_t pmax3(uint32_t a, uint32_t b, uint32_t c) {
+    if (KIND == 6) return __vimax3_u16x2(a, b, c);
+    return __vimax3_u32(a, b, c);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) probe3_kernel(const uint32_t *in, uint32_t *out, int iters) {
+    uint32_t a[8], b[8];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        a[i] = in[(t * 16 + i) & 1023];
+        b[i] = in[(t * 16 + 8 + i) & 1023];
+    }
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            a[i] = pmin3<KIND>(a[i], b[i], a[(i + 3) & 7]);
+            b[i] = pmax3<KIND>(b[i], a[(i + 1) & 7], b[(i + 5) & 7]);
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) acc ^= a[i] ^ b[i];
+    out[t] = acc;
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256) probe_kernel(const uint32_t *in, uint32_t *out, int iters) {
     uint32_t a[8], b[8];
@@ -58,11 +92,12 @@ __global__ void __launch_bounds__(256) probe_kernel(const uint32_t *in, uint32_t
 using namespace mf;
 
 // kind: 0 u32 min/max, 1 u16x2 min/max, 2 f32 min/max, 3 f16x2 min/max,
-// 4 u16x2 min interleaved with f16x2 max, 5 u32 min interleaved with f32 max.
+// 4 u16x2 min interleaved with f16x2 max, 5 u32 min interleaved with f32 max,
+// 6 three-input u16x2 min/max, 7 three-input u32 min/max.
 // Writes min/max instructions per second (per warp-lane instruction) and
 // the elapsed milliseconds; buffers are allocated and freed here.
 extern "C" int mf_probe_minmax(int kind, int iters, double *instr_per_s, double *ms_out) {
-    if (kind < 0 || kind > 5 || iters < 1 || !instr_per_s) { set_error("bad probe arguments"); return MF_ERR_ARG; }
+    if (kind < 0 || kind > 7 || iters < 1 || !instr_per_s) { set_error("bad probe arguments"); return MF_ERR_ARG; }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -77,7 +112,8 @@ extern "C" int mf_probe_minmax(int kind, int iters, double *instr_per_s, double 
     cudaMemset(in, 0x5a, 1024 * 4);
     void (*kern)(const uint32_t *, uint32_t *, int) =
         kind == 0 ? probe_kernel<0> : kind == 1 ? probe_kernel<1> : kind == 2 ? probe_kernel<2>
-        : kind == 3 ? probe_kernel<3> : kind == 4 ? probe_kernel<4> : probe_kernel<5>;
+        : kind == 3 ? probe_kernel<3> : kind == 4 ? probe_kernel<4> : kind == 5 ? probe_kernel<5>
+        : kind == 6 ? probe3_kernel<6> : probe3_kernel<7>;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -63,6 +63,7 @@ class Network:
         self._kind.append(what)
 
     def __post_init__(self):
+        self.third = {}  # value id of a three-input op ("min3"/"max3") -> its third operand
         self._kind = []  # value id -> ("in", desc) | ("op", index)
         self.cur_path = ()   # tree path (child index per split) of ops being created
         self.op_path = {}    # value id -> tree path
@@ -385,17 +386,70 @@ def schedule(net, out_order):
     return out
 
 
+def fuse3(net):
+    """Fuses an op into its only user when both are the same kind:
+    v = min(min(a, b), c) becomes one three-input min3(a, b, c) (a single
+    instruction on sm_100+, at the two-input rate).  Runs on a pruned,
+    scheduled network; keeps ids, order and tree paths."""
+    uses = {}
+    for kind, a, b, v in net.ops:
+        uses[a] = uses.get(a, 0) + 1
+        uses[b] = uses.get(b, 0) + 1
+    for v in net.outputs:
+        uses[v] = uses.get(v, 0) + 1
+    kind_of = {v: kind for kind, a, b, v in net.ops}
+    src = {v: (a, b) for kind, a, b, v in net.ops}
+    path = net.op_path
+    absorbed, new_ops, third = set(), [], {}
+    for kind, a, b, v in net.ops:
+        if kind in ("min", "max"):
+            for x, y in ((a, b), (b, a)):
+                # same kind, used once, same tree path (keeps both children of
+                # every split structurally identical for loop rolling)
+                if (kind_of.get(x) == kind and uses.get(x) == 1 and x not in absorbed
+                        and x not in third and path.get(x) == path.get(v)):
+                    absorbed.add(x)
+                    xa, xb = src[x]
+                    kind, a, b = kind + "3", xa, xb
+                    third[v] = y
+                    break
+        new_ops.append((kind, a, b, v))
+    new_ops = [op for op in new_ops if op[3] not in absorbed]
+    live = {v for _, _, _, v in new_ops}
+    n_in = len(net.inputs)
+    for kind, a, b, v in new_ops:  # nothing may refer to an absorbed op
+        assert all(x < n_in or x in live for x in (a, b, third.get(v, a)))
+    out = Network(net.k, net.tw, net.th)
+    out.inputs = net.inputs
+    out.ops = new_ops
+    out.outputs = net.outputs
+    out._memo = net._memo
+    out.op_path = {v: p for v, p in net.op_path.items() if v in live}
+    out.leaf_pixel = net.leaf_pixel
+    out.third = third
+    return out
+
+
+def n_minmax(net):
+    """Element min/max operations of a network (a three-input op counts 2)."""
+    return sum(2 if kind.endswith("3") else 1 for kind, _, _, _ in net.ops)
+
+
 def evaluate(net, col_fn, px_fn, row_fn=None):
     """Run the network on the host.  col_fn(fx, i), px_fn(fy, fx) and
     row_fn(fy, i) return numpy arrays (one entry per tile instance);
     returns the outputs."""
     import numpy as np
-    vals = [None] * (len(net.inputs) + len(net.ops))
+    top = max([v for _, _, _, v in net.ops], default=-1) + 1
+    vals = [None] * max(top, len(net.inputs) + len(net.ops))
     for i, desc in enumerate(net.inputs):
         f = {"col": col_fn, "px": px_fn, "row": row_fn}[desc[0]]
         vals[i] = f(desc[1], desc[2])
     for kind, a, b, v in net.ops:
-        vals[v] = np.minimum(vals[a], vals[b]) if kind == "min" else np.maximum(vals[a], vals[b])
+        f = np.minimum if kind.startswith("min") else np.maximum
+        vals[v] = f(vals[a], vals[b])
+        if kind.endswith("3"):
+            vals[v] = f(vals[v], vals[net.third[v]])
     return [vals[v] for v in net.outputs]
 
 

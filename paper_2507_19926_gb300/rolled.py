@@ -34,7 +34,8 @@ def _depth(net, v):
 
 def build_ir(net):
     n_in = len(net.inputs)
-    ops = {v: (kind, a, b) for kind, a, b, v in net.ops}
+    third = getattr(net, "third", {})
+    ops = {v: (kind, a, b, third.get(v)) for kind, a, b, v in net.ops}
     sched = [v for _, _, _, v in net.ops]
     paths = net.op_path
     leaf_paths = sorted(net.leaf_pixel)
@@ -114,10 +115,11 @@ def build_ir(net):
         L = len(P)
         out = []
         for o in ops_at.get(P, []):
-            kind, a, b = ops[o]
+            kind = ops[o][0]
             oa = operand(lambda bits, pos=1: ops[cp(o, bits)][pos], L)
             ob = operand(lambda bits, pos=2: ops[cp(o, bits)][pos], L)
-            out.append(("op", o, kind, oa, ob))
+            oc = operand(lambda bits, pos=3: ops[cp(o, bits)][pos], L) if kind.endswith("3") else None
+            out.append(("op", o, kind, oa, ob, oc))
         if P in net.leaf_pixel:
             pix = {bits: ("const", net.leaf_pixel[bits]) for bits in itertools.product((0, 1), repeat=L)}
             val = operand(lambda bits: net.outputs[net.leaf_pixel[bits]], L)
@@ -126,7 +128,10 @@ def build_ir(net):
             out.append(("loop", L, block(P + (0,))))
         return out
 
-    ir = block(())
+    try:
+        ir = block(())
+    except KeyError as e:  # an operand outside the paired subtrees
+        raise RollError("unpaired operand %s" % e)
     return ir, D
 
 
@@ -155,10 +160,11 @@ def interpret(net, ir, col_fn, px_fn, row_fn=None):
     def run(blk, svals):
         for st in blk:
             if st[0] == "op":
-                _, v, kind, oa, ob = st
-                a = _sel_value(oa, svals, vals, inputs_fn)
-                b = _sel_value(ob, svals, vals, inputs_fn)
-                vals[v] = np.minimum(a, b) if kind == "min" else np.maximum(a, b)
+                _, v, kind, oa, ob, oc = st
+                f = np.minimum if kind.startswith("min") else np.maximum
+                vals[v] = f(_sel_value(oa, svals, vals, inputs_fn), _sel_value(ob, svals, vals, inputs_fn))
+                if oc is not None:
+                    vals[v] = f(vals[v], _sel_value(oc, svals, vals, inputs_fn))
             elif st[0] == "loop":
                 for s in (0, 1):
                     run(st[2], svals + [s])
@@ -181,7 +187,7 @@ def emit(net, ir, name, max_sel_levels=4, unroll_levels=0):
     w = lines.append
     n_in = len(net.inputs)
     w("struct %s {" % name)
-    w("  static constexpr int n_ops = %d;" % len(net.ops))
+    w("  static constexpr int n_ops = %d;" % sum(2 if op[0].endswith("3") else 1 for op in net.ops))
     w("  static constexpr bool rows_smem = %s;" % ("true" if any(d[0] == "row" for d in net.inputs) else "false"))
     w("  template <class KO, class L, class OUT>")
     w("  static __device__ __forceinline__ void run(const typename KO::T *__restrict__ cs,")
@@ -245,9 +251,11 @@ def emit(net, ir, name, max_sel_levels=4, unroll_levels=0):
 
         for st in blk:
             if st[0] == "op":
-                _, v, kind, oa, ob = st
+                _, v, kind, oa, ob, oc = st
                 ea, eb = opnd_expr(oa), opnd_expr(ob)
-                w("%sconst T v%d = KO::%s(%s, %s);" % (pad, v, "mn" if kind == "min" else "mx", ea, eb))
+                fn = ("mn" if kind.startswith("min") else "mx") + ("3" if oc is not None else "")
+                args = "%s, %s" % (ea, eb) if oc is None else "%s, %s, %s" % (ea, eb, opnd_expr(oc))
+                w("%sconst T v%d = KO::%s(%s);" % (pad, v, fn, args))
             elif st[0] == "loop":
                 lvl = st[1]
                 if lvl < unroll_levels:

@@ -145,11 +145,18 @@ def test_op_counts_grow_like_k_log_k():
 
 @pytest.mark.parametrize("k,tw,th", [(5, 2, 2), (9, 4, 4), (13, 4, 4), (17, 4, 4), (9, 8, 2), (7, 2, 4)])
 @pytest.mark.parametrize("rows_smem", [False, True])
-def test_rolled_network_matches_oracle(k, tw, th, rows_smem):
+@pytest.mark.parametrize("fuse", [False, True])
+def test_rolled_network_matches_oracle(k, tw, th, rows_smem, fuse):
     """The loop-rolled form (one child per split, run for both children)
-    computes exactly what the straight-line network does."""
+    computes exactly what the straight-line network does, with and without
+    three-input min/max fusion."""
     from paper_2507_19926_gb300 import rolled
     net = netgen.build(k, tw, th, rows_smem=rows_smem)
+    if fuse:
+        fused = netgen.fuse3(net)
+        assert netgen.n_minmax(fused) == netgen.n_minmax(net)
+        assert len(fused.ops) < len(net.ops) or len(net.ops) < 50
+        net = fused
     ir, depth = rolled.build_ir(net)
     assert depth == (tw * th).bit_length() - 1
     for s in range(2):
