@@ -39,7 +39,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # where the straight-line code no longer stays in the instruction cache).
 O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1)], 9: [(4, 4, 32, 4, -1)],
             11: [(4, 4, 32, 4, -1)], 13: [(4, 4, 32, 4, -1)], 15: [(4, 4, 32, 4, -1)],
-            17: [(4, 4, 32, 4, 0)], 19: [(4, 4, 32, 4, 0, 1)], 21: [(4, 4, 32, 4, 0)], 23: [(4, 4, 32, 4, 0)],
+            17: [(4, 4, 32, 4, 0)], 19: [(4, 4, 32, 4, 0, 1, 16), (4, 4, 32, 4, 0, 0, 32)], 21: [(4, 4, 32, 4, 0)], 23: [(4, 4, 32, 4, 0)],
             25: [(4, 4, 32, 4, 0)]}
 # extra configurations for timing (comma list "k:tw:th:bx:by:U[:R]" in
 # MF_O1_EXTRA); R = 1: the root extra rows are sorted into shared memory
@@ -47,7 +47,9 @@ O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1
 for _spec in filter(None, os.environ.get("MF_O1_EXTRA", "").split(",")):
     _v = [int(v) for v in _spec.split(":")]
     O1_VALUE.setdefault(_v[0], []).append(tuple((_v + [0, 0])[1:7]))
-O1_VALUE = {k: [tuple(c) + (0,) * (6 - len(c)) for c in v] for k, v in O1_VALUE.items()}
+# a 7th field restricts a configuration to 16-bit keys (u8/u16) or 32-bit
+# keys (u32/f32); 0 = both
+O1_VALUE = {k: [tuple(c) + (0,) * (7 - len(c)) for c in v] for k, v in O1_VALUE.items()}
 # argmedian with 32-bit records (8/16-bit data) and 64-bit records (32-bit data)
 O1_ARG32 = {k: v[0] for k, v in O1_VALUE.items()}
 # 32-bit data: the argmedian comes from the value kernel plus the recovery
@@ -73,15 +75,17 @@ def _o1_instances():
     """(k, tw, th, bx, by, dtype, ko, arg, ib) for every O1 kernel built."""
     out = []
     for k, cfgs in sorted(O1_VALUE.items()):
-        for (tw, th, bx, by, u, rs) in cfgs:
-            for dt in (0, 1):
-                out.append((k, tw, th, bx, by, (u, rs), dt, "KoU16x2", False, 0))
-            for dt in (2, 3):
-                out.append((k, tw, th, bx, by, (u, rs), dt, "KoU32", False, 0))
-    for k, (tw, th, bx, by, u, rs) in sorted(O1_ARG32.items()):
+        for (tw, th, bx, by, u, rs, keys) in cfgs:
+            if keys in (0, 16):
+                for dt in (0, 1):
+                    out.append((k, tw, th, bx, by, (u, rs), dt, "KoU16x2", False, 0))
+            if keys in (0, 32):
+                for dt in (2, 3):
+                    out.append((k, tw, th, bx, by, (u, rs), dt, "KoU32", False, 0))
+    for k, (tw, th, bx, by, u, rs, keys) in sorted(O1_ARG32.items()):
         out.append((k, tw, th, bx, by, (u, rs), 0, "KoU32", True, 24))
         out.append((k, tw, th, bx, by, (u, rs), 1, "KoU32", True, 16))
-    for k, (tw, th, bx, by, u, rs) in sorted(O1_ARG64.items()):
+    for k, (tw, th, bx, by, u, rs, keys) in sorted(O1_ARG64.items()):
         for dt in (2, 3):
             out.append((k, tw, th, bx, by, (u, rs), dt, "KoU64", True, 32))
     return out
@@ -102,7 +106,7 @@ def generate():
     entries = []
 
     def cfg_rank(key):  # each k's configurations in their listed order (default first)
-        cfgs = O1_VALUE.get(key[0], [])
+        cfgs = [c[:6] for c in O1_VALUE.get(key[0], [])]
         c = key[1:5] + key[5]
         return (key[0], cfgs.index(c) if c in cfgs else len(cfgs))
 

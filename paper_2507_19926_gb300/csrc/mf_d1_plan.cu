@@ -21,6 +21,7 @@
 // exchanges rows and columns.  Merges whose needed output ranks are known
 // only read the input ranks that can reach them.
 #include <algorithm>
+#include <cstdlib>
 #include <cstdio>
 #include <functional>
 #include <map>
@@ -30,6 +31,9 @@
 #include "mf_d1_plan.h"
 
 namespace mf {
+
+// Shortest merge chunk (outputs per work item; each chunk pays one binary search).
+static const int D1_MIN_CHUNK = getenv("MF_D1_MIN_CHUNK") ? atoi(getenv("MF_D1_MIN_CHUNK")) : 4;
 
 namespace {
 
@@ -370,8 +374,9 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt) {
         long long outs_p = 0;
         for (int ti : by_phase[p])
             if (B.tasks[ti].type == D1_MERGE) outs_p += B.tasks[ti].hi - B.tasks[ti].lo + 1;
-        // about two chunks per thread, each 16..32 outputs long
-        int chunk = (int)std::min<long long>(32, std::max<long long>(16, outs_p / (2 * nt)));
+        // about one chunk per thread: phases with few outputs (the upper tree
+        // levels) get short chunks so the whole block shares them
+        int chunk = (int)std::min<long long>(32, std::max<long long>(D1_MIN_CHUNK, outs_p / nt));
         // sorts first, grouped by size class, then merges
         std::vector<int> order = by_phase[p];
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
