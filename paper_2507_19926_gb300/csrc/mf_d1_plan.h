@@ -50,7 +50,7 @@ struct D1Plan {
 // (T a power of two, 2 <= T <= min(k, 32); B >= 1), chunking merges for
 // blocks of nt threads.  The strip's footprint columns are sorted once and
 // shared by its tiles (paper Sec. 3.3).  Returns false outside that range.
-bool d1_build_plan(int k, int T, D1Plan *plan, int B = 1, int nt = 256);
+bool d1_build_plan(int k, int T, D1Plan *plan, int B = 1, int nt = 256, int key_bytes = 4);
 
 struct D1Packed;
 // The 16-byte device form of every task (layout in mf_d1_ops.cuh).

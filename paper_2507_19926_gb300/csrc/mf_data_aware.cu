@@ -155,10 +155,10 @@ struct D1Cached {
 };
 
 static std::mutex g_d1_mu;
-typedef std::tuple<int, int, int, int> PlanKey;  // k, T, B, nt
+typedef std::tuple<int, int, int, int, int> PlanKey;  // k, T, B, nt, key bytes
 static std::map<PlanKey, D1Plan *> *g_plans = new std::map<PlanKey, D1Plan *>();
-static std::map<std::tuple<int, int, int, int, int>, D1Cached *> *g_d1 =
-    new std::map<std::tuple<int, int, int, int, int>, D1Cached *>();
+static std::map<std::tuple<int, int, int, int, int, int>, D1Cached *> *g_d1 =
+    new std::map<std::tuple<int, int, int, int, int, int>, D1Cached *>();
 
 static size_t key_bytes(int dtype, bool arg) {
     const bool wide = dtype == MF_U32 || dtype == MF_F32;
@@ -167,13 +167,13 @@ static size_t key_bytes(int dtype, bool arg) {
 }
 
 // Host plan; nullptr if none exists.  No device work.
-static const D1Plan *host_plan(int k, int T, int B, int nt) {
+static const D1Plan *host_plan(int k, int T, int B, int nt, int kb) {
     std::lock_guard<std::mutex> lk(g_d1_mu);
-    const PlanKey key(k, T, B, nt);
+    const PlanKey key(k, T, B, nt, kb);
     auto it = g_plans->find(key);
     if (it != g_plans->end()) return it->second;
     D1Plan *pl = new D1Plan();
-    if (!d1_build_plan(k, T, pl, B, nt)) {
+    if (!d1_build_plan(k, T, pl, B, nt, kb)) {
         delete pl;
         pl = nullptr;
     }
@@ -186,9 +186,9 @@ static const D1Plan *host_plan(int k, int T, int B, int nt) {
 // and several blocks per SM; otherwise one tile with 512 threads.
 static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt) {
     if (k < 3 || k > 75 || !(k & 1) || T < 2 || T > 32 || (T & (T - 1)) || T > k) return false;
-    const size_t kb = key_bytes(dtype, arg);
+    const int kb = (int)key_bytes(dtype, arg);
     for (int b = 8; b >= 1; b /= 2) {
-        const D1Plan *p = host_plan(k, T, b, 256);
+        const D1Plan *p = host_plan(k, T, b, 256, kb);
         if (p && (size_t)p->smem_elems * kb <= D1_SMEM_SMALL) {
             *B = b;
             *nt = 256;
@@ -197,13 +197,13 @@ static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt) {
     }
     // one tile per block: 512 threads when two blocks share an SM, else
     // 1024 threads (32 warps) in a block of its own
-    const D1Plan *p5 = host_plan(k, T, 1, 512);
+    const D1Plan *p5 = host_plan(k, T, 1, 512, kb);
     if (p5 && 2 * ((size_t)p5->smem_elems * kb + 1024) <= 227 * 1024) {
         *B = 1;
         *nt = 512;
         return true;
     }
-    const D1Plan *p = host_plan(k, T, 1, 1024);
+    const D1Plan *p = host_plan(k, T, 1, 1024, kb);
     if (p && (size_t)p->smem_elems * kb <= D1_SMEM_BUDGET) {
         *B = 1;
         *nt = 1024;
@@ -213,8 +213,8 @@ static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt) {
 }
 
 // Plan uploaded to the current device (once per device).
-static D1Cached *get_plan(int k, int T, int B, int nt) {
-    const D1Plan *hp = host_plan(k, T, B, nt);
+static D1Cached *get_plan(int k, int T, int B, int nt, int kb) {
+    const D1Plan *hp = host_plan(k, T, B, nt, kb);
     if (!hp) return nullptr;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -222,7 +222,7 @@ static D1Cached *get_plan(int k, int T, int B, int nt) {
         return nullptr;
     }
     std::lock_guard<std::mutex> lk(g_d1_mu);
-    auto key = std::make_tuple(k, T, B, nt, dev);
+    auto key = std::make_tuple(k, T, B, nt, kb, dev);
     auto it = g_d1->find(key);
     if (it != g_d1->end()) return it->second;
     D1Cached *c = new D1Cached();
@@ -318,7 +318,7 @@ int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s) 
         set_error("no data-aware plan for k=%d tile=%d", k, T);
         return MF_ERR_UNSUPPORTED;
     }
-    const D1Cached *c = get_plan(k, T, B, nt);
+    const D1Cached *c = get_plan(k, T, B, nt, (int)key_bytes(dtype, arg));
     if (!c) {
         set_error("cannot allocate or upload the data-aware plan for k=%d tile=%d", k, T);
         return MF_ERR_ALLOC;
@@ -391,7 +391,7 @@ int d1_persist(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *co
     if (d1_geometry(k, dtype, false, &T, &B, &nt)) return MF_ERR_UNSUPPORTED;
     // the plan upload (synchronous copies) happens in the prepare call,
     // before any stream capture
-    const D1Cached *c = get_plan(k, T, B, nt);
+    const D1Cached *c = get_plan(k, T, B, nt, (int)key_bytes(dtype, false));
     if (!c) return MF_ERR_CUDA;
     const int b = blocks_per_sm;
     switch (dtype) {
@@ -405,7 +405,7 @@ int d1_persist(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *co
 
 int d1_describe(int k, int dtype, bool arg, int T, char *buf, size_t n) {
     int B = 0, nt = 0;
-    const D1Plan *p = T && choose_config(k, dtype, arg, T, &B, &nt) ? host_plan(k, T, B, nt) : nullptr;
+    const D1Plan *p = T && choose_config(k, dtype, arg, T, &B, &nt) ? host_plan(k, T, B, nt, (int)key_bytes(dtype, arg)) : nullptr;
     if (!p) {
         snprintf(buf, n, "data-aware k=%d (no plan)", k);
         return MF_OK;
