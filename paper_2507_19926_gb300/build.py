@@ -37,13 +37,17 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # Measured on GB300 (4096^2 u8/u32): straight-line is fastest up to k = 15,
 # the fully rolled tree at k = 17 (13-15% faster than straight-line there,
 # where the straight-line code no longer stays in the instruction cache).
-O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1)], 9: [(4, 4, 32, 4, -1)],
-            11: [(4, 4, 32, 4, -1)], 13: [(4, 4, 32, 4, -1)], 15: [(4, 4, 32, 4, -1)],
-            17: [(4, 4, 32, 4, 0)], 19: [(4, 4, 32, 4, 0, 1, 16), (4, 4, 32, 4, 0, 0, 32)], 21: [(4, 4, 32, 4, 0)], 23: [(4, 4, 32, 4, 0)],
-            25: [(4, 4, 32, 4, 0)]}
-# extra configurations for timing (comma list "k:tw:th:bx:by:U[:R]" in
-# MF_O1_EXTRA); R = 1: the root extra rows are sorted into shared memory
-# by a stage of their own (netgen.build rows_smem)
+# Form 6 (lazy extra rows/columns, pressure-aware order) removes the
+# register spills at k = 13 and most of them at k = 17 (1432 -> 252 spilled
+# bytes a thread): k = 17 u8 0.459 -> 0.387 ms, u32 0.850 -> 0.770 ms.
+O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1, 6)], 9: [(4, 4, 32, 4, -1, 6)],
+            11: [(4, 4, 32, 4, -1, 6)], 13: [(4, 4, 32, 4, -1, 6)], 15: [(4, 4, 32, 4, -1, 6)],
+            17: [(4, 4, 32, 4, 0, 6)], 19: [(4, 4, 32, 4, 0, 6), (4, 4, 32, 4, 0, 7, 16)],
+            21: [(4, 4, 32, 4, 0, 6)], 23: [(4, 4, 32, 4, 0, 6)], 25: [(4, 4, 32, 4, 0, 6), (4, 4, 32, 4, 0, 0)]}
+# extra configurations for timing (comma list "k:tw:th:bx:by:U[:R[:keys]]"
+# in MF_O1_EXTRA).  R is the network form, a bit set: 1 = the root extra
+# rows are sorted into shared memory by a stage of their own (netgen.build
+# rows_smem), 2 = lazy extra rows/columns, 4 = pressure-aware op order.
 for _spec in filter(None, os.environ.get("MF_O1_EXTRA", "").split(",")):
     _v = [int(v) for v in _spec.split(":")]
     O1_VALUE.setdefault(_v[0], []).append(tuple((_v + [0, 0])[1:7]))
@@ -117,23 +121,25 @@ def generate():
         unroll, rsm = key[5]
         nets = sorted({(i[1], i[2]) for i in lst})
         sorts = sorted({k - th + 1 for (_, th) in nets} | {k - tw + 1 for (tw, _) in nets})
+        n_ops = {}
         for tw, th in nets:
-            net = netgen.build(k, tw, th, rows_smem=bool(rsm))
+            net = netgen.build(k, tw, th, rows_smem=bool(rsm & 1), lazy=bool(rsm & 2), pressure=bool(rsm & 4))
+            n_ops[(tw, th)] = netgen.n_minmax(net)
             if O1_FUSE3:
                 net = netgen.fuse3(net)
             sync = O1_SYNC_EVERY if O1_SYNC_EVERY and len(net.ops) > 4 * O1_SYNC_EVERY else 0
             u_eff = unroll if O1_ROLLED else -1
-            src, _ = codegen.emit_network_auto(net, codegen.net_name(k, tw, th, u_eff, bool(rsm)), sync, u_eff)
+            src, _ = codegen.emit_network_auto(net, codegen.net_name(k, tw, th, u_eff, rsm), sync, u_eff)
             parts.append(src)
         for n in sorts:
             parts.append(codegen.emit_colsort(n))
         for (k_, tw, th, bx, by, (u, rsm), dt, ko, arg, ib) in lst:
             fn = "o1_launch_k%d_%dx%d_b%dx%d_u%s%s_%s_%s%s" % (k, tw, th, bx, by, "m1" if u < 0 else u,
-                                                            "_rs" if rsm else "", DT_NAMES[dt], ko,
+                                                            codegen.form_suffix(rsm), DT_NAMES[dt], ko,
                                                             "_arg" if arg else "")
             targs = "%d, %d, %d, %d, %d, %s, %s, %s, %d, %s, %s, %s" % (
                 k, tw, th, bx, by, DT_NAMES[dt], ko, "true" if arg else "false", ib,
-                codegen.net_name(k, tw, th, u if O1_ROLLED else -1, bool(rsm)), codegen.sort_name(k - th + 1),
+                codegen.net_name(k, tw, th, u if O1_ROLLED else -1, rsm), codegen.sort_name(k - th + 1),
                 codegen.sort_name(k - tw + 1))
             parts.append("int %s(const ImgArgs &a, int c, cudaStream_t s) {\n"
                          "  return launch_o1<%s>(a, c, s);\n}" % (fn, targs))
@@ -148,10 +154,10 @@ def generate():
             decls.append("int %s(const ImgArgs &a, int c, cudaStream_t s);" % fn)
             entries.append("  {%d, %s, %d, %d, %d, %d, %d, %d, %s, %s, \"%s\"}," %
                            (k, DT_NAMES[dt], 1 if arg else 0, tw, th, bx, by,
-                            netgen.build(k, tw, th).ops.__len__(), fn, pfn, fn))
+                            n_ops[(tw, th)], fn, pfn, fn))
         parts.append("}  // namespace mf")
         path = os.path.join(GEN, "o1_k%d_%dx%d_b%dx%d_u%s%s_%s%s_%s.cu" % (
-            key[:5] + ("m1" if key[5][0] < 0 else key[5][0], "_rs" if key[5][1] else "", key[6],
+            key[:5] + ("m1" if key[5][0] < 0 else key[5][0], codegen.form_suffix(key[5][1]), key[6],
                        "_arg" if key[7] else "", DT_NAMES[key[8]])))
         codegen.write_if_changed(path, "\n".join(parts) + "\n")
         tus.append(path)

@@ -16,13 +16,19 @@ import os
 from . import netgen
 
 
-def net_name(k, tw, th, unroll=None, rows_smem=False):
+def form_suffix(form):
+    """Name suffix of a network form (bit 0: root rows from shared memory,
+    bit 1: lazy extra rows/columns, bit 2: pressure-aware order)."""
+    return ("_rs" if form & 1 else "") + ("_lz" if form & 2 else "") + ("_pr" if form & 4 else "")
+
+
+def net_name(k, tw, th, unroll=None, form=0):
     """Struct name of one generated network; distinct per emission form so
     that no two translation units define the same kernel differently."""
     base = "Net_k%d_%dx%d" % (k, tw, th)
     if unroll is None:
         return base
-    return base + ("_flat" if unroll < 0 else "_u%d" % unroll) + ("_rs" if rows_smem else "")
+    return base + ("_flat" if unroll < 0 else "_u%d" % unroll) + form_suffix(form)
 
 
 def sort_name(n):

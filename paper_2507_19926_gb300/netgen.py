@@ -206,11 +206,19 @@ def keep_range(k, c, d, n_held):
     return max(0, m - d - u), min(n_held - 1, m - d)
 
 
-def build(k, tw, th=None, rows_smem=False):
+def build(k, tw, th=None, rows_smem=False, lazy=False, pressure=False):
     """The full network for one root tile of tw x th pixels.  rows_smem:
     the root's extra rows arrive already sorted as inputs ("row", fy, i)
     (the kernel sorts them in a stage of its own) instead of being sorted
-    inside the network -- same work, fewer values live in registers."""
+    inside the network -- same work, fewer values live in registers.
+
+    lazy: an extra row (column) of a node is carried as a list of runs --
+    the sorted parent row plus the groups of corner pixels that the splits
+    added -- and the runs are merged only by the child whose core takes the
+    row in (paper Sec. 3.4: each extra row or column joins the core of
+    exactly one descendant on every path).  The same lists are merged, in a
+    different tree; the merged copies are never held across a sibling's
+    subtree, which keeps far fewer values live."""
     th = tw if th is None else th
     assert k % 2 == 1 and k >= 1
     assert tw >= 1 and th >= 1 and tw & (tw - 1) == 0 and th & (th - 1) == 0
@@ -247,6 +255,19 @@ def build(k, tw, th=None, rows_smem=False):
     else:
         rows = {fy: net.sort([px(fy, fx) for fx in range(cx0, cx1 + 1)])
                 for fy in range(0, k + th - 1) if not (cy0 <= fy <= cy1)}
+    if lazy:
+        # runs: ("list", sorted ids) or ("px", [(fy, fx), ...]) still unsorted
+        rows = {fy: [("list", r)] for fy, r in rows.items()}
+        cols = {fx: [("list", c)] for fx, c in cols.items()}
+
+    def runs_sorted(runs):
+        return [r[1] if r[0] == "list" else net.sort([px(fy, fx) for fy, fx in r[1]]) for r in runs]
+
+    def consume(lines):
+        # sorted union of extra rows (or columns): eager lists or lazy runs
+        if not lazy:
+            return net.multiway_range(lines, 0, 10**9)
+        return net.multiway_range([l for runs in lines for l in runs_sorted(runs)], 0, 10**9)
 
     outputs = {}
 
@@ -264,7 +285,7 @@ def build(k, tw, th=None, rows_smem=False):
                 ncx0, ncx1 = cx + h - 1, cx + k - 1
                 new = [fx for fx in range(ncx0, ncx1 + 1) if not (cx0 <= fx <= cx1)]
                 c = (ncx1 - ncx0 + 1) * (cy1 - cy0 + 1)
-                extra = net.multiway_range([cols[fx] for fx in new], 0, 10**9)
+                extra = consume([cols[fx] for fx in new])
                 lo, hi = keep_range(k, c, d, len(core) + len(extra))
                 ncore = net.merge_range(core, extra, lo, hi)
                 # extra columns of the child: its footprint columns outside its core
@@ -274,8 +295,11 @@ def build(k, tw, th=None, rows_smem=False):
                 nrows = {}
                 for fy, r in rows.items():
                     if y0 <= fy <= y0 + th_ + k - 2:
-                        corners = net.sort([px(fy, fx) for fx in new])
-                        nrows[fy] = net.merge(r, corners)
+                        if lazy:
+                            nrows[fy] = r + [("px", [(fy, fx) for fx in new])]
+                        else:
+                            corners = net.sort([px(fy, fx) for fx in new])
+                            nrows[fy] = net.merge(r, corners)
                 recurse(cx, y0, h, th_, ncore, d + lo, ncols, nrows, path + (si,))
                 net.cur_path = path
         else:  # vertical split: halve the height
@@ -285,7 +309,7 @@ def build(k, tw, th=None, rows_smem=False):
                 ncy0, ncy1 = cy + h - 1, cy + k - 1
                 new = [fy for fy in range(ncy0, ncy1 + 1) if not (cy0 <= fy <= cy1)]
                 c = (cx1 - cx0 + 1) * (ncy1 - ncy0 + 1)
-                extra = net.multiway_range([rows[fy] for fy in new], 0, 10**9)
+                extra = consume([rows[fy] for fy in new])
                 lo, hi = keep_range(k, c, d, len(core) + len(extra))
                 ncore = net.merge_range(core, extra, lo, hi)
                 nrows = {fy: rows[fy] for fy in range(cy, cy + h + k - 1)
@@ -293,13 +317,18 @@ def build(k, tw, th=None, rows_smem=False):
                 ncols = {}
                 for fx, cl in cols.items():
                     if x0 <= fx <= x0 + tw_ + k - 2:
-                        corners = net.sort([px(fy, fx) for fy in new])
-                        ncols[fx] = net.merge(cl, corners)
+                        if lazy:
+                            ncols[fx] = cl + [("px", [(fy, fx) for fy in new])]
+                        else:
+                            corners = net.sort([px(fy, fx) for fy in new])
+                            ncols[fx] = net.merge(cl, corners)
                 recurse(x0, cy, tw_, h, ncore, d + lo, ncols, nrows, path + (si,))
                 net.cur_path = path
 
     recurse(0, 0, tw, th, core, d, cols, rows)
     net.outputs = [outputs[(y, x)] for y in range(th) for x in range(tw)]
+    if pressure:
+        return schedule_pressure(prune(net), leaf_order(tw, th))
     return schedule(prune(net), leaf_order(tw, th))
 
 
@@ -383,6 +412,84 @@ def schedule(net, out_order):
     out._memo = net._memo
     out.op_path = net.op_path
     out.leaf_pixel = net.leaf_pixel
+    return out
+
+
+def schedule_pressure(net, out_order):
+    """Register-pressure-aware order.  Blocks follow the execution order of
+    the split tree (a node's own ops, then its first child's subtree, then
+    the second's -- the order a rolled kernel runs them in); inside a block
+    a greedy list scheduler takes the ready op that ends the most live
+    ranges (operands at their last use) and breaks ties by the
+    demand-driven order of ``schedule``.  Same ops, fewer values live at
+    once: the large networks then need fewer spill slots."""
+    base = schedule(net, out_order)
+    n_in = len(net.inputs)
+    pos = {op[3]: i for i, op in enumerate(base.ops)}
+    op_of = {op[3]: op for op in base.ops}
+    remaining = {}
+    for kind, a, b, v in base.ops:
+        for x in {a, b}:
+            if x >= n_in:
+                remaining[x] = remaining.get(x, 0) + 1
+    for v in base.outputs:
+        if v >= n_in:
+            remaining[v] = remaining.get(v, 0) + 1
+    by_path = {}
+    for kind, a, b, v in base.ops:
+        by_path.setdefault(base.op_path[v], []).append(v)
+    leaf_out = {}
+    for P, pix in base.leaf_pixel.items():
+        leaf_out.setdefault(P, []).append(base.outputs[pix])
+    paths = set(by_path) | set(base.leaf_pixel)
+    order = []
+    done = set(range(n_in))
+
+    def run_block(P):
+        todo = set(by_path.get(P, ()))
+        users = {}
+        for v in todo:
+            _, a, b, _ = op_of[v]
+            for x in {a, b}:
+                if x in todo:
+                    users.setdefault(x, []).append(v)
+        waiting = {v: sum(1 for x in {op_of[v][1], op_of[v][2]} if x in todo) for v in todo}
+        ready = [v for v in todo if waiting[v] == 0]
+        while ready:
+            best, best_key = None, None
+            for v in ready:
+                _, a, b, _ = op_of[v]
+                freed = sum(1 for x in {a, b} if x >= n_in and remaining[x] == 1)
+                key = (-freed, pos[v])
+                if best_key is None or key < best_key:
+                    best, best_key = v, key
+            ready.remove(best)
+            order.append(op_of[best])
+            done.add(best)
+            _, a, b, _ = op_of[best]
+            for x in {a, b}:
+                if x >= n_in:
+                    remaining[x] -= 1
+            for u in users.get(best, ()):
+                waiting[u] -= 1
+                if waiting[u] == 0:
+                    ready.append(u)
+        for v in leaf_out.get(P, ()):
+            if v >= n_in:
+                remaining[v] -= 1
+        for c in (0, 1):
+            if any(q[:len(P) + 1] == P + (c,) for q in paths):
+                run_block(P + (c,))
+
+    run_block(())
+    assert len(order) == len(base.ops)
+    out = Network(net.k, net.tw, net.th)
+    out.inputs = base.inputs
+    out.ops = order
+    out.outputs = base.outputs
+    out._memo = base._memo
+    out.op_path = base.op_path
+    out.leaf_pixel = base.leaf_pixel
     return out
 
 

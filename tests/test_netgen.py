@@ -144,14 +144,15 @@ def test_op_counts_grow_like_k_log_k():
 
 
 @pytest.mark.parametrize("k,tw,th", [(5, 2, 2), (9, 4, 4), (13, 4, 4), (17, 4, 4), (9, 8, 2), (7, 2, 4)])
-@pytest.mark.parametrize("rows_smem", [False, True])
+@pytest.mark.parametrize("form", [0, 1, 6, 7])
 @pytest.mark.parametrize("fuse", [False, True])
-def test_rolled_network_matches_oracle(k, tw, th, rows_smem, fuse):
+def test_rolled_network_matches_oracle(k, tw, th, form, fuse):
     """The loop-rolled form (one child per split, run for both children)
     computes exactly what the straight-line network does, with and without
-    three-input min/max fusion."""
+    three-input min/max fusion, in every network form (root rows from
+    shared memory, lazy extra rows/columns, pressure-aware order)."""
     from paper_2507_19926_gb300 import rolled
-    net = netgen.build(k, tw, th, rows_smem=rows_smem)
+    net = netgen.build(k, tw, th, rows_smem=bool(form & 1), lazy=bool(form & 2), pressure=bool(form & 4))
     if fuse:
         fused = netgen.fuse3(net)
         assert netgen.n_minmax(fused) == netgen.n_minmax(net)
@@ -166,3 +167,32 @@ def test_rolled_network_matches_oracle(k, tw, th, rows_smem, fuse):
         assert np.array_equal(_run_hierarchy(img, k, tw, th, net), want)
     src = rolled.emit(net, ir, "T")
     assert src.count("KO::m") < len(net.ops) or len(net.ops) < 100
+
+
+@pytest.mark.parametrize("k,tw,th", [(9, 4, 4), (13, 4, 4), (17, 4, 4)])
+def test_pressure_order_is_a_permutation_with_lower_peak(k, tw, th):
+    """The pressure-aware order runs the same ops (a topological permutation
+    of them) and never holds more values live than the demand-driven order
+    when both carry the extra rows lazily."""
+    a = netgen.build(k, tw, th, lazy=True)
+    b = netgen.build(k, tw, th, lazy=True, pressure=True)
+    assert sorted(a.ops, key=lambda o: o[3]) == sorted(b.ops, key=lambda o: o[3])
+    n_in = len(b.inputs)
+    seen = set(range(n_in))
+    for kind, x, y, v in b.ops:
+        assert x in seen and y in seen
+        seen.add(v)
+
+    def peak(net):
+        last = {}
+        for i, (_, x, y, _) in enumerate(net.ops):
+            last[x] = last[y] = i
+        for v in net.outputs:
+            last[v] = len(net.ops)
+        live = best = 0
+        for i, (_, x, y, v) in enumerate(net.ops):
+            live += 1
+            best = max(best, live)
+            live -= sum(1 for u in {x, y} if u >= n_in and last[u] == i)
+        return best
+    assert peak(b) <= peak(a)
