@@ -91,6 +91,15 @@ int mf_median_filter_ex(const void *src, void *dst, int H, int W, size_t pitch, 
 int mf_median_filter_tile(const void *src, void *dst, int H, int W, size_t pitch, int channels,
                           mf_dtype dtype, int k, int tile, mf_stream_t stream);
 
+/* The data-oblivious variant (Sec. 4) with the config-th instantiated
+ * network configuration for (k, dtype) (0 = the default; the others are the
+ * autotuner's candidates: other network forms, tiles or key widths, all
+ * computing the same filter).  Arguments and errors as mf_median_filter;
+ * MF_ERR_UNSUPPORTED when config is negative or past the last one, so
+ * callers can enumerate them. */
+int mf_median_filter_config(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                            mf_dtype dtype, int k, int config, mf_stream_t stream);
+
 /* Gradient of the filter with respect to its f32 input: grad_in[p] = sum
  * of grad_out[q] over the outputs q whose argmedian is p (the median is the
  * identity on its selected input).  All pointers are caller-owned device

@@ -18,6 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmedianfilter.so")
 
 MF_U8, MF_U16, MF_U32, MF_F32 = 0, 1, 2, 3
+DTYPE_CODES = {"u8": MF_U8, "u16": MF_U16, "u32": MF_U32, "f32": MF_F32}
+MF_ERR_UNSUPPORTED = -9
 MF_BORDER_CLAMP = 0
 MF_AUTO, MF_OBLIVIOUS, MF_DATA_AWARE = 0, 1, 2
 MF_GRAD_ATOMIC, MF_GRAD_DETERMINISTIC = 0, 1
@@ -25,7 +27,8 @@ VARIANTS = {"auto": MF_AUTO, "oblivious": MF_OBLIVIOUS, "data_aware": MF_DATA_AW
 GRAD_MODES = {"atomic": MF_GRAD_ATOMIC, "deterministic": MF_GRAD_DETERMINISTIC}
 
 # C symbols declared in include/medianfilter.h
-EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_tile", "mf_median_filter_bwd",
+EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_tile", "mf_median_filter_config",
+           "mf_median_filter_bwd",
            "mf_median_filter_host", "mf_batch_plan_create", "mf_batch_run",
            "mf_batch_plan_destroy", "mf_batch_describe", "mf_batch_run_static", "mf_autotune", "mf_describe", "mf_kernel_launch_count",
            "mf_status_string", "mf_last_error", "mf_version", "mf_shutdown", "mf_probe_minmax",
@@ -33,7 +36,8 @@ EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_tile", "
 
 
 class MedianFilterError(RuntimeError):
-    pass
+    """A non-zero mf_status; .status holds the code."""
+    status = 0
 
 
 class ImageDesc(ctypes.Structure):
@@ -61,6 +65,7 @@ def load_library(path=LIB_PATH):
         lib.mf_median_filter.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp]
         lib.mf_median_filter_ex.argtypes = [vp, vp, i, i, sz, i, i, i, i, i, vp, sz, vp]
         lib.mf_median_filter_tile.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp]
+        lib.mf_median_filter_config.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp]
         lib.mf_median_filter_bwd.argtypes = [vp, vp, vp, i, i, sz, sz, i, i, i, vp]
         lib.mf_median_filter_host.argtypes = [vp, vp, i, i, sz, i, i, i, i, i, vp]
         lib.mf_batch_plan_create.argtypes = [ctypes.POINTER(ImageDesc), i, ctypes.POINTER(vp)]
@@ -87,8 +92,10 @@ def load_library(path=LIB_PATH):
 def _check(rc):
     if rc != 0:
         lib = load_library()
-        raise MedianFilterError("%s: %s" % (lib.mf_status_string(rc).decode(),
+        err = MedianFilterError("%s: %s" % (lib.mf_status_string(rc).decode(),
                                             lib.mf_last_error().decode()))
+        err.status = rc
+        raise err
     return rc
 
 
@@ -106,6 +113,11 @@ def mf_median_filter_ex(src, dst, H, W, pitch, channels, dtype, k, border, varia
 def mf_median_filter_tile(src, dst, H, W, pitch, channels, dtype, k, tile, stream=None):
     return _check(load_library().mf_median_filter_tile(src, dst, H, W, pitch, channels, dtype, k, tile,
                                                        stream))
+
+
+def mf_median_filter_config(src, dst, H, W, pitch, channels, dtype, k, config, stream=None):
+    return _check(load_library().mf_median_filter_config(src, dst, H, W, pitch, channels, dtype, k, config,
+                                                         stream))
 
 
 def mf_median_filter_bwd(grad_out, argidx, grad_in, H, W, pitch, idx_pitch, channels, k, mode,

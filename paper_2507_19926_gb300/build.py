@@ -39,11 +39,16 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # where the straight-line code no longer stays in the instruction cache).
 # Form 6 (lazy extra rows/columns, pressure-aware order) removes the
 # register spills at k = 13 and most of them at k = 17 (1432 -> 252 spilled
-# bytes a thread): k = 17 u8 0.459 -> 0.387 ms, u32 0.850 -> 0.770 ms.
-O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1, 6)], 9: [(4, 4, 32, 4, -1, 6)],
-            11: [(4, 4, 32, 4, -1, 6)], 13: [(4, 4, 32, 4, -1, 6)], 15: [(4, 4, 32, 4, -1, 6)],
-            17: [(4, 4, 32, 4, 0, 6)], 19: [(4, 4, 32, 4, 0, 6), (4, 4, 32, 4, 0, 7, 16)],
-            21: [(4, 4, 32, 4, 0, 6)], 23: [(4, 4, 32, 4, 0, 6)], 25: [(4, 4, 32, 4, 0, 6), (4, 4, 32, 4, 0, 0)]}
+# bytes a thread): k = 17 u8 0.459 -> 0.387 ms, u32 0.850 -> 0.770 ms;
+# u32 k = 25 4.51 -> 2.64 ms.  The straight-line networks up to k = 15 gain
+# nothing from it (within 1-5%, either way) except u8 k = 9 (0.127 -> 0.117
+# ms); u8 k = 25 loses (3.18 -> 5.49 ms) and keeps form 0.
+O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1)],
+            9: [(4, 4, 32, 4, -1, 6, 16), (4, 4, 32, 4, -1, 0, 32)],
+            11: [(4, 4, 32, 4, -1)], 13: [(4, 4, 32, 4, -1)], 15: [(4, 4, 32, 4, -1)],
+            17: [(4, 4, 32, 4, 0, 6)], 19: [(4, 4, 32, 4, 0, 7, 16), (4, 4, 32, 4, 0, 6, 32)],
+            21: [(4, 4, 32, 4, 0, 6)], 23: [(4, 4, 32, 4, 0, 6), (4, 4, 32, 4, 0, 6, 1)],
+            25: [(4, 4, 32, 4, 0, 0, 16), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 0, 6, 1)]}
 # extra configurations for timing (comma list "k:tw:th:bx:by:U[:R[:keys]]"
 # in MF_O1_EXTRA).  R is the network form, a bit set: 1 = the root extra
 # rows are sorted into shared memory by a stage of their own (netgen.build
@@ -51,8 +56,9 @@ O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1
 for _spec in filter(None, os.environ.get("MF_O1_EXTRA", "").split(",")):
     _v = [int(v) for v in _spec.split(":")]
     O1_VALUE.setdefault(_v[0], []).append(tuple((_v + [0, 0])[1:7]))
-# a 7th field restricts a configuration to 16-bit keys (u8/u16) or 32-bit
-# keys (u32/f32); 0 = both
+# a 7th field restricts a configuration to 16-bit keys (u8/u16, two tiles a
+# thread) or 32-bit keys (u32/f32); 0 = both; 1 = u8/u16 data with 32-bit
+# keys (one tile a thread: half the values in flight of the packed form)
 O1_VALUE = {k: [tuple(c) + (0,) * (7 - len(c)) for c in v] for k, v in O1_VALUE.items()}
 # argmedian with 32-bit records (8/16-bit data) and 64-bit records (32-bit data)
 O1_ARG32 = {k: v[0] for k, v in O1_VALUE.items()}
@@ -79,19 +85,22 @@ def _o1_instances():
     """(k, tw, th, bx, by, dtype, ko, arg, ib) for every O1 kernel built."""
     out = []
     for k, cfgs in sorted(O1_VALUE.items()):
-        for (tw, th, bx, by, u, rs, keys) in cfgs:
+        for ci, (tw, th, bx, by, u, rs, keys) in enumerate(cfgs):
             if keys in (0, 16):
                 for dt in (0, 1):
-                    out.append((k, tw, th, bx, by, (u, rs), dt, "KoU16x2", False, 0))
+                    out.append((k, tw, th, bx, by, (u, rs), dt, "KoU16x2", False, 0, ci))
             if keys in (0, 32):
                 for dt in (2, 3):
-                    out.append((k, tw, th, bx, by, (u, rs), dt, "KoU32", False, 0))
+                    out.append((k, tw, th, bx, by, (u, rs), dt, "KoU32", False, 0, ci))
+            if keys == 1:
+                for dt in (0, 1):
+                    out.append((k, tw, th, bx, by, (u, rs), dt, "KoU32", False, 0, ci))
     for k, (tw, th, bx, by, u, rs, keys) in sorted(O1_ARG32.items()):
-        out.append((k, tw, th, bx, by, (u, rs), 0, "KoU32", True, 24))
-        out.append((k, tw, th, bx, by, (u, rs), 1, "KoU32", True, 16))
+        out.append((k, tw, th, bx, by, (u, rs), 0, "KoU32", True, 24, 0))
+        out.append((k, tw, th, bx, by, (u, rs), 1, "KoU32", True, 16, 0))
     for k, (tw, th, bx, by, u, rs, keys) in sorted(O1_ARG64.items()):
         for dt in (2, 3):
-            out.append((k, tw, th, bx, by, (u, rs), dt, "KoU64", True, 32))
+            out.append((k, tw, th, bx, by, (u, rs), dt, "KoU64", True, 32, 0))
     return out
 
 
@@ -109,12 +118,8 @@ def generate():
     decls = []
     entries = []
 
-    def cfg_rank(key):  # each k's configurations in their listed order (default first)
-        cfgs = [c[:6] for c in O1_VALUE.get(key[0], [])]
-        c = key[1:5] + key[5]
-        return (key[0], cfgs.index(c) if c in cfgs else len(cfgs))
-
-    for key, lst in sorted(by_k.items(), key=lambda kv: cfg_rank(kv[0])):
+    # each k's configurations in their listed order (default first)
+    for key, lst in sorted(by_k.items(), key=lambda kv: (kv[0][0], min(i[10] for i in kv[1]))):
         k = key[0]
         parts = ['// generated by codegen/build.py -- do not edit', '#include "mf_oblivious.cuh"',
                  "namespace mf {"]
@@ -133,7 +138,7 @@ def generate():
             parts.append(src)
         for n in sorts:
             parts.append(codegen.emit_colsort(n))
-        for (k_, tw, th, bx, by, (u, rsm), dt, ko, arg, ib) in lst:
+        for (k_, tw, th, bx, by, (u, rsm), dt, ko, arg, ib, _) in lst:
             fn = "o1_launch_k%d_%dx%d_b%dx%d_u%s%s_%s_%s%s" % (k, tw, th, bx, by, "m1" if u < 0 else u,
                                                             codegen.form_suffix(rsm), DT_NAMES[dt], ko,
                                                             "_arg" if arg else "")
@@ -152,8 +157,8 @@ def generate():
                 decls.append("int %s(const ImgArgs *i, const int4 *w, int n, unsigned *q, int b, int sms, "
                              "cudaStream_t s, int *g);" % pfn)
             decls.append("int %s(const ImgArgs &a, int c, cudaStream_t s);" % fn)
-            entries.append("  {%d, %s, %d, %d, %d, %d, %d, %d, %s, %s, \"%s\"}," %
-                           (k, DT_NAMES[dt], 1 if arg else 0, tw, th, bx, by,
+            entries.append("  {%d, %s, %d, %d, %d, %d, %d, %d, %d, %s, %s, \"%s\"}," %
+                           (k, DT_NAMES[dt], 1 if arg else 0, tw, th, bx, by, 2 if ko == "KoU16x2" else 1,
                             n_ops[(tw, th)], fn, pfn, fn))
         parts.append("}  // namespace mf")
         path = os.path.join(GEN, "o1_k%d_%dx%d_b%dx%d_u%s%s_%s%s_%s.cu" % (

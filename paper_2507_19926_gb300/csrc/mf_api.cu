@@ -241,6 +241,30 @@ int mf_median_filter_tile(const void *src, void *dst, int H, int W, size_t pitch
     return d1_launch(a, channels, k, dtype, tile, (cudaStream_t)stream);
 }
 
+int mf_median_filter_config(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                            mf_dtype dtype, int k, int config, mf_stream_t stream) {
+    int rc = check_fwd(src, dst, H, W, pitch, channels, dtype, k, MF_BORDER_CLAMP, nullptr, 0);
+    if (rc) return rc;
+    if (!dst) { set_error("null dst"); return MF_ERR_ARG; }
+    const O1Entry *o1 = config >= 0 && k > 1 ? find_o1_nth(k, dtype, false, config) : nullptr;
+    if (!o1) {
+        set_error("no data-oblivious configuration %d for k=%d dtype=%d", config, k, (int)dtype);
+        return MF_ERR_UNSUPPORTED;
+    }
+    ImgArgs a;
+    a.src = (const char *)src;
+    a.dst = (char *)dst;
+    a.idx = nullptr;
+    a.H = H;
+    a.W = W;
+    a.pitch = pitch;
+    a.plane = (size_t)H * pitch;
+    a.idx_pitch = a.idx_plane = 0;
+    rc = o1->launch(a, channels, (cudaStream_t)stream);
+    if (rc == MF_ERR_CUDA) set_error("%s: %s", o1->name, cudaGetErrorString(cudaGetLastError()));
+    return rc;
+}
+
 // Device staging buffers and streams of the host entry point (one set per
 // process, grown on demand, serialised by a mutex, released by
 // mf_shutdown).  Planes are independent, so the copies of one plane overlap

@@ -111,7 +111,7 @@ extern "C" int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_
             c.k = d.k;
             c.dtype = d.dtype;
             if (var == MF_OBLIVIOUS) {
-                const int lanes = (d.dtype == MF_U8 || d.dtype == MF_U16) ? 2 : 1;
+                const int lanes = o1->lanes;
                 c.rw = lanes * o1->bx * o1->tw;
                 c.rh = o1->by * o1->th;
             } else {

@@ -16,6 +16,7 @@ struct O1Entry {
     int arg;        // 1: argmedian (composite records)
     int tw, th;     // root tile
     int bx, by;     // threads per block (x, y)
+    int lanes;      // root tiles a thread (2: two 16-bit keys a register)
     int net_ops;    // min/max ops of one root tile's network (excl. column sort)
     ImgLaunchFn launch;
     PersistFn persist;

@@ -92,3 +92,32 @@ def test_photo_rgb_k17_sampled_rows():
                       list(g.integers(0, H, size=24))))
     want = oracle.median_filter_rows(x, 17, rows)
     assert np.array_equal(got[:, rows], want)
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("k", KS)
+def test_every_configuration(dt, k):
+    """Every instantiated network configuration of (k, dtype) -- the
+    autotuner's candidates: network forms, key widths -- against the oracle
+    through mf_median_filter_config, until the entry reports no more."""
+    import torch
+    import paper_2507_19926_gb300 as mf
+    from gpu_util import ensure_lib, to_dev, to_host
+    ensure_lib()
+    x = synth.levels16((2, 45, 290), dt, 3000 + k)
+    want = oracle.median_filter(x, k)
+    xd = to_dev(x)
+    n = 0
+    for config in range(16):
+        yd = torch.empty_like(xd)
+        _, H, W, pitch = mf._planes(xd)
+        try:
+            mf.mf_median_filter_config(xd.data_ptr(), yd.data_ptr(), H, W, pitch, 2, mf.DTYPE_CODES[dt], k, config,
+                                       torch.cuda.current_stream().cuda_stream)
+        except mf.MedianFilterError as e:
+            assert e.status == mf.MF_ERR_UNSUPPORTED and config > 0, e
+            break
+        torch.cuda.synchronize()
+        assert same_bits(to_host(yd, None), want), (dt, k, config)
+        n += 1
+    assert n >= 1
