@@ -164,9 +164,10 @@ int mf_batch_describe(const mf_batch_plan *plan, int *kernels, long long *items)
  * data-oblivious kernels, taking its work queues from one fixed array of
  * 2 MiB that the library's module holds on every device where it is used,
  * until the library is unloaded.  Limits: at most 256 images, k = 1 or an
- * odd k from 3 to 17, and at most 126,976 work items (one item is one
+ * odd k from 3 to 25, and at most 126,976 work items (one item is one
  * block of pixels: 128 x 8 for k = 3, 5 and 8/16-bit data, 64 x 8 for 32-bit
- * data, 256 x 16 / 128 x 16 for larger k); beyond them it returns MF_ERR_ARG
+ * data, 256 x 16 for larger k with 8/16-bit data up to k = 21, else
+ * 128 x 16); beyond them it returns MF_ERR_ARG
  * or MF_ERR_UNSUPPORTED with a message, before touching the device.
  * Nothing is allocated (no cudaMalloc, cudaFree or allocating library
  * call): the image table and work records are copied from the stack, the

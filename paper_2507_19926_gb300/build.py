@@ -42,13 +42,16 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # bytes a thread): k = 17 u8 0.459 -> 0.387 ms, u32 0.850 -> 0.770 ms;
 # u32 k = 25 4.51 -> 2.64 ms.  The straight-line networks up to k = 15 gain
 # nothing from it (within 1-5%, either way) except u8 k = 9 (0.127 -> 0.117
-# ms); u8 k = 25 loses (3.18 -> 5.49 ms) and keeps form 0.
+# ms).  At k = 23, 25 the packed two-tiles-a-thread form spills too much:
+# 8/16-bit data runs one tile a thread on 32-bit keys there (u8 k = 23
+# 2.53 -> 1.87 ms, k = 25 3.11 -> 2.82 ms).
 O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1)],
             9: [(4, 4, 32, 4, -1, 6, 16), (4, 4, 32, 4, -1, 0, 32)],
             11: [(4, 4, 32, 4, -1)], 13: [(4, 4, 32, 4, -1)], 15: [(4, 4, 32, 4, -1)],
             17: [(4, 4, 32, 4, 0, 6)], 19: [(4, 4, 32, 4, 0, 7, 16), (4, 4, 32, 4, 0, 6, 32)],
-            21: [(4, 4, 32, 4, 0, 6)], 23: [(4, 4, 32, 4, 0, 6), (4, 4, 32, 4, 0, 6, 1)],
-            25: [(4, 4, 32, 4, 0, 0, 16), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 0, 6, 1)]}
+            21: [(4, 4, 32, 4, 0, 6)],
+            23: [(4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 0, 6, 16)],
+            25: [(4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 0, 0, 16)]}
 # extra configurations for timing (comma list "k:tw:th:bx:by:U[:R[:keys]]"
 # in MF_O1_EXTRA).  R is the network form, a bit set: 1 = the root extra
 # rows are sorted into shared memory by a stage of their own (netgen.build

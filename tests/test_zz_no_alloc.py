@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 CODES = {"u8": mf.MF_U8, "u16": mf.MF_U16, "u32": mf.MF_U32, "f32": mf.MF_F32}
 SPECS = [(1, 300, 200, "u8", 3), (2, 90, 130, "u16", 5), (1, 64, 256, "f32", 7), (3, 41, 77, "u8", 9),
          (1, 120, 90, "u32", 11), (1, 70, 333, "u16", 13), (1, 33, 40, "f32", 15), (1, 200, 150, "u8", 17),
-         (2, 25, 60, "u8", 1), (1, 515, 700, "u8", 5)]
+         (2, 25, 60, "u8", 1), (1, 515, 700, "u8", 5), (2, 70, 290, "u8", 23), (1, 40, 150, "u16", 21)]
 
 
 def _images(seed):
