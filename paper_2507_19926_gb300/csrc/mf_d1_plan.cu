@@ -37,6 +37,8 @@ namespace mf {
 // min, 32).  Measured on 4096^2 images, k = 27..75: 2-byte keys do best with
 // (min 16, div 2), wider keys with (min 12, div 1).  MF_D1_CHUNK="min:div"
 // overrides both (tuning sweeps).
+static const bool D1_ODD_CHUNKS = !getenv("MF_D1_EVEN_CHUNKS");
+
 static void chunk_rule(int key_bytes, int *min_chunk, int *div) {
     *min_chunk = key_bytes <= 2 ? 16 : 12;
     *div = key_bytes <= 2 ? 2 : 1;
@@ -392,6 +394,10 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes) {
         // about one chunk per thread: phases with few outputs (the upper tree
         // levels) get short chunks so the whole block shares them
         int chunk = (int)std::min<long long>(32, std::max<long long>(min_chunk, outs_p / ((long long)div * nt)));
+        // the chunks of one merge run on consecutive threads: an odd number of
+        // 4-byte words between their output runs spreads a warp's stores
+        // (and its roughly proportional input reads) over all 32 banks
+        if (D1_ODD_CHUNKS) chunk = key_bytes == 2 ? (chunk & ~3) + 2 : (chunk | 1);
         // sorts first, grouped by size class, then merges
         std::vector<int> order = by_phase[p];
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
