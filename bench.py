@@ -432,6 +432,22 @@ def run_ours(args):
                          "peak = %d SMs x %d min/max instr/clk/SM x %.0f MHz x %d lanes "
                          "(probe: %.1f instr/clk/SM at %.0f MHz)" % (
                              ops_px, px_per_step, sms, ipc_nominal, max_mhz, lanes, ipc, probe_mhz)}
+    elif "data-aware" in plan:
+        # shared-memory merging: every merged or sorted element is read once
+        # and written once at the least; peak = 128 B/clk/SM of shared memory
+        import re
+        m = re.search(r"merged/px=([\d.]+) sorted/px=([\d.]+)", plan)
+        if m:
+            kb = 2 if dt in ("u8", "u16") else 4
+            elems_px = float(m.group(1)) + float(m.group(2))
+            max_mhz = peaks.get("sm_max_mhz", 2070.0)
+            peak = sms * 128 * max_mhz * 1e6 / 1e9  # GB/s
+            achieved = elems_px * 2 * kb * px_per_step / (ms_per_step * 1e-3) / 1e9
+            roof = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "basis": "(%.1f merged + %.1f sorted) elements per pixel x 2 accesses x %d B x %d px; "
+                             "peak = %d SMs x 128 B/clk x %.0f MHz" % (
+                                 float(m.group(1)), float(m.group(2)), kb, px_per_step, sms, max_mhz)}
     bytes_per_step = 2 * px_per_step * x.element_size()
     extra["hbm"] = {"achieved_gbs": bytes_per_step / (ms_per_step * 1e-3) / 1e9,
                     "peak_gbs": peaks.get("hbm_gbs"),
