@@ -71,10 +71,8 @@ __host__ __device__ __forceinline__ void d1_merge_chunk(KT *sm, const D1Task &t,
     }
     int i = lo, j = p0 - lo;
     KT *out = sm + t.out_off + (p0 - t.lo);
-    // branch-free, one shared-memory read a step: only the list whose head
-    // was taken advances, so only its next element is read.  The index of
-    // an exhausted list is clamped to its last element and that list is
-    // never chosen again (ta is forced by the length tests).
+    // branch-free: the index of an exhausted list is clamped to its last
+    // element and never chosen again (ta is forced by the length tests)
     const int ia = na - 1, jb = nb - 1;
     KT a = A[i < ia ? i : ia];
     KT b = B[j < jb ? j : jb];
@@ -84,9 +82,8 @@ __host__ __device__ __forceinline__ void d1_merge_chunk(KT *sm, const D1Task &t,
         out[n] = ta ? a : b;
         i += ta;
         j += !ta;
-        const KT nxt = *(ta ? A + (i < ia ? i : ia) : B + (j < jb ? j : jb));
-        a = ta ? nxt : a;
-        b = ta ? b : nxt;
+        a = A[i < ia ? i : ia];
+        b = B[j < jb ? j : jb];
     }
 }
 
