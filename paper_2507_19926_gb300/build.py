@@ -44,12 +44,15 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # nothing from it (within 1-5%, either way) except u8 k = 9 (0.127 -> 0.117
 # ms).  At k = 23, 25 the packed two-tiles-a-thread form spills too much:
 # 8/16-bit data runs one tile a thread on 32-bit keys there (u8 k = 23
-# 2.53 -> 1.87 ms, k = 25 3.11 -> 2.82 ms).
+# 2.53 -> 1.87 ms, k = 25 3.11 -> 2.82 ms).  With form 6 the first tree
+# level unrolled (U = 1) wins at k = 17 (photo 2.147 -> 2.004 ms, u32 4096^2
+# 0.770 -> 0.740) and for 32-bit keys at k = 21; U = 2 loses (2.70 ms).
 O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1)],
             9: [(4, 4, 32, 4, -1, 6, 16), (4, 4, 32, 4, -1, 0, 32)],
             11: [(4, 4, 32, 4, -1)], 13: [(4, 4, 32, 4, -1)], 15: [(4, 4, 32, 4, -1)],
-            17: [(4, 4, 32, 4, 0, 6)], 19: [(4, 4, 32, 4, 0, 7, 16), (4, 4, 32, 4, 0, 6, 32)],
-            21: [(4, 4, 32, 4, 0, 6)],
+            17: [(4, 4, 32, 4, 1, 6), (4, 4, 32, 4, 0, 6)],
+            19: [(4, 4, 32, 4, 0, 7, 16), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 1, 6)],
+            21: [(4, 4, 32, 4, 0, 6, 16), (4, 4, 32, 4, 1, 6, 32)],
             23: [(4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 0, 6, 16)],
             25: [(4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 0, 0, 16)]}
 # extra configurations for timing (comma list "k:tw:th:bx:by:U[:R[:keys]]"
