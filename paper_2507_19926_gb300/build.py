@@ -46,22 +46,23 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # 8/16-bit data runs one tile a thread on 32-bit keys there (u8 k = 23
 # 2.53 -> 1.87 ms, k = 25 3.11 -> 2.82 ms).  With form 6 the first tree
 # level unrolled (U = 1) wins at k = 17 (photo 2.147 -> 2.004 ms, u32 4096^2
-# 0.770 -> 0.740) and for 32-bit keys at k = 21; U = 2 loses (2.70 ms).
+# 0.770 -> 0.740) and for 32-bit keys at k = 21..25 (u32 k = 25 2.86 ->
+# 2.56 ms); U = 2 loses (2.70 ms).
 O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1)],
             9: [(4, 4, 32, 4, -1, 6, 16), (4, 4, 32, 4, -1, 0, 32)],
             11: [(4, 4, 32, 4, -1)], 13: [(4, 4, 32, 4, -1)], 15: [(4, 4, 32, 4, -1)],
             17: [(4, 4, 32, 4, 1, 6), (4, 4, 32, 4, 0, 6)],
             19: [(4, 4, 32, 4, 0, 7, 16), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 1, 6)],
             21: [(4, 4, 32, 4, 0, 6, 16), (4, 4, 32, 4, 1, 6, 32)],
-            23: [(4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 0, 6, 16)],
-            25: [(4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 0, 0, 16)]}
+            23: [(4, 4, 32, 4, 1, 6, 1), (4, 4, 32, 4, 1, 6, 32), (4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 6, 16)],
+            25: [(4, 4, 32, 4, 1, 6, 1), (4, 4, 32, 4, 1, 6, 32), (4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 0, 16)]}
 # extra configurations for timing (comma list "k:tw:th:bx:by:U[:R[:keys]]"
 # in MF_O1_EXTRA).  R is the network form, a bit set: 1 = the root extra
 # rows are sorted into shared memory by a stage of their own (netgen.build
 # rows_smem), 2 = lazy extra rows/columns, 4 = pressure-aware op order.
 for _spec in filter(None, os.environ.get("MF_O1_EXTRA", "").split(",")):
     _v = [int(v) for v in _spec.split(":")]
-    O1_VALUE.setdefault(_v[0], []).append(tuple((_v + [0, 0])[1:7]))
+    O1_VALUE.setdefault(_v[0], []).append(tuple((_v + [0, 0, 0])[1:8]))
 # a 7th field restricts a configuration to 16-bit keys (u8/u16, two tiles a
 # thread) or 32-bit keys (u32/f32); 0 = both; 1 = u8/u16 data with 32-bit
 # keys (one tile a thread: half the values in flight of the packed form)
