@@ -273,6 +273,54 @@ def bench_batched(dev, stream, flush, reps=5):
             "plain_mpix_s": px / t_plain / 1e3, "speedup": t_plain / t_batch}
 
 
+def bench_small(dev, stream, n_graph=200, reps=20):
+    """640 x 480 u8, k = 5 (a launch-latency-bound frame): the time of one
+    launch, and back-to-back launches replayed from one CUDA graph."""
+    import torch
+    import paper_2507_19926_gb300 as mf
+    from paper_2507_19926_gb300 import synth
+    H, W, k = 480, 640, 5
+    x = to_device(synth.uniform((1, H, W), "u8", synth.SEED_BASE + 0), dev)
+    y = torch.empty_like(x)
+    call = lambda s: mf.mf_median_filter(x.data_ptr(), y.data_ptr(), H, W, W, 1, mf.MF_U8, k,
+                                         mf.MF_BORDER_CLAMP, s)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            call(stream.cuda_stream)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call(stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    single = statistics.median(ts)
+    # n_graph launches captured once, replayed: no per-launch CPU cost
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(device=dev)
+    cap.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(g, stream=cap):
+            for _ in range(n_graph):
+                call(cap.cuda_stream)
+    torch.cuda.current_stream(dev).wait_stream(cap)
+    g.replay()
+    torch.cuda.synchronize(dev)
+    tg = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        e1.synchronize()
+        tg.append(e0.elapsed_time(e1))
+    per = statistics.median(tg) / n_graph
+    return {"workload": "1 x 480 x 640 u8, k = 5", "single_launch_ms": single,
+            "graph_replayed_ms_per_frame": per, "graph_mpix_s": H * W / per / 1e3,
+            "frames_per_graph": n_graph, "plan": mf.mf_describe(H, W, 1, mf.MF_U8, k)}
+
+
 def bench_fwd_bwd(dev, stream, flush, reps=5):
     """f32 16x1x1024x1024, k = 9 and 25: forward, forward + argmedian, and
     forward + argmedian + backward (atomic and deterministic)."""
@@ -460,6 +508,7 @@ def run_ours(args):
         cpu = {"value": v, "unit": "Mpix/s", "cores": oracle.max_threads(), "kind": "oracle",
                "sample": "%d output channel-pixels on random full rows of the same image (%.1f s)" % (npx, secs)}
     if ws == 1 and not args.no_extras:
+        extra["small_frame"] = bench_small(dev, stream)
         extra["batched_vs_plain"] = bench_batched(dev, stream, flush)
         extra["fwd_bwd_vs_fwd"] = bench_fwd_bwd(dev, stream, flush)
         extra["sweep_4096"] = bench_sweep(dev, stream, flush)
