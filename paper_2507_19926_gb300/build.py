@@ -59,7 +59,9 @@ O1_VALUE = {3: [(2, 2, 32, 4, -1)], 5: [(2, 2, 32, 4, -1)], 7: [(4, 4, 32, 4, -1
 # extra configurations for timing (comma list "k:tw:th:bx:by:U[:R[:keys]]"
 # in MF_O1_EXTRA).  R is the network form, a bit set: 1 = the root extra
 # rows are sorted into shared memory by a stage of their own (netgen.build
-# rows_smem), 2 = lazy extra rows/columns, 4 = pressure-aware op order.
+# rows_smem), 2 = lazy extra rows/columns, 4 = pressure-aware op order,
+# 8 = the direct kernel (each thread loads its own footprint into
+# registers and sorts its own columns: no shared memory, no barriers).
 for _spec in filter(None, os.environ.get("MF_O1_EXTRA", "").split(",")):
     _v = [int(v) for v in _spec.split(":")]
     O1_VALUE.setdefault(_v[0], []).append(tuple((_v + [0, 0, 0])[1:8]))
@@ -103,6 +105,7 @@ def _o1_instances():
                 for dt in (0, 1):
                     out.append((k, tw, th, bx, by, (u, rs), dt, "KoU32", False, 0, ci))
     for k, (tw, th, bx, by, u, rs, keys) in sorted(O1_ARG32.items()):
+        rs &= ~8  # argmedian records run in the shared-memory kernel
         out.append((k, tw, th, bx, by, (u, rs), 0, "KoU32", True, 24, 0))
         out.append((k, tw, th, bx, by, (u, rs), 1, "KoU32", True, 16, 0))
     for k, (tw, th, bx, by, u, rs, keys) in sorted(O1_ARG64.items()):
@@ -135,13 +138,15 @@ def generate():
         sorts = sorted({k - th + 1 for (_, th) in nets} | {k - tw + 1 for (tw, _) in nets})
         n_ops = {}
         for tw, th in nets:
+            assert not (rsm & 8 and rsm & 1), "the direct kernel takes no shared-memory rows"
             net = netgen.build(k, tw, th, rows_smem=bool(rsm & 1), lazy=bool(rsm & 2), pressure=bool(rsm & 4))
             n_ops[(tw, th)] = netgen.n_minmax(net)
             if O1_FUSE3:
                 net = netgen.fuse3(net)
             sync = O1_SYNC_EVERY if O1_SYNC_EVERY and len(net.ops) > 4 * O1_SYNC_EVERY else 0
             u_eff = unroll if O1_ROLLED else -1
-            src, _ = codegen.emit_network_auto(net, codegen.net_name(k, tw, th, u_eff, rsm), sync, u_eff)
+            src, _ = codegen.emit_network_auto(net, codegen.net_name(k, tw, th, u_eff, rsm), sync, u_eff,
+                                               direct=bool(rsm & 8))
             parts.append(src)
         for n in sorts:
             parts.append(codegen.emit_colsort(n))

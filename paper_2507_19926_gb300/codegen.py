@@ -18,8 +18,10 @@ from . import netgen
 
 def form_suffix(form):
     """Name suffix of a network form (bit 0: root rows from shared memory,
-    bit 1: lazy extra rows/columns, bit 2: pressure-aware order)."""
-    return ("_rs" if form & 1 else "") + ("_lz" if form & 2 else "") + ("_pr" if form & 4 else "")
+    bit 1: lazy extra rows/columns, bit 2: pressure-aware order, bit 3: the
+    direct kernel -- footprint in registers, no shared memory)."""
+    return (("_rs" if form & 1 else "") + ("_lz" if form & 2 else "") + ("_pr" if form & 4 else "") +
+            ("_dr" if form & 8 else ""))
 
 
 def net_name(k, tw, th, unroll=None, form=0):
@@ -35,7 +37,7 @@ def sort_name(n):
     return "ColSort_%d" % n
 
 
-def emit_network(net, name, sync_every=0):
+def emit_network(net, name, sync_every=0, direct=False):
     """sync_every > 0 inserts a block barrier after every that many ops: all
     threads of a block run this same branch-free code, so the barrier only
     keeps the block's warps within one window of the (very long) program,
@@ -45,6 +47,7 @@ def emit_network(net, name, sync_every=0):
     w("struct %s {" % name)
     w("  static constexpr int n_ops = %d;" % netgen.n_minmax(net))
     w("  static constexpr bool rows_smem = %s;" % ("true" if any(d[0] == "row" for d in net.inputs) else "false"))
+    w("  static constexpr bool direct = %s;" % ("true" if direct else "false"))
     w("  template <class KO, class L, class OUT>")
     w("  static __device__ __forceinline__ void run(const typename KO::T *__restrict__ cs,")
     w("                                            const typename KO::T *__restrict__ rw,")
@@ -82,17 +85,20 @@ def emit_network(net, name, sync_every=0):
     return "\n".join(lines) + "\n"
 
 
-def emit_network_auto(net, name, sync_every=0, unroll_levels=0):
+def emit_network_auto(net, name, sync_every=0, unroll_levels=0, direct=False):
     """The loop-rolled form (rolled.py) when the tree's children pair up,
-    else the straight-line form.  unroll_levels < 0 forces straight-line."""
+    else the straight-line form.  unroll_levels < 0 forces straight-line.
+    direct: the network runs in the register-footprint kernel, which needs
+    the straight-line form (its inputs are constant indices of local
+    arrays, kept in registers only when every index is a constant)."""
     from . import rolled
-    if unroll_levels >= 0:
+    if unroll_levels >= 0 and not direct:
         try:
             ir, _ = rolled.build_ir(net)
             return rolled.emit(net, ir, name, unroll_levels=unroll_levels), True
         except rolled.RollError:
             pass
-    return emit_network(net, name, sync_every), False
+    return emit_network(net, name, sync_every, direct), False
 
 
 def emit_colsort(n):

@@ -153,10 +153,99 @@ struct O1Store {
     }
 };
 
+// ------------------------------------------------------------ direct form
+// For small k the staging, column-sort and output stages of the shared-
+// memory form cost more instructions per pixel than the network itself.
+// The direct form gives every thread its own (TH + K - 1) x (TW + K - 1)
+// footprint in registers (clamp-to-edge loads that neighbouring threads
+// share through L1), sorts its own column segments and stores its medians
+// straight to global memory: no shared memory and no barriers.  Block and
+// tile geometry are those of the shared-memory form (lane-0 tiles in the
+// left half of the block's region, lane-1 tiles in the right half), so the
+// batched paths cut work items the same way.
+template <int K, int TW, int TH>
+struct O1RegLayout {
+    static constexpr int FW = TW + K - 1;   // footprint of one tile
+    static constexpr int FH = TH + K - 1;
+    static constexpr int CH0 = K - TH + 1;  // root core height
+    static __host__ __device__ constexpr int px(int fy, int fx) { return fy * FW + fx; }
+    static __host__ __device__ constexpr int col(int fx, int i) { return fx * CH0 + i; }
+    static __host__ __device__ constexpr int row(int, int) { return 0; }  // not used: no shared rows
+};
+
+template <int TW, int BX, int DT, class KO>
+struct O1DirectStore {
+    typedef typename KO::T T;
+    typedef typename Dt<DT>::E E;
+    const ImgArgs &a;
+    char *dst;
+    int x0, y0;
+    __device__ __forceinline__ void operator()(int pix, T w) const {
+        constexpr int P = KO::lanes;
+        const int py = pix / TW, px = pix - py * TW;
+        const int y = y0 + py;
+        if (y >= a.H) return;
+        E *row = reinterpret_cast<E *>(dst + (size_t)y * a.pitch);
+#pragma unroll
+        for (int l = 0; l < P; l++) {
+            const int x = x0 + l * BX * TW + px;
+            const uint32_t key = P == 2 ? (uint32_t)((w >> (16 * l)) & 0xffffu) : (uint32_t)w;
+            if (x < a.W) row[x] = Dt<DT>::val(key);
+        }
+    }
+};
+
+template <int K, int TW, int TH, int BX, int BY, int DT, class KO, class NET, class CSORT>
+__device__ __forceinline__ void o1_block_direct(const ImgArgs &a, int bxi, int byi, int z) {
+    typedef O1RegLayout<K, TW, TH> RL;
+    typedef typename KO::T T;
+    typedef typename Dt<DT>::E E;
+    constexpr int P = KO::lanes, R = (K - 1) / 2;
+    const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
+    const int x0 = bxi * (P * BX * TW) + tx * TW;
+    const int y0 = byi * (BY * TH) + ty * TH;
+    if (x0 >= a.W || y0 >= a.H) return;  // whole tile (both lanes) outside
+    const char *src = a.src + (size_t)z * a.plane;
+    // footprint in registers: the clamped columns of both lanes once, then
+    // one row pointer per footprint row
+    int xc0[RL::FW], xc1[RL::FW];
+#pragma unroll
+    for (int fx = 0; fx < RL::FW; fx++) {
+        xc0[fx] = clampi(x0 - R + fx, 0, a.W - 1);
+        xc1[fx] = clampi(x0 + BX * TW - R + fx, 0, a.W - 1);
+    }
+    T f[RL::FH * RL::FW];
+#pragma unroll
+    for (int fy = 0; fy < RL::FH; fy++) {
+        const E *row = reinterpret_cast<const E *>(src + (size_t)clampi(y0 - R + fy, 0, a.H - 1) * a.pitch);
+#pragma unroll
+        for (int fx = 0; fx < RL::FW; fx++)
+            f[RL::px(fy, fx)] = O1Words<DT, KO, false, 0>::template make<RL>(row, xc0[fx], xc1[fx], 0, 0);
+    }
+    // the tile's own column segments over the root core rows
+    T cs[RL::FW * RL::CH0];
+#pragma unroll
+    for (int fx = 0; fx < RL::FW; fx++) {
+        T v[RL::CH0];
+#pragma unroll
+        for (int i = 0; i < RL::CH0; i++) v[i] = f[RL::px(TH - 1 + i, fx)];
+        CSORT::template run<KO>(v);
+#pragma unroll
+        for (int i = 0; i < RL::CH0; i++) cs[RL::col(fx, i)] = v[i];
+    }
+    O1DirectStore<TW, BX, DT, KO> out{a, a.dst + (size_t)z * a.plane, x0, y0};
+    NET::template run<KO, RL>(cs, f, f, out);
+}
+
 // One block's work: the block of tiles at (bxi, byi) of plane z.
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
           class CSORT, class RSORT>
 __device__ __forceinline__ void o1_block(const ImgArgs &a, int bxi, int byi, int z) {
+    if constexpr (NET::direct) {
+        static_assert(!ARG, "the direct form computes values only");
+        o1_block_direct<K, TW, TH, BX, BY, DT, KO, NET, CSORT>(a, bxi, byi, z);
+        return;
+    }
     typedef O1Layout<K, TW, TH, BX, BY, NET::rows_smem> L;
     typedef typename KO::T T;
     typedef typename Dt<DT>::E E;
@@ -291,8 +380,9 @@ __global__ void __launch_bounds__(BX *BY) o1_persistent(const ImgArgs *imgs, con
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, class NET>
 constexpr size_t o1_smem_bytes() {
     typedef O1Layout<K, TW, TH, BX, BY, NET::rows_smem> L;
-    return sizeof(typename KO::T) * (size_t)L::WORDS +
-           (ARG ? 0 : (size_t)KO::lanes * BX * TW * BY * TH * sizeof(typename Dt<DT>::E));
+    return NET::direct ? 0
+                       : sizeof(typename KO::T) * (size_t)L::WORDS +
+                             (ARG ? 0 : (size_t)KO::lanes * BX * TW * BY * TH * sizeof(typename Dt<DT>::E));
 }
 
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,

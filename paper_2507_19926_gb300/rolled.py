@@ -189,6 +189,7 @@ def emit(net, ir, name, max_sel_levels=4, unroll_levels=0):
     w("struct %s {" % name)
     w("  static constexpr int n_ops = %d;" % sum(2 if op[0].endswith("3") else 1 for op in net.ops))
     w("  static constexpr bool rows_smem = %s;" % ("true" if any(d[0] == "row" for d in net.inputs) else "false"))
+    w("  static constexpr bool direct = false;")
     w("  template <class KO, class L, class OUT>")
     w("  static __device__ __forceinline__ void run(const typename KO::T *__restrict__ cs,")
     w("                                            const typename KO::T *__restrict__ rw,")
