@@ -173,26 +173,12 @@ struct O1RegLayout {
     static __host__ __device__ constexpr int row(int, int) { return 0; }  // not used: no shared rows
 };
 
-template <int TW, int BX, int DT, class KO>
-struct O1DirectStore {
-    typedef typename KO::T T;
-    typedef typename Dt<DT>::E E;
-    const ImgArgs &a;
-    char *dst;
-    int x0, y0;
-    __device__ __forceinline__ void operator()(int pix, T w) const {
-        constexpr int P = KO::lanes;
-        const int py = pix / TW, px = pix - py * TW;
-        const int y = y0 + py;
-        if (y >= a.H) return;
-        E *row = reinterpret_cast<E *>(dst + (size_t)y * a.pitch);
-#pragma unroll
-        for (int l = 0; l < P; l++) {
-            const int x = x0 + l * BX * TW + px;
-            const uint32_t key = P == 2 ? (uint32_t)((w >> (16 * l)) & 0xffffu) : (uint32_t)w;
-            if (x < a.W) row[x] = Dt<DT>::val(key);
-        }
-    }
+// Collects the tile's medians in registers (the flat network calls it with
+// constant pixel indices).
+template <class T, int N>
+struct O1Collect {
+    T *res;
+    __device__ __forceinline__ void operator()(int pix, T w) const { res[pix] = w; }
 };
 
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, class NET, class CSORT>
@@ -200,27 +186,40 @@ __device__ __forceinline__ void o1_block_direct(const ImgArgs &a, int bxi, int b
     typedef O1RegLayout<K, TW, TH> RL;
     typedef typename KO::T T;
     typedef typename Dt<DT>::E E;
-    constexpr int P = KO::lanes, R = (K - 1) / 2;
+    constexpr int P = KO::lanes, R = (K - 1) / 2, LX = BX * TW;  // LX: lane-1 column offset
     const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
     const int x0 = bxi * (P * BX * TW) + tx * TW;
     const int y0 = byi * (BY * TH) + ty * TH;
     if (x0 >= a.W || y0 >= a.H) return;  // whole tile (both lanes) outside
     const char *src = a.src + (size_t)z * a.plane;
-    // footprint in registers: the clamped columns of both lanes once, then
-    // one row pointer per footprint row
-    int xc0[RL::FW], xc1[RL::FW];
-#pragma unroll
-    for (int fx = 0; fx < RL::FW; fx++) {
-        xc0[fx] = clampi(x0 - R + fx, 0, a.W - 1);
-        xc1[fx] = clampi(x0 + BX * TW - R + fx, 0, a.W - 1);
-    }
     T f[RL::FH * RL::FW];
+    // footprint in registers.  Inside the image every row is one pointer and
+    // the columns are constant offsets from it; near the border each column
+    // and row is clamped.
+    const bool inside = x0 - R >= 0 && x0 + (P - 1) * LX - R + RL::FW - 1 < a.W && y0 - R >= 0 &&
+                        y0 - R + RL::FH - 1 < a.H;
+    if (inside) {
 #pragma unroll
-    for (int fy = 0; fy < RL::FH; fy++) {
-        const E *row = reinterpret_cast<const E *>(src + (size_t)clampi(y0 - R + fy, 0, a.H - 1) * a.pitch);
+        for (int fy = 0; fy < RL::FH; fy++) {
+            const E *row = reinterpret_cast<const E *>(src + (size_t)(y0 - R + fy) * a.pitch) + (x0 - R);
 #pragma unroll
-        for (int fx = 0; fx < RL::FW; fx++)
-            f[RL::px(fy, fx)] = O1Words<DT, KO, false, 0>::template make<RL>(row, xc0[fx], xc1[fx], 0, 0);
+            for (int fx = 0; fx < RL::FW; fx++)
+                f[RL::px(fy, fx)] = O1Words<DT, KO, false, 0>::template make<RL>(row, fx, fx + LX, 0, 0);
+        }
+    } else {
+        int xc0[RL::FW], xc1[RL::FW];
+#pragma unroll
+        for (int fx = 0; fx < RL::FW; fx++) {
+            xc0[fx] = clampi(x0 - R + fx, 0, a.W - 1);
+            xc1[fx] = clampi(x0 + LX - R + fx, 0, a.W - 1);
+        }
+#pragma unroll
+        for (int fy = 0; fy < RL::FH; fy++) {
+            const E *row = reinterpret_cast<const E *>(src + (size_t)clampi(y0 - R + fy, 0, a.H - 1) * a.pitch);
+#pragma unroll
+            for (int fx = 0; fx < RL::FW; fx++)
+                f[RL::px(fy, fx)] = O1Words<DT, KO, false, 0>::template make<RL>(row, xc0[fx], xc1[fx], 0, 0);
+        }
     }
     // the tile's own column segments over the root core rows
     T cs[RL::FW * RL::CH0];
@@ -233,8 +232,27 @@ __device__ __forceinline__ void o1_block_direct(const ImgArgs &a, int bxi, int b
 #pragma unroll
         for (int i = 0; i < RL::CH0; i++) cs[RL::col(fx, i)] = v[i];
     }
-    O1DirectStore<TW, BX, DT, KO> out{a, a.dst + (size_t)z * a.plane, x0, y0};
+    T res[TW * TH];
+    O1Collect<T, TW * TH> out{res};
     NET::template run<KO, RL>(cs, f, f, out);
+    // medians out: constant offsets from one row pointer when the tiles of
+    // both lanes lie inside the image, else element by element
+    char *dst = a.dst + (size_t)z * a.plane;
+    const bool full = y0 + TH - 1 < a.H && x0 + (P - 1) * LX + TW - 1 < a.W;
+#pragma unroll
+    for (int py = 0; py < TH; py++) {
+        const int y = y0 + py;
+        if (!full && y >= a.H) break;
+        E *orow = reinterpret_cast<E *>(dst + (size_t)y * a.pitch) + x0;
+#pragma unroll
+        for (int l = 0; l < P; l++)
+#pragma unroll
+            for (int px = 0; px < TW; px++) {
+                const T w = res[py * TW + px];
+                const uint32_t key = P == 2 ? (uint32_t)((w >> (16 * l)) & 0xffffu) : (uint32_t)w;
+                if (full || x0 + l * LX + px < a.W) orow[l * LX + px] = Dt<DT>::val(key);
+            }
+    }
 }
 
 // One block's work: the block of tiles at (bxi, byi) of plane z.
