@@ -163,8 +163,9 @@ int mf_batch_describe(const mf_batch_plan *plan, int *kernels, long long *items)
  * descs (device buffers, as for mf_batch_plan_create) with the persistent
  * data-oblivious kernels, taking its work queues from one fixed array of
  * 2 MiB that the library's module holds on every device where it is used,
- * until the library is unloaded.  Limits: at most 256 images, k = 1 or an
- * odd k from 3 to 25, and at most 126,976 work items (one item is one
+ * until the library is unloaded.  Limits: at most 256 images, k = 1 or a
+ * k the data-oblivious kernels are built for (odd 3 to 25 for every dtype,
+ * 27 for 32-bit data), and at most 126,976 work items (one item is one
  * block of pixels: 128 x 8 for k = 3, 5 and 8/16-bit data, 64 x 8 for 32-bit
  * data, 256 x 16 for larger k with 8/16-bit data up to k = 21, else
  * 128 x 16); beyond them it returns MF_ERR_ARG

@@ -51,6 +51,9 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # staging dominates: k = 3 (u8 35.6 -> 25.0 us, u32 56.7 -> 35.4 us at
 # 4096^2) and 32-bit keys up to k = 9 (u32 k = 7 180 -> 121 us, k = 9 280 ->
 # 229 us); with packed 8/16-bit keys it ties at k = 5, 7 and spills at 9.
+# k = 27 is built for 32-bit keys only: 3.64 ms against 7.62 ms for the best
+# data-aware tile (u32 4096^2); for u8 the gain is 4.03 vs 5.02 ms and at
+# k = 29 the data-aware kernel wins for u8 -- not worth the compile time.
 O1_VALUE = {3: [(2, 2, 32, 4, -1, 8), (2, 2, 32, 4, -1, 0)],
             5: [(2, 2, 32, 4, -1, 0, 16), (2, 2, 32, 4, -1, 8, 32), (2, 2, 32, 4, -1, 0, 32)],
             7: [(4, 4, 32, 4, -1, 0, 16), (4, 4, 32, 4, -1, 8, 32), (4, 4, 32, 4, -1, 0, 32)],
@@ -60,7 +63,8 @@ O1_VALUE = {3: [(2, 2, 32, 4, -1, 8), (2, 2, 32, 4, -1, 0)],
             19: [(4, 4, 32, 4, 0, 7, 16), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 1, 6)],
             21: [(4, 4, 32, 4, 0, 6, 16), (4, 4, 32, 4, 1, 6, 32)],
             23: [(4, 4, 32, 4, 1, 6, 1), (4, 4, 32, 4, 1, 6, 32), (4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 6, 16)],
-            25: [(4, 4, 32, 4, 1, 6, 1), (4, 4, 32, 4, 1, 6, 32), (4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 0, 16)]}
+            25: [(4, 4, 32, 4, 1, 6, 1), (4, 4, 32, 4, 1, 6, 32), (4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 0, 16)],
+            27: [(4, 4, 32, 4, 1, 6, 32)]}
 # extra configurations for timing (comma list "k:tw:th:bx:by:U[:R[:keys]]"
 # in MF_O1_EXTRA).  R is the network form, a bit set: 1 = the root extra
 # rows are sorted into shared memory by a stage of their own (netgen.build
@@ -74,8 +78,16 @@ for _spec in filter(None, os.environ.get("MF_O1_EXTRA", "").split(",")):
 # thread) or 32-bit keys (u32/f32); 0 = both; 1 = u8/u16 data with 32-bit
 # keys (one tile a thread: half the values in flight of the packed form)
 O1_VALUE = {k: [tuple(c) + (0,) * (7 - len(c)) for c in v] for k, v in O1_VALUE.items()}
-# argmedian with 32-bit records (8/16-bit data) and 64-bit records (32-bit data)
-O1_ARG32 = {k: v[0] for k, v in O1_VALUE.items()}
+# argmedian with 32-bit records (8/16-bit data) and 64-bit records (32-bit data);
+# above k = 25 the argmedian comes from the values and the recovery pass
+O1_ARG32 = {k: v[0] for k, v in O1_VALUE.items() if k <= 25}
+
+
+def o1_covers(k, dtype):
+    """True when a data-oblivious value kernel is built for (k, dtype name)."""
+    wide = dtype in ("u32", "f32")
+    return any(keys == 0 or keys == (32 if wide else 16) or (keys == 1 and not wide)
+               for (_, _, _, _, _, _, keys) in O1_VALUE.get(k, []))
 # 32-bit data: the argmedian comes from the value kernel plus the recovery
 # pass (mf_argmedian.cu), which beats 64-bit records (1.33 vs ~0.4 ms at
 # k = 9, f32 16 x 1024^2); no 64-bit-record networks are built.

@@ -277,6 +277,9 @@ int d1_default_tile(int k, int dtype, bool arg) {
     while (t * 4 <= k) t *= 2;
     if (t < 2) t = 2;
     if (t > 16) t = 16;
+    // 2-byte keys: the 16 x 16 tree measured faster from k = 27 on
+    // (u8 4096^2: 5.02 vs 5.61 ms at k = 27, 6.25 vs 6.40 ms at k = 31)
+    if (key_bytes(dtype, arg) == 2 && k >= 27) t = 16;
     for (; t >= 2; t /= 2)
         if (d1_supported_tile(k, dtype, arg, t)) return t;
     return 0;

@@ -114,7 +114,8 @@ extern "C" int mf_batch_run_static(const mf_image_desc *descs, int n, mf_stream_
         if (d.k == 1) continue;
         const O1Entry *o1 = (d.k >= 3 && (d.k & 1)) ? find_o1(d.k, d.dtype, false) : nullptr;
         if (!o1 || !o1->persist) {
-            set_error("image %d: the static batch supports k = 1 and the data-oblivious k (odd 3..25), got %d", i, d.k);
+            set_error("image %d: the static batch runs only the data-oblivious kernels, not built for k = %d "
+                      "with this dtype", i, d.k);
             return MF_ERR_UNSUPPORTED;
         }
         int c = 0;

@@ -15,6 +15,8 @@ KS = sorted(build.O1_VALUE)
 @pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("k", KS)
 def test_value_parity_ragged(dt, k):
+    if not build.o1_covers(k, dt):
+        pytest.skip("no data-oblivious kernel built for this k and dtype")
     # 77 x 203 spans several blocks in both directions with ragged tails
     for j, gen in enumerate((synth.uniform, synth.levels16)):
         x = gen((2, 77, 203), dt, 1000 + 10 * k + j)
@@ -66,7 +68,10 @@ def test_k1_identity(dt):
 @pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("k", KS)
 def test_argmedian_parity(dt, k):
-    # 32-bit data above k = 9: oblivious values + the argmedian recovery pass
+    # 32-bit data, and every dtype above k = 25: oblivious values + the
+    # argmedian recovery pass
+    if not build.o1_covers(k, dt):
+        pytest.skip("no data-oblivious kernel built for this k and dtype")
     for j, gen in enumerate((synth.levels16, synth.uniform)):
         x = gen((2, 45, 170), dt, 2000 + 10 * k + j)
         got, idx = gpu_filter(x, k, "oblivious", return_idx=True)
@@ -100,6 +105,8 @@ def test_every_configuration(dt, k):
     """Every instantiated network configuration of (k, dtype) -- the
     autotuner's candidates: network forms, key widths -- against the oracle
     through mf_median_filter_config, until the entry reports no more."""
+    if not build.o1_covers(k, dt):
+        pytest.skip("no data-oblivious kernel built for this k and dtype")
     import torch
     import paper_2507_19926_gb300 as mf
     from gpu_util import ensure_lib, to_dev, to_host
