@@ -87,64 +87,4 @@ __host__ __device__ __forceinline__ void d1_merge_chunk(KT *sm, const D1Task &t,
     }
 }
 
-#ifdef __CUDACC__
-// Device merge of one chunk by a sorting network instead of a sequential
-// loop: after the merge-path search, the chunk's cnt <= C outputs are the
-// cnt smallest of A[i0 .. i0+C) and B[j0 .. j0+C) (positions past a list's
-// end read as the largest key), which Batcher's odd-even merge of the two
-// windows -- held in registers, fully unrolled -- puts first.  The
-// comparators that only feed the upper half are dead code and vanish, so a
-// chunk costs about 5 min/max a output (C = 16) and its loads are
-// independent of each other: no load -> compare -> load chain per step as
-// in the sequential merge.  Equal keys are equal values (value mode) or
-// cannot occur (records carry the footprint index), so the outputs equal
-// d1_merge_chunk's.
-template <class KT, int N2>
-__device__ __forceinline__ void d1_oe_merge(KT (&v)[N2]) {
-    constexpr int p = N2 / 2;
-#pragma unroll
-    for (int k = p; k >= 1; k /= 2)
-#pragma unroll
-        for (int j = k % p; j + k < N2; j += 2 * k)
-#pragma unroll
-            for (int i = 0; i < k; i++)
-                if (i + j + k < N2) {
-                    const KT a = v[i + j], b = v[i + j + k];
-                    v[i + j] = a < b ? a : b;
-                    v[i + j + k] = a < b ? b : a;
-                }
-}
-
-template <class KT, int C>
-__device__ __forceinline__ void d1_merge_chunk_net(KT *sm, const D1Task &t, int chunk) {
-    const KT *A = sm + t.a_off;
-    const KT *B = sm + t.b_off;
-    const int na = t.a_len, nb = t.b_len;
-    const int p0 = t.lo + chunk * t.chunk;
-    int cnt = t.hi - p0 + 1;
-    if (cnt > t.chunk) cnt = t.chunk;
-    int lo = p0 - nb > 0 ? p0 - nb : 0;
-    int hi = p0 < na ? p0 : na;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (A[mid] <= B[p0 - 1 - mid]) lo = mid + 1;
-        else hi = mid;
-    }
-    const int i0 = lo, j0 = p0 - lo;
-    const int ra = na - i0, rb = nb - j0;  // elements left in each list
-    const KT S = d1_sentinel<KT>();
-    KT v[2 * C];
-#pragma unroll
-    for (int n = 0; n < C; n++) {
-        v[n] = n < ra ? A[i0 + n] : S;
-        v[C + n] = n < rb ? B[j0 + n] : S;
-    }
-    d1_oe_merge<KT, 2 * C>(v);
-    KT *out = sm + t.out_off + (p0 - t.lo);
-#pragma unroll
-    for (int n = 0; n < C; n++)
-        if (n < cnt) out[n] = v[n];
-}
-#endif
-
 }  // namespace mf

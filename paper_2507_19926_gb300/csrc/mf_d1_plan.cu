@@ -32,6 +32,24 @@
 
 namespace mf {
 
+// Merge chunk rule (outputs per work item; each chunk pays one binary search
+// over its two input lists): chunk = clamp(phase outputs / (div * threads),
+// min, 32).  Measured on 4096^2 images, k = 27..75: 2-byte keys do best with
+// (min 16, div 2), wider keys with (min 12, div 1).  MF_D1_CHUNK="min:div"
+// overrides both (tuning sweeps).
+static const bool D1_ODD_CHUNKS = !getenv("MF_D1_EVEN_CHUNKS");
+
+static void chunk_rule(int key_bytes, int *min_chunk, int *div) {
+    *min_chunk = key_bytes <= 2 ? 16 : 12;
+    *div = key_bytes <= 2 ? 2 : 1;
+    const char *e = getenv("MF_D1_CHUNK");
+    int a = 0, b = 0;
+    if (e && sscanf(e, "%d:%d", &a, &b) == 2 && a >= 1 && a <= 32 && b >= 1 && b <= 64) {
+        *min_chunk = a;
+        *div = b;
+    }
+}
+
 namespace {
 
 struct Ref {
@@ -364,7 +382,8 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes) {
     plan->merge_outputs = plan->sort_elems = 0;
     auto resolve = [&](const Ref &r) { return r.list >= 0 ? B.lists[r.list].off + r.start : (r.list == -1 ? r.start : 0); };
     std::vector<std::vector<int>> by_phase(nph);
-    const int chunk = d1_merge_chunk_len(key_bytes);
+    int min_chunk = 16, div = 1;
+    chunk_rule(key_bytes, &min_chunk, &div);
     for (size_t ti = 0; ti < B.tasks.size(); ti++)
         if (keep[ti]) by_phase[task_phase[ti]].push_back((int)ti);
     for (int p = 0; p < nph; p++) {
@@ -372,6 +391,13 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes) {
         long long outs_p = 0;
         for (int ti : by_phase[p])
             if (B.tasks[ti].type == D1_MERGE) outs_p += B.tasks[ti].hi - B.tasks[ti].lo + 1;
+        // about one chunk per thread: phases with few outputs (the upper tree
+        // levels) get short chunks so the whole block shares them
+        int chunk = (int)std::min<long long>(32, std::max<long long>(min_chunk, outs_p / ((long long)div * nt)));
+        // the chunks of one merge run on consecutive threads: an odd number of
+        // 4-byte words between their output runs spreads a warp's stores
+        // (and its roughly proportional input reads) over all 32 banks
+        if (D1_ODD_CHUNKS) chunk = key_bytes == 2 ? (chunk & ~3) + 2 : (chunk | 1);
         // sorts first, grouped by size class, then merges
         std::vector<int> order = by_phase[p];
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {

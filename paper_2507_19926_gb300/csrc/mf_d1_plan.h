@@ -20,11 +20,6 @@ enum { D1_SORT = 0, D1_MERGE = 1 };
 // block can run 1024 threads.
 constexpr int D1_MAX_SORT = 32;
 
-// Outputs per merge work item: the device merges a chunk with a register
-// network over two windows of this many elements (mf_d1_ops.cuh), 16 for
-// keys of up to 4 bytes and 8 for 8-byte records (64 registers a thread).
-constexpr int d1_merge_chunk_len(int key_bytes) { return key_bytes > 4 ? 8 : 16; }
-
 // One task.  Offsets and lengths are in list elements of shared memory.
 struct D1Task {
     int32_t type;

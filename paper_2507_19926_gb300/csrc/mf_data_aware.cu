@@ -99,7 +99,7 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
             const uint32_t item = p.work[w];
             const D1Task t = d1_unpack(p.tasks[item >> 12], FW);
             if (t.type == D1_SORT) d1_sort_any<KT, NMAX>(sm, t);
-            else d1_merge_chunk_net<KT, d1_merge_chunk_len(sizeof(KT))>(sm, t, (int)(item & 4095u));
+            else d1_merge_chunk<KT>(sm, t, (int)(item & 4095u));
         }
         __syncthreads();
     }
