@@ -106,6 +106,9 @@ O1_ROLLED = os.environ.get("MF_O1_ROLLED", "1") == "1"
 # Fuse min(min(a, b), c) chains into three-input min/max (one instruction).
 O1_FUSE3 = os.environ.get("MF_O1_FUSE3", "1") == "1"
 
+# Rolled networks: one-level value selects as multiply-adds (rolled.emit).
+O1_MAD_SELECT = os.environ.get("MF_O1_MAD_SELECT", "0") == "1"
+
 # Barrier spacing (min/max ops) inside long per-thread networks.
 O1_SYNC_EVERY = int(os.environ.get("MF_O1_SYNC_EVERY", "0"))
 
@@ -166,7 +169,7 @@ def generate():
             sync = O1_SYNC_EVERY if O1_SYNC_EVERY and len(net.ops) > 4 * O1_SYNC_EVERY else 0
             u_eff = unroll if O1_ROLLED else -1
             src, _ = codegen.emit_network_auto(net, codegen.net_name(k, tw, th, u_eff, rsm), sync, u_eff,
-                                               direct=bool(rsm & 8))
+                                               direct=bool(rsm & 8), mad_select=O1_MAD_SELECT)
             parts.append(src)
         for n in sorts:
             parts.append(codegen.emit_colsort(n))

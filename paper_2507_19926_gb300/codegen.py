@@ -85,7 +85,7 @@ def emit_network(net, name, sync_every=0, direct=False):
     return "\n".join(lines) + "\n"
 
 
-def emit_network_auto(net, name, sync_every=0, unroll_levels=0, direct=False):
+def emit_network_auto(net, name, sync_every=0, unroll_levels=0, direct=False, mad_select=False):
     """The loop-rolled form (rolled.py) when the tree's children pair up,
     else the straight-line form.  unroll_levels < 0 forces straight-line.
     direct: the network runs in the register-footprint kernel, which needs
@@ -95,7 +95,7 @@ def emit_network_auto(net, name, sync_every=0, unroll_levels=0, direct=False):
     if unroll_levels >= 0 and not direct:
         try:
             ir, _ = rolled.build_ir(net)
-            return rolled.emit(net, ir, name, unroll_levels=unroll_levels), True
+            return rolled.emit(net, ir, name, unroll_levels=unroll_levels, mad_select=mad_select), True
         except rolled.RollError:
             pass
     return emit_network(net, name, sync_every, direct), False

@@ -56,6 +56,16 @@ struct KoU64 {
     static __device__ __forceinline__ T mx3(T a, T b, T c) { return mx(mx(a, b), c); }
 };
 
+// a + s * d for a loop variable s in {0, 1} and d = b - a: the select
+// between a and b as one multiply-add (modular arithmetic makes it exact for
+// any bit patterns, packed lanes included), issued on the FMA pipe instead
+// of the integer pipe the min/max networks saturate.
+__device__ __forceinline__ uint32_t mad_sel(unsigned s, uint32_t d, uint32_t a) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(s), "r"(d), "r"(a));
+    return r;
+}
+
 // ------------------------------------------------------------ dtype traits
 __device__ __forceinline__ uint32_t f32_key(uint32_t b) {
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);

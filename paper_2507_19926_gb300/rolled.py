@@ -178,11 +178,45 @@ def interpret(net, ir, col_fn, px_fn, row_fn=None):
     return [outs[i] for i in range(net.tw * net.th)]
 
 
-def emit(net, ir, name, max_sel_levels=4, unroll_levels=0):
+def _value_pairs(net, blk, level):
+    """(value a, value b) of every one-level value select on loop `level`
+    inside blk (nested loops included) whose two values are both defined
+    outside that loop, in first-use order."""
+    pairs = []
+
+    def visit(o):
+        if o is None or o[0] != "sel":
+            return
+        leaves = list(o[2].values())
+        if o[1] == (level,) and all(x[0] == "v" for x in leaves):
+            pr = (o[2][(0,)][1], o[2][(1,)][1])
+            if pr not in pairs and all(len(net.op_path[v]) <= level for v in pr):
+                pairs.append(pr)
+        else:
+            for x in leaves:
+                visit(x)
+
+    def walk(b):
+        for st in b:
+            if st[0] == "op":
+                for o in st[3:6]:
+                    visit(o)
+            elif st[0] == "loop":
+                walk(st[2])
+            else:
+                visit(st[2])
+    walk(blk)
+    return pairs
+
+
+def emit(net, ir, name, max_sel_levels=4, unroll_levels=0, mad_select=False):
     """CUDA source of the rolled network: a struct whose run() takes the
     thread's shared-memory bases and a store callback out(pixel, value).
     The loops of the first `unroll_levels` tree levels are emitted twice with
-    a constant loop variable instead (selects fold away, code doubles)."""
+    a constant loop variable instead (selects fold away, code doubles).
+    mad_select: a one-level select between two values a, b defined outside
+    its loop becomes a + s * (b - a) (one multiply-add, with b - a computed
+    once before the loop), which moves it off the integer min/max pipe."""
     lines = []
     w = lines.append
     n_in = len(net.inputs)
@@ -212,6 +246,8 @@ def emit(net, ir, name, max_sel_levels=4, unroll_levels=0):
                 return leaf(sub[tuple(prefix)])
             return "(s%d ? %s : %s)" % (levels[li], rec(li + 1, prefix + [1]), rec(li + 1, prefix + [0]))
         return rec(0, [])
+
+    diffs = {}  # (level, a, b) -> name of the hoisted b - a
 
     def emit_block(blk, indent, scope_loads):
         pad = "  " * indent
@@ -248,6 +284,10 @@ def emit(net, ir, name, max_sel_levels=4, unroll_levels=0):
                 return load_expr(opnd)
             if len(opnd[1]) > max_sel_levels:
                 raise RollError("select too deep")
+            if len(opnd[1]) == 1 and all(x[0] == "v" for x in leaves):
+                key = (opnd[1][0], opnd[2][(0,)][1], opnd[2][(1,)][1])
+                if key in diffs:
+                    return "mad_sel((unsigned)s%d, %s, v%d)" % (key[0], diffs[key], key[1])
             return sel_expr(opnd[1], opnd[2], lambda x: opnd_expr(x))
 
         for st in blk:
@@ -266,6 +306,11 @@ def emit(net, ir, name, max_sel_levels=4, unroll_levels=0):
                         emit_block(st[2], indent + 1, {})
                         w("%s}" % pad)
                 else:
+                    if mad_select:
+                        for a, b in _value_pairs(net, st[2], lvl):
+                            nm = "d%d_%d_%d" % (lvl, a, b)
+                            w("%sconst T %s = v%d - v%d;" % (pad, nm, b, a))
+                            diffs[(lvl, a, b)] = nm
                     w("%s#pragma unroll 1" % pad)
                     w("%sfor (int s%d = 0; s%d < 2; s%d++) {" % (pad, lvl, lvl, lvl))
                     emit_block(st[2], indent + 1, loads)
