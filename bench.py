@@ -146,6 +146,27 @@ def algorithmic_ops_per_px(k):
     return best
 
 
+def measured_traffic(plan):
+    """DRAM bytes per launch (read + write) that an ncu capture recorded for
+    the kernel the plan names, from profiles/dram_traffic.md, or None when no
+    row matches the kernel's current build hash (the kernel changed since)."""
+    import re
+    from paper_2507_19926_gb300 import build
+    m = re.search(r"kernel=(\S+)", plan)
+    if not m:
+        return None
+    h = build.kernel_source_hash(m.group(1))
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.md")) as f:
+            for line in f:
+                cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                if len(cells) >= 4 and cells[0] == "`%s`" % m.group(1) and h and cells[1] == "`%s`" % h:
+                    return int(cells[2]) + int(cells[3])
+    except (OSError, ValueError):
+        return None
+    return None
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -475,7 +496,7 @@ def run_ours(args):
         peak = sms * ipc_nominal * max_mhz * 1e6 * lanes / 1e9  # G element-ops/s
         achieved = ops_px * px_per_step / (ms_per_step * 1e-3) / 1e9
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gminmax/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": measured_traffic(plan),
                 "basis": "%.1f min/max element-ops per pixel (cheapest generated hierarchy) x %d px; "
                          "peak = %d SMs x %d min/max instr/clk/SM x %.0f MHz x %d lanes "
                          "(probe: %.1f instr/clk/SM at %.0f MHz)" % (

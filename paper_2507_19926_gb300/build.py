@@ -214,6 +214,23 @@ def generate():
     return tus
 
 
+def kernel_source_hash(fn_name):
+    """Build hash (generated translation unit + headers + flags) of the TU
+    that defines the registry launch function fn_name, or None: profiles
+    record it beside ncu counters, so a reader can tell whether the counters
+    still describe the kernel that is built."""
+    if not os.path.isdir(GEN):
+        return None
+    needle = "int %s(" % fn_name
+    for name in sorted(os.listdir(GEN)):
+        if name.startswith("o1_k") and name.endswith(".cu"):
+            path = os.path.join(GEN, name)
+            with open(path) as f:
+                if needle in f.read():
+                    return _flags_hash(path, NVCC_FLAGS + ARCH)
+    return None
+
+
 def _flags_hash(src, flags):
     h = hashlib.sha1()
     h.update(" ".join(flags).encode())
