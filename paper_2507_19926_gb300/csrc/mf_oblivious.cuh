@@ -20,6 +20,9 @@
 //      its inputs from shared memory at compile-time offsets;
 //   4. the TW x TH medians of every lane are stored (or, in argmedian mode,
 //      the source index recovered from the composite record).
+// Networks flagged `direct` (small k) run o1_block_direct instead: each
+// thread loads its own footprint into registers and sorts its own columns,
+// with no shared memory and no barrier.
 //
 // Shared-memory words are stored column-group-transposed: word (row, gx) at
 // row*RS + (gx % TW)*G + gx / TW with G odd.  Thread tx then reads
