@@ -105,9 +105,11 @@ int mf_median_filter_config(const void *src, void *dst, int H, int W, size_t pit
  * identity on its selected input).  All pointers are caller-owned device
  * memory; grad_out and grad_in use `pitch` (bytes, >= 4 * W), argidx uses
  * idx_pitch.  MF_GRAD_ATOMIC zeroes grad_in and scatter-adds with atomics
- * (summation order unspecified); MF_GRAD_DETERMINISTIC gathers, for each p,
- * the contributions in increasing row-major q (bit-identical run to run and
- * to a sequential scatter).  grad_in must not overlap grad_out or argidx. */
+ * (summation order unspecified); MF_GRAD_DETERMINISTIC adds, for each p,
+ * the contributions in increasing row-major q (an ordered scatter through
+ * shared memory; bit-identical run to run and to a sequential scatter).
+ * k bounds the distance between q and p.  grad_in must not overlap
+ * grad_out or argidx. */
 int mf_median_filter_bwd(const float *grad_out, const int32_t *argidx, float *grad_in,
                          int H, int W, size_t pitch, size_t idx_pitch, int channels, int k,
                          mf_grad_mode mode, mf_stream_t stream);

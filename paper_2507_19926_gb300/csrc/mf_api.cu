@@ -353,7 +353,7 @@ int mf_median_filter_bwd(const float *grad_out, const int32_t *argidx, float *gr
     cudaStream_t s = (cudaStream_t)stream;
     if (mode == MF_GRAD_ATOMIC) return bwd_atomic(grad_out, argidx, grad_in, H, W, pitch, idx_pitch, channels, s);
     if (mode == MF_GRAD_DETERMINISTIC)
-        return bwd_gather(grad_out, argidx, grad_in, H, W, pitch, idx_pitch, channels, k, s);
+        return bwd_ordered(grad_out, argidx, grad_in, H, W, pitch, idx_pitch, channels, k, s);
     set_error("unknown gradient mode %d", (int)mode);
     return MF_ERR_ARG;
 }

@@ -54,7 +54,7 @@ int launch_identity_idx(const ImgArgs &a, int channels, cudaStream_t s);
 // Backward (mf_backward.cu).
 int bwd_atomic(const float *g, const int32_t *idx, float *gi, int H, int W, size_t pitch,
                size_t idx_pitch, int C, cudaStream_t s);
-int bwd_gather(const float *g, const int32_t *idx, float *gi, int H, int W, size_t pitch,
+int bwd_ordered(const float *g, const int32_t *idx, float *gi, int H, int W, size_t pitch,
                size_t idx_pitch, int C, int k, cudaStream_t s);
 
 void set_error(const char *fmt, ...);

@@ -18,11 +18,14 @@ def _grad(idx_np, g_np, k, mode):
     return gi.cpu().numpy()
 
 
-@pytest.mark.parametrize("k", [3, 5, 9])
-def test_backward_modes(k):
-    x = synth.levels16((2, 60, 90), "f32", 31 + k)
+@pytest.mark.parametrize("k,shape", [(3, (2, 60, 90)), (5, (2, 60, 90)), (9, (2, 60, 90)), (25, (1, 70, 101)),
+                                     (5, (1, 37, 7)), (9, (3, 5, 200)), (3, (1, 1, 1)), (17, (1, 64, 64))])
+def test_backward_modes(k, shape):
+    """Ragged tiles, images narrower than a tile (several rows of p in one
+    32-wide tile row), heavy ties (many outputs picking the same input)."""
+    x = synth.levels16(shape, "f32", 31 + k)
     _, idx = oracle.median_filter(x, k, with_idx=True)
-    g = synth.normal_f32((2, 60, 90), 41 + k)
+    g = synth.normal_f32(shape, 41 + k)
     want = oracle.median_backward(g, idx)
     det = _grad(idx, g, k, "deterministic")
     assert np.array_equal(det.view(np.uint32), want.view(np.uint32))  # bit-exact
