@@ -4,19 +4,24 @@
 // window (m = (k*k-1)/2) has the median key v, and it is the j-th element
 // with key v in slot order, j = m - #{window keys < v} (0-based): all
 // elements below v precede it, and equal keys order by slot.  Given the
-// median value (from any of the value kernels), one pass over the window
-// finds that element: count the keys below v and remember the slots of the
-// first equal keys; a second pass is only needed when more than NCAND keys
-// tie with the median before the j-th one.  The window is read from a
-// shared-memory tile of the block's footprint (clamp-to-edge).
+// median value (from any of the value kernels), one branch-free pass over
+// the window counts the keys below v and equal to v and keeps the last
+// equal slot; that slot is the answer when the median is the last of its
+// ties in slot order (always, without ties), else a second pass finds the
+// j-th equal key.  The window is read from a shared-memory tile of the
+// block's footprint (clamp-to-edge); for 32-bit data at k <= 27 the window
+// width is a compile-time constant and each window row is unrolled.
 #include "mf_registry.h"
 
 namespace mf {
 
-constexpr int AM_BW = 32, AM_BH = 8, AM_NCAND = 4;
+constexpr int AM_BW = 32, AM_BH = 8;
 
-template <int DT>
-__global__ void __launch_bounds__(AM_BW *AM_BH) argmedian_kernel(ImgArgs a, int k) {
+// KC > 0: k fixed at compile time (every window loop unrolled, shared-memory
+// offsets constant); KC = 0: k at run time.
+template <int DT, int KC>
+__global__ void __launch_bounds__(AM_BW *AM_BH) argmedian_kernel(ImgArgs a, int k_rt) {
+    const int k = KC > 0 ? KC : k_rt;
     extern __shared__ __align__(16) uint32_t am_smem[];
     typedef typename Dt<DT>::E E;
     const int r = (k - 1) / 2;
@@ -35,29 +40,24 @@ __global__ void __launch_bounds__(AM_BW *AM_BH) argmedian_kernel(ImgArgs a, int 
     const char *dst = a.dst + (size_t)z * a.plane;
     const uint32_t v = Dt<DT>::key(reinterpret_cast<const E *>(dst + (size_t)y * a.pitch)[x]);
     const int m = (k * k - 1) / 2;
-    int below = 0, eq = 0;
-    int cand[AM_NCAND];
-#pragma unroll
-    for (int c = 0; c < AM_NCAND; c++) cand[c] = 0;
+    // one pass: keys below v, keys equal to v and the last equal slot --
+    // branch-free, so the unrolled row is straight-line code
+    int below = 0, eq = 0, last = -1;
+#pragma unroll 1
     for (int dy = 0; dy < k; dy++) {
         const uint32_t *row = am_smem + (threadIdx.y + dy) * SW + threadIdx.x;
+#pragma unroll
         for (int dx = 0; dx < k; dx++) {
             const uint32_t e = row[dx];
+            const bool same = e == v;
             below += e < v;
-            if (e == v) {
-#pragma unroll
-                for (int c = 0; c < AM_NCAND; c++)
-                    if (c == eq) cand[c] = dy * k + dx;
-                eq++;
-            }
+            eq += same;
+            last = same ? dy * k + dx : last;
         }
     }
     const int j = m - below;  // 0 <= j < eq when v is the window's median
-    int slot = -1;
-#pragma unroll
-    for (int c = 0; c < AM_NCAND; c++)
-        if (c == j) slot = cand[c];
-    if (j >= AM_NCAND) {  // many ties: find the j-th equal key in a second pass
+    int slot = j == eq - 1 ? last : -1;
+    if (slot < 0 && j >= 0 && j < eq) {  // ties after the median's own slot: find the j-th equal key
         int seen = 0;
         for (int dy = 0; dy < k && slot < 0; dy++) {
             const uint32_t *row = am_smem + (threadIdx.y + dy) * SW + threadIdx.x;
@@ -75,15 +75,41 @@ __global__ void __launch_bounds__(AM_BW *AM_BH) argmedian_kernel(ImgArgs a, int 
     reinterpret_cast<int32_t *>(idx + (size_t)y * a.idx_pitch)[x] = slot < 0 ? -1 : sy * a.W + sx;
 }
 
+template <int DT>
+static void (*pick_k(int k))(ImgArgs, int) {
+    switch (k) {  // the k of the data-oblivious range, where the value kernel is fast
+        case 3: return argmedian_kernel<DT, 3>;
+        case 5: return argmedian_kernel<DT, 5>;
+        case 7: return argmedian_kernel<DT, 7>;
+        case 9: return argmedian_kernel<DT, 9>;
+        case 11: return argmedian_kernel<DT, 11>;
+        case 13: return argmedian_kernel<DT, 13>;
+        case 15: return argmedian_kernel<DT, 15>;
+        case 17: return argmedian_kernel<DT, 17>;
+        case 19: return argmedian_kernel<DT, 19>;
+        case 21: return argmedian_kernel<DT, 21>;
+        case 23: return argmedian_kernel<DT, 23>;
+        case 25: return argmedian_kernel<DT, 25>;
+        case 27: return argmedian_kernel<DT, 27>;
+        default: return argmedian_kernel<DT, 0>;
+    }
+}
+
+// 32-bit data takes this pass at every k; 8/16-bit data only above the
+// record-carrying networks (k >= 27), where the run-time-k form serves
+static void (*pick_argmedian(int dtype, int k))(ImgArgs, int) {
+    return dtype == MF_U8 ? argmedian_kernel<MF_U8, 0>
+           : dtype == MF_U16 ? argmedian_kernel<MF_U16, 0>
+           : dtype == MF_U32 ? pick_k<MF_U32>(k)
+                             : pick_k<MF_F32>(k);
+}
+
 // a.dst must already hold the medians of a.src.
 int launch_argmedian_from_values(const ImgArgs &a, int channels, int k, int dtype, cudaStream_t s) {
     const size_t smem = (size_t)(AM_BW + k - 1) * (AM_BH + k - 1) * 4;
     dim3 grid((a.W + AM_BW - 1) / AM_BW, (a.H + AM_BH - 1) / AM_BH, channels);
     dim3 block(AM_BW, AM_BH);
-    void (*kern)(ImgArgs, int) = dtype == MF_U8 ? argmedian_kernel<MF_U8>
-                                 : dtype == MF_U16 ? argmedian_kernel<MF_U16>
-                                 : dtype == MF_U32 ? argmedian_kernel<MF_U32>
-                                                   : argmedian_kernel<MF_F32>;
+    void (*kern)(ImgArgs, int) = pick_argmedian(dtype, k);
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         set_error("argmedian smem: %s", cudaGetErrorString(cudaGetLastError()));
