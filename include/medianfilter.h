@@ -168,10 +168,10 @@ int mf_batch_describe(const mf_batch_plan *plan, int *kernels, long long *items)
  * until the library is unloaded.  Limits: at most 256 images, k = 1 or a
  * k the data-oblivious kernels are built for (odd 3 to 25 for every dtype,
  * 27 for 32-bit data), and at most 126,976 work items (one item is one
- * thread block's pixels: 128 x 8 for k = 3, 5 and 8/16-bit data, 64 x 8 for
- * 32-bit data; from k = 7, 256 x 16 for 8/16-bit data up to k = 21 (128 x 16
- * at k = 17), else 128 x 16; mf_describe names the kernel and its block);
- * beyond them it returns MF_ERR_ARG
+ * thread block's pixels -- lanes x block width x tile width by block height
+ * x tile height, as mf_describe reports them: from 64 x 8 (k = 3, 32-bit
+ * data) to 256 x 16 (k = 7, 8/16-bit data)); beyond them it returns
+ * MF_ERR_ARG
  * or MF_ERR_UNSUPPORTED with a message, before touching the device.
  * Nothing is allocated (no cudaMalloc, cudaFree or allocating library
  * call): the image table and work records are copied from the stack, the

@@ -50,7 +50,8 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # 2.56 ms); U = 2 loses (2.70 ms).  At k = 17 with 16-bit keys, blocks of
 # 16 x 8 threads (a 128 x 32 pixel region: less halo per pixel than 256 x 16)
 # run the 30 MP photo in 1.941 ms against 2.005 (32 x 4), 1.974 (16 x 4),
-# 1.961 (8 x 8); u32 4096^2 0.726 against 0.738 ms.  The direct kernel (form 8) wins where
+# 1.961 (8 x 8); u32 4096^2 0.726 against 0.738 ms.  The same shape gains
+# 1-6% at k = 9..15 (u32 k = 11: 0.422 -> 0.397 ms).  The direct kernel (form 8) wins where
 # staging dominates: k = 3 (u8 35.6 -> 25.0 us, u32 56.7 -> 35.4 us at
 # 4096^2) and 32-bit keys up to k = 9 (u32 k = 7 180 -> 121 us, k = 9 280 ->
 # 229 us); with packed 8/16-bit keys it ties at k = 5, 7 and spills at 9.
@@ -60,8 +61,8 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 O1_VALUE = {3: [(2, 2, 32, 4, -1, 8), (2, 2, 32, 4, -1, 0)],
             5: [(2, 2, 32, 4, -1, 0, 16), (2, 2, 32, 4, -1, 8, 32), (2, 2, 32, 4, -1, 0, 32)],
             7: [(4, 4, 32, 4, -1, 0, 16), (4, 4, 32, 4, -1, 8, 32), (4, 4, 32, 4, -1, 0, 32)],
-            9: [(4, 4, 32, 4, -1, 6, 16), (4, 4, 32, 4, -1, 8, 32), (4, 4, 32, 4, -1, 0, 32)],
-            11: [(4, 4, 32, 4, -1)], 13: [(4, 4, 32, 4, -1)], 15: [(4, 4, 32, 4, -1)],
+            9: [(4, 4, 16, 8, -1, 6, 16), (4, 4, 32, 4, -1, 8, 32), (4, 4, 32, 4, -1, 0, 32)],
+            11: [(4, 4, 16, 8, -1)], 13: [(4, 4, 16, 8, -1)], 15: [(4, 4, 16, 8, -1)],
             17: [(4, 4, 16, 8, 1, 6), (4, 4, 32, 4, 1, 6), (4, 4, 16, 4, 1, 6, 16), (4, 4, 32, 4, 0, 6)],
             19: [(4, 4, 32, 4, 0, 7, 16), (4, 4, 32, 4, 0, 6, 32), (4, 4, 32, 4, 1, 6)],
             21: [(4, 4, 32, 4, 0, 6, 16), (4, 4, 32, 4, 1, 6, 32)],
