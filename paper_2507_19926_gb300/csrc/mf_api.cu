@@ -342,6 +342,7 @@ int mf_median_filter_bwd(const float *grad_out, const int32_t *argidx, float *gr
                          mf_stream_t stream) {
     if (!grad_out || !argidx || !grad_in) { set_error("null pointer"); return MF_ERR_ARG; }
     if (H < 1 || W < 1 || channels < 1 || channels > 65535) { set_error("bad shape"); return MF_ERR_ARG; }
+    if ((long long)H * W > (1ll << 31) - 1) { set_error("plane too large for int32 indices"); return MF_ERR_ARG; }
     if (k < 1 || k > 75 || !(k & 1)) { set_error("k must be odd in 1..75"); return MF_ERR_ARG; }
     if (pitch < (size_t)W * 4 || pitch % 4) { set_error("bad pitch"); return MF_ERR_PITCH; }
     if (idx_pitch < (size_t)W * 4 || idx_pitch % 4) { set_error("bad idx_pitch"); return MF_ERR_PITCH; }

@@ -58,6 +58,13 @@ def test_rejects_bad_pitch_alias_dtype_shape(lib):
     assert lib.mf_median_filter(None, b, 8, 8, 8, 1, 0, 3, 0, None) == -1  # null
     assert lib.mf_median_filter_bwd(a, b, a, 8, 8, 32, 32, 1, 3, 0, None) == -4  # grad_in aliases
     assert lib.mf_median_filter_bwd(a, b, ctypes.c_void_p(0x5000000), 8, 8, 32, 32, 1, 3, 9, None) == -1
+    # a plane whose linear indices do not fit int32
+    far = ctypes.c_void_p(1 << 45)
+    assert lib.mf_median_filter_bwd(a, b, far, 65536, 65536, 1 << 18, 1 << 18, 1, 3, 1, None) == -1
+    # config entry: k = 1 and configurations past the last one are refused before any launch
+    assert lib.mf_median_filter_config(a, b, 8, 8, 8, 1, 0, 1, 0, None) == -9
+    assert lib.mf_median_filter_config(a, b, 8, 8, 8, 1, 0, 3, 99, None) == -9
+    assert lib.mf_median_filter_config(a, b, 8, 8, 8, 1, 0, 3, -1, None) == -9
 
 
 def test_describe_dispatch(lib):
