@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -151,6 +152,19 @@ int resolve_variant(int k, int dtype, bool arg, int variant, const O1Entry **o1)
     return p.variant;
 }
 
+// The value (or record) kernel the variant resolves to, on prepared args.
+static int launch_resolved(const ImgArgs &a, int C, int k, int dtype, int variant, cudaStream_t s) {
+    Plan p;
+    int rc = resolve(k, dtype, a.idx != nullptr, variant, &p);
+    if (rc) return rc;
+    if (p.variant == MF_OBLIVIOUS) {
+        rc = p.o1->launch(a, C, s);
+        if (rc == MF_ERR_CUDA) set_error("%s: %s", p.o1->name, cudaGetErrorString(cudaGetLastError()));
+        return rc;
+    }
+    return d1_launch(a, C, k, dtype, p.tile, s);
+}
+
 static int run_filter(const void *src, void *dst, int H, int W, size_t pitch, int C, int dtype, int k,
                       int variant, int32_t *idx, size_t idx_pitch, cudaStream_t s) {
     ImgArgs a;
@@ -158,6 +172,8 @@ static int run_filter(const void *src, void *dst, int H, int W, size_t pitch, in
     a.dst = (char *)dst;
     a.idx = idx;
     a.H = H;
+    a.y_lo = 0;
+    a.y_hi = H - 1;
     a.W = W;
     a.pitch = pitch;
     a.plane = (size_t)H * pitch;
@@ -180,15 +196,31 @@ static int run_filter(const void *src, void *dst, int H, int W, size_t pitch, in
         if (rc) return rc;
         return launch_argmedian_from_values(a, C, k, dtype, s);
     }
-    Plan p;
-    int rc = resolve(k, dtype, idx != nullptr, variant, &p);
-    if (rc) return rc;
-    if (p.variant == MF_OBLIVIOUS) {
-        rc = p.o1->launch(a, C, s);
-        if (rc == MF_ERR_CUDA) set_error("%s: %s", p.o1->name, cudaGetErrorString(cudaGetLastError()));
-        return rc;
+    return launch_resolved(a, C, k, dtype, variant, s);
+}
+
+// Rows y0 .. y0 + h - 1 of one plane of H_img rows, all of which are valid
+// input (the rows around the band feed its windows): the host pipeline's
+// unit of work.
+static int run_filter_band(const char *src, char *dst, int H_img, int W, size_t pitch, int dtype, int k,
+                           int variant, int y0, int h, cudaStream_t s) {
+    if (k == 1) {
+        cudaError_t e = cudaMemcpy2DAsync(dst + (size_t)y0 * pitch, pitch, src + (size_t)y0 * pitch, pitch,
+                                          (size_t)W * esize(dtype), (size_t)h, cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? MF_OK : cuda_fail(e, "identity copy");
     }
-    return d1_launch(a, C, k, dtype, p.tile, s);
+    ImgArgs a;
+    a.src = src + (size_t)y0 * pitch;
+    a.dst = dst + (size_t)y0 * pitch;
+    a.idx = nullptr;
+    a.H = h;
+    a.W = W;
+    a.y_lo = -y0;
+    a.y_hi = H_img - 1 - y0;
+    a.pitch = pitch;
+    a.plane = (size_t)H_img * pitch;
+    a.idx_pitch = a.idx_plane = 0;
+    return launch_resolved(a, 1, k, dtype, variant, s);
 }
 
 }  // namespace mf
@@ -234,6 +266,8 @@ int mf_median_filter_tile(const void *src, void *dst, int H, int W, size_t pitch
     a.dst = (char *)dst;
     a.idx = nullptr;
     a.H = H;
+    a.y_lo = 0;
+    a.y_hi = H - 1;
     a.W = W;
     a.pitch = pitch;
     a.plane = (size_t)H * pitch;
@@ -256,6 +290,8 @@ int mf_median_filter_config(const void *src, void *dst, int H, int W, size_t pit
     a.dst = (char *)dst;
     a.idx = nullptr;
     a.H = H;
+    a.y_lo = 0;
+    a.y_hi = H - 1;
     a.W = W;
     a.pitch = pitch;
     a.plane = (size_t)H * pitch;
@@ -267,14 +303,17 @@ int mf_median_filter_config(const void *src, void *dst, int H, int W, size_t pit
 
 // Device staging buffers and streams of the host entry point (one set per
 // process, grown on demand, serialised by a mutex, released by
-// mf_shutdown).  Planes are independent, so the copies of one plane overlap
-// the filtering of its neighbours: plane c is uploaded on stream c % 3 while
-// earlier planes are filtered and downloaded.
+// mf_shutdown).  The planes are cut into bands of whole rows (about 8 MB of
+// input each) that flow through three streams: uploads, filtering and
+// downloads.  A band is filtered as soon as its rows and the r rows below
+// it are on the device (each row is uploaded once), and downloaded as soon
+// as it is filtered, so only the first band's upload and the last band's
+// download are not hidden behind the filtering of other bands.
 static std::mutex g_stage_mu;
 static void *g_stage_src = nullptr, *g_stage_dst = nullptr;
 static size_t g_stage_bytes = 0;
-static cudaStream_t g_stage_streams[3] = {nullptr, nullptr, nullptr};
-static cudaEvent_t g_stage_events[3] = {nullptr, nullptr, nullptr};
+static cudaStream_t g_stage_streams[3] = {nullptr, nullptr, nullptr};  // uploads, filtering, downloads
+static cudaEvent_t g_stage_events[3] = {nullptr, nullptr, nullptr};    // start, uploaded, filtered
 
 int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, size_t pitch,
                           int channels, mf_dtype dtype, int k, mf_border border,
@@ -284,6 +323,10 @@ int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, si
     if (es == 0) { set_error("unknown dtype %d", dtype); return MF_ERR_DTYPE; }
     if (H < 1 || W < 1 || channels < 1) { set_error("bad shape"); return MF_ERR_ARG; }
     if (pitch < (size_t)W * es || pitch % es) { set_error("bad pitch"); return MF_ERR_PITCH; }
+    if (variant != MF_AUTO && variant != MF_OBLIVIOUS && variant != MF_DATA_AWARE) {
+        set_error("unknown variant %d", (int)variant);
+        return MF_ERR_ARG;
+    }
     const size_t dpitch = ((size_t)W * es + 255) & ~(size_t)255;
     const size_t plane = (size_t)H * dpitch;
     const size_t bytes = (size_t)channels * plane;
@@ -302,6 +345,9 @@ int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, si
         }
         g_stage_bytes = bytes;
     }
+    // the same checks as the device entry points (k, border, sizes)
+    int rc = check_fwd(g_stage_src, g_stage_dst, H, W, dpitch, channels, dtype, k, border, nullptr, 0);
+    if (rc) return rc;
     if (!g_stage_streams[0]) {
         for (int i = 0; i < 3; i++) {
             if (cudaStreamCreateWithFlags(&g_stage_streams[i], cudaStreamNonBlocking) != cudaSuccess ||
@@ -311,24 +357,42 @@ int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, si
             }
         }
     }
+    cudaStream_t s_in = g_stage_streams[0], s_k = g_stage_streams[1], s_out = g_stage_streams[2];
     // the pipeline starts after work already queued on the caller's stream
     cudaError_t e = cudaEventRecord(g_stage_events[0], s);
     for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaStreamWaitEvent(g_stage_streams[i], g_stage_events[0], 0);
     if (e != cudaSuccess) return cuda_fail(e, "pipeline start");
+    const size_t row_bytes = (size_t)W * es;
+    int bh = (int)std::min<size_t>((size_t)H, std::max<size_t>(32, ((size_t)8 << 20) / row_bytes / 32 * 32));
+    const int r = (k - 1) / 2;
     const char *hs = (const char *)src_host;
     char *hd = (char *)dst_host;
     for (int c = 0; c < channels; c++) {
-        cudaStream_t sc = g_stage_streams[c % 3];
         char *ds = (char *)g_stage_src + c * plane, *dd = (char *)g_stage_dst + c * plane;
-        e = cudaMemcpy2DAsync(ds, dpitch, hs + (size_t)c * H * pitch, pitch, (size_t)W * es, H,
-                              cudaMemcpyHostToDevice, sc);
-        if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
-        int rc = mf_median_filter_ex(ds, dd, H, W, dpitch, 1, dtype, k, border, variant, nullptr, 0,
-                                     (mf_stream_t)sc);
-        if (rc) return rc;
-        e = cudaMemcpy2DAsync(hd + (size_t)c * H * pitch, pitch, dd, dpitch, (size_t)W * es, H,
-                              cudaMemcpyDeviceToHost, sc);
-        if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+        const char *hsc = hs + (size_t)c * H * pitch;
+        char *hdc = hd + (size_t)c * H * pitch;
+        int uploaded = 0;  // rows of this plane already on the device
+        for (int y0 = 0; y0 < H; y0 += bh) {
+            const int h = std::min(bh, H - y0);
+            const int need = std::min(H, y0 + h + r);
+            if (need > uploaded) {
+                e = cudaMemcpy2DAsync(ds + (size_t)uploaded * dpitch, dpitch, hsc + (size_t)uploaded * pitch, pitch,
+                                      row_bytes, (size_t)(need - uploaded), cudaMemcpyHostToDevice, s_in);
+                if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
+                uploaded = need;
+            }
+            e = cudaEventRecord(g_stage_events[1], s_in);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s_k, g_stage_events[1], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "pipeline order");
+            rc = run_filter_band(ds, dd, H, W, dpitch, dtype, k, variant, y0, h, s_k);
+            if (rc) return rc;
+            e = cudaEventRecord(g_stage_events[2], s_k);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, g_stage_events[2], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "pipeline order");
+            e = cudaMemcpy2DAsync(hdc + (size_t)y0 * pitch, pitch, dd + (size_t)y0 * dpitch, dpitch, row_bytes,
+                                  (size_t)h, cudaMemcpyDeviceToHost, s_out);
+            if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
+        }
     }
     for (int i = 0; i < 3; i++) {
         e = cudaStreamSynchronize(g_stage_streams[i]);

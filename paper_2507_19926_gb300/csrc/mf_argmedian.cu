@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(AM_BW *AM_BH) argmedian_kernel(ImgArgs a, int 
     const int tid = threadIdx.y * AM_BW + threadIdx.x;
     for (int i = tid; i < SW * SH; i += AM_BW * AM_BH) {
         const int sy = i / SW, sx = i - sy * SW;
-        const int y = clampi(y0 - r + sy, 0, a.H - 1), x = clampi(x0 - r + sx, 0, a.W - 1);
+        const int y = clampi(y0 - r + sy, a.y_lo, a.y_hi), x = clampi(x0 - r + sx, 0, a.W - 1);
         am_smem[i] = Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, x));
     }
     __syncthreads();
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(AM_BW *AM_BH) argmedian_kernel(ImgArgs a, int 
             }
         }
     }
-    const int sy = clampi(y - r + slot / k, 0, a.H - 1);
+    const int sy = clampi(y - r + slot / k, a.y_lo, a.y_hi);
     const int sx = clampi(x - r + slot % k, 0, a.W - 1);
     char *idx = reinterpret_cast<char *>(a.idx) + (size_t)z * a.idx_plane;
     reinterpret_cast<int32_t *>(idx + (size_t)y * a.idx_pitch)[x] = slot < 0 ? -1 : sy * a.W + sx;

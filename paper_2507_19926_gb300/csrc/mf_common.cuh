@@ -7,6 +7,7 @@
 // are bit-identical values.  Min/max networks on keys therefore select the
 // exact input element (paper Sec. 4: networks compile to min/max sequences).
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -106,15 +107,19 @@ __host__ __device__ __forceinline__ int clampi(int v, int lo, int hi) {
 
 template <class E>
 __device__ __forceinline__ E ldg_elem(const char *plane, size_t pitch, int y, int x) {
-    return __ldg(reinterpret_cast<const E *>(plane + (size_t)y * pitch) + x);
+    return __ldg(reinterpret_cast<const E *>(plane + (ptrdiff_t)y * (ptrdiff_t)pitch) + x);  // y may be < 0 in a band
 }
 
-// Launch arguments common to all image kernels.
+// Launch arguments common to all image kernels.  src and dst point at the
+// first row to filter; H rows are filtered.  Reads clamp to rows y_lo..y_hi
+// relative to src: 0..H-1 for a whole image, wider when the rows are a band
+// of a larger image whose neighbouring rows are valid input.
 struct ImgArgs {
     const char *src;
     char *dst;
     int32_t *idx;       // argmedian output or nullptr
     int H, W;
+    int y_lo, y_hi;     // readable rows for clamp-to-edge, relative to src
     size_t pitch;       // bytes per row, src and dst
     size_t plane;       // bytes per plane = H * pitch
     size_t idx_pitch;   // bytes per row of idx

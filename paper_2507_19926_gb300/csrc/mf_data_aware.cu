@@ -87,7 +87,7 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
     // footprint of the strip, clamped to the image
     for (int i = tid; i < FW * FH; i += NT) {
         const int fy = i / FW, fx = i - fy * FW;
-        const int y = clampi(y0 - R + fy, 0, a.H - 1);
+        const int y = clampi(y0 - R + fy, a.y_lo, a.y_hi);
         const int x = clampi(x0 - R + fx, 0, a.W - 1);
         sm[i] = D1Key<DT, KT, ARG>::make(Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, x)), i);
     }
@@ -118,7 +118,7 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
             const int fidx = (int)((unsigned long long)v & ((1ull << IB) - 1));
             const uint32_t key = (uint32_t)((unsigned long long)v >> IB);
             const int fy = fidx / FW, fx = fidx - fy * FW;
-            const int ys = clampi(y0 - R + fy, 0, a.H - 1), xs = clampi(x0 - R + fx, 0, a.W - 1);
+            const int ys = clampi(y0 - R + fy, a.y_lo, a.y_hi), xs = clampi(x0 - R + fx, 0, a.W - 1);
             if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
             if (idx) reinterpret_cast<int32_t *>(idx + (size_t)y * a.idx_pitch)[x] = ys * a.W + xs;
         }

@@ -147,7 +147,7 @@ struct O1Store {
                 const uint32_t fidx = (uint32_t)(w & ((1ull << IB) - 1));
                 const uint32_t key = (uint32_t)(w >> IB);
                 const int fy = fidx / L::FW, gx = fidx - fy * L::FW;
-                const int ys = clampi(by0 - L::R + fy, 0, a.H - 1);
+                const int ys = clampi(by0 - L::R + fy, a.y_lo, a.y_hi);
                 const int xs = clampi(bx0 - L::R + gx, 0, a.W - 1);
                 if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
                 if (idx) reinterpret_cast<int32_t *>(idx + (size_t)y * a.idx_pitch)[x] = ys * a.W + xs;
@@ -199,12 +199,12 @@ __device__ __forceinline__ void o1_block_direct(const ImgArgs &a, int bxi, int b
     // footprint in registers.  Inside the image every row is one pointer and
     // the columns are constant offsets from it; near the border each column
     // and row is clamped.
-    const bool inside = x0 - R >= 0 && x0 + (P - 1) * LX - R + RL::FW - 1 < a.W && y0 - R >= 0 &&
-                        y0 - R + RL::FH - 1 < a.H;
+    const bool inside = x0 - R >= 0 && x0 + (P - 1) * LX - R + RL::FW - 1 < a.W && y0 - R >= a.y_lo &&
+                        y0 - R + RL::FH - 1 <= a.y_hi;
     if (inside) {
 #pragma unroll
         for (int fy = 0; fy < RL::FH; fy++) {
-            const E *row = reinterpret_cast<const E *>(src + (size_t)(y0 - R + fy) * a.pitch) + (x0 - R);
+            const E *row = reinterpret_cast<const E *>(src + (ptrdiff_t)(y0 - R + fy) * (ptrdiff_t)a.pitch) + (x0 - R);
 #pragma unroll
             for (int fx = 0; fx < RL::FW; fx++)
                 f[RL::px(fy, fx)] = O1Words<DT, KO, false, 0>::template make<RL>(row, fx, fx + LX, 0, 0);
@@ -218,7 +218,7 @@ __device__ __forceinline__ void o1_block_direct(const ImgArgs &a, int bxi, int b
         }
 #pragma unroll
         for (int fy = 0; fy < RL::FH; fy++) {
-            const E *row = reinterpret_cast<const E *>(src + (size_t)clampi(y0 - R + fy, 0, a.H - 1) * a.pitch);
+            const E *row = reinterpret_cast<const E *>(src + (ptrdiff_t)clampi(y0 - R + fy, a.y_lo, a.y_hi) * (ptrdiff_t)a.pitch);
 #pragma unroll
             for (int fx = 0; fx < RL::FW; fx++)
                 f[RL::px(fy, fx)] = O1Words<DT, KO, false, 0>::template make<RL>(row, xc0[fx], xc1[fx], 0, 0);
@@ -294,8 +294,8 @@ __device__ __forceinline__ void o1_block(const ImgArgs &a, int bxi, int byi, int
         for (int j = 0; j < RG; j++) {
             const int fy = g * RG + j;
             if (RG * NRG != L::FH && fy >= L::FH) break;
-            const int y = clampi(by0 - L::R + fy, 0, a.H - 1);
-            const E *row = reinterpret_cast<const E *>(src + (size_t)y * a.pitch);
+            const int y = clampi(by0 - L::R + fy, a.y_lo, a.y_hi);
+            const E *row = reinterpret_cast<const E *>(src + (ptrdiff_t)y * (ptrdiff_t)a.pitch);
             sm[fy * L::RS + sw] = O1Words<DT, KO, ARG, IB>::template make<L>(row, x0, x1, fy, gx);
         }
     }

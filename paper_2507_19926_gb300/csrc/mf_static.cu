@@ -160,6 +160,8 @@ extern "C" int mf_batch_run_static(const mf_image_desc *descs, int n, mf_stream_
         a.dst = (char *)d.dst;
         a.idx = nullptr;
         a.H = d.H;
+        a.y_lo = 0;
+        a.y_hi = d.H - 1;
         a.W = d.W;
         a.pitch = d.pitch;
         a.plane = (size_t)d.H * d.pitch;

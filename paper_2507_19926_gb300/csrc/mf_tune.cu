@@ -138,6 +138,8 @@ extern "C" int mf_autotune(const void *src, void *dst, int H, int W, size_t pitc
     a.dst = (char *)dst;
     a.idx = nullptr;
     a.H = H;
+    a.y_lo = 0;
+    a.y_hi = H - 1;
     a.W = W;
     a.pitch = pitch;
     a.plane = (size_t)H * pitch;

@@ -1,5 +1,6 @@
-"""The host-buffer entry point (copies inside, planes pipelined over
-streams) against the oracle, with padded host pitches and several planes."""
+"""The host-buffer entry point (copies inside, planes cut into row bands
+pipelined over streams) against the oracle, with padded host pitches,
+several planes and planes of several bands."""
 import ctypes
 
 import numpy as np
@@ -26,3 +27,30 @@ def test_host_entry_point(dt, k, C):
     want = oracle.median_filter(x, k)
     assert np.array_equal(dst[:, :, :133].view(np.uint8), want.view(np.uint8))
     assert (dst[:, :, 133:].view(np.uint8) == 0).all()
+
+
+@pytest.mark.parametrize("dt,k,C,H,W", [("u8", 17, 2, 4500, 4096), ("u32", 31, 1, 2300, 2048),
+                                        ("f32", 3, 1, 5000, 1700), ("u16", 45, 1, 2600, 3000)])
+def test_host_entry_point_bands(dt, k, C, H, W):
+    """Planes larger than one band (about 8 MB of input): the rows around
+    every band boundary against the oracle, every row against the device
+    entry point."""
+    import torch
+    from gpu_util import to_dev, to_host
+    ensure_lib()
+    x = synth.uniform((C, H, W), dt, 950 + k)
+    dst = np.zeros_like(x)
+    es = x.itemsize
+    code = {"u8": 0, "u16": 1, "u32": 2, "f32": 3}[dt]
+    mf.mf_median_filter_host(x.ctypes.data, dst.ctypes.data, H, W, W * es, C, code, k)
+    bh = max(32, (8 << 20) // (W * es) // 32 * 32)
+    assert bh < H  # several bands
+    r = (k - 1) // 2
+    rows = sorted({y for b in range(bh, H, bh) for y in range(b - r - 1, b + r + 1) if 0 <= y < H} | {0, H - 1})
+    want_rows = oracle.median_filter_rows(x, k, np.array(rows, np.int32))
+    assert np.array_equal(dst[:, rows, :].view(np.uint8), want_rows.view(np.uint8))
+    xd = to_dev(x)
+    yd = torch.empty_like(xd)
+    mf.mf_median_filter(xd.data_ptr(), yd.data_ptr(), H, W, W * es, C, code, k)
+    torch.cuda.synchronize()
+    assert np.array_equal(dst.view(np.uint8), np.ascontiguousarray(to_host(yd, None)).view(np.uint8))
