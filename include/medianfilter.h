@@ -117,9 +117,10 @@ int mf_median_filter_bwd(const float *grad_out, const int32_t *argidx, float *gr
 /* The same filter on HOST buffers: copies src (pitch bytes per row) to the
  * device, filters, copies the result back into dst (host) and waits for
  * completion.  Each plane is cut into bands of whole rows (about 8 MB of
- * input each) that flow through three internal streams -- uploads,
- * filtering, downloads -- so that only the first band's upload and the last
- * band's download are not overlapped; a band is filtered once its rows and
+ * input each) that flow through internal streams -- uploads, two filtering
+ * streams taking bands in turn, downloads -- so that only the first band's
+ * upload and the last band's download are not overlapped; a band is
+ * filtered once its rows and
  * the (k-1)/2 rows below it are on the device.  The pipeline starts after
  * whatever is already queued on `stream`.  Host buffers are
  * caller-owned; page-locked memory makes the copies asynchronous DMA.

@@ -304,15 +304,16 @@ int mf_median_filter_config(const void *src, void *dst, int H, int W, size_t pit
 // Device staging buffers and streams of the host entry point (one set per
 // process, grown on demand, serialised by a mutex, released by
 // mf_shutdown).  The planes are cut into bands of whole rows (about 8 MB of
-// input each) that flow through three streams: uploads, filtering and
-// downloads.  A band is filtered as soon as its rows and the r rows below
-// it are on the device (each row is uploaded once), and downloaded as soon
-// as it is filtered, so only the first band's upload and the last band's
-// download are not hidden behind the filtering of other bands.
+// input each) that flow through four streams: uploads, two filtering
+// streams taking bands in turn (so the tail of one band's kernel overlaps
+// the next band's), and downloads.  A band is filtered as soon as its rows
+// and the r rows below it are on the device (each row is uploaded once),
+// and downloaded as soon as it is filtered, so only the first band's upload
+// and the last band's download are not hidden behind the filtering.
 static std::mutex g_stage_mu;
 static void *g_stage_src = nullptr, *g_stage_dst = nullptr;
 static size_t g_stage_bytes = 0;
-static cudaStream_t g_stage_streams[3] = {nullptr, nullptr, nullptr};  // uploads, filtering, downloads
+static cudaStream_t g_stage_streams[4] = {nullptr, nullptr, nullptr, nullptr};  // uploads, filtering x 2, downloads
 static cudaEvent_t g_stage_events[3] = {nullptr, nullptr, nullptr};    // start, uploaded, filtered
 
 int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, size_t pitch,
@@ -349,18 +350,19 @@ int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, si
     int rc = check_fwd(g_stage_src, g_stage_dst, H, W, dpitch, channels, dtype, k, border, nullptr, 0);
     if (rc) return rc;
     if (!g_stage_streams[0]) {
-        for (int i = 0; i < 3; i++) {
+        for (int i = 0; i < 4; i++) {
             if (cudaStreamCreateWithFlags(&g_stage_streams[i], cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&g_stage_events[i], cudaEventDisableTiming) != cudaSuccess) {
+                (i < 3 && cudaEventCreateWithFlags(&g_stage_events[i], cudaEventDisableTiming) != cudaSuccess)) {
                 set_error("cannot create staging streams: %s", cudaGetErrorString(cudaGetLastError()));
                 return MF_ERR_CUDA;
             }
         }
     }
-    cudaStream_t s_in = g_stage_streams[0], s_k = g_stage_streams[1], s_out = g_stage_streams[2];
+    cudaStream_t s_in = g_stage_streams[0], s_out = g_stage_streams[3];
+    int band = 0;
     // the pipeline starts after work already queued on the caller's stream
     cudaError_t e = cudaEventRecord(g_stage_events[0], s);
-    for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaStreamWaitEvent(g_stage_streams[i], g_stage_events[0], 0);
+    for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaStreamWaitEvent(g_stage_streams[i], g_stage_events[0], 0);
     if (e != cudaSuccess) return cuda_fail(e, "pipeline start");
     const size_t row_bytes = (size_t)W * es;
     int bh = (int)std::min<size_t>((size_t)H, std::max<size_t>(32, ((size_t)8 << 20) / row_bytes / 32 * 32));
@@ -381,6 +383,8 @@ int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, si
                 if (e != cudaSuccess) return cuda_fail(e, "host to device copy");
                 uploaded = need;
             }
+            cudaStream_t s_k = g_stage_streams[1 + (band++ & 1)];
+            // each wait takes the event's latest record at the time it is enqueued
             e = cudaEventRecord(g_stage_events[1], s_in);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s_k, g_stage_events[1], 0);
             if (e != cudaSuccess) return cuda_fail(e, "pipeline order");
@@ -394,7 +398,7 @@ int mf_median_filter_host(const void *src_host, void *dst_host, int H, int W, si
             if (e != cudaSuccess) return cuda_fail(e, "device to host copy");
         }
     }
-    for (int i = 0; i < 3; i++) {
+    for (int i = 0; i < 4; i++) {
         e = cudaStreamSynchronize(g_stage_streams[i]);
         if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
     }
@@ -468,10 +472,12 @@ int mf_shutdown(void) {
     if (g_stage_dst) cudaFree(g_stage_dst);
     g_stage_src = g_stage_dst = nullptr;
     g_stage_bytes = 0;
-    for (int i = 0; i < 3; i++) {
+    for (int i = 0; i < 4; i++) {
         if (g_stage_streams[i]) cudaStreamDestroy(g_stage_streams[i]);
-        if (g_stage_events[i]) cudaEventDestroy(g_stage_events[i]);
         g_stage_streams[i] = nullptr;
+    }
+    for (int i = 0; i < 3; i++) {
+        if (g_stage_events[i]) cudaEventDestroy(g_stage_events[i]);
         g_stage_events[i] = nullptr;
     }
     d1_release_all();
