@@ -170,8 +170,8 @@ int mf_batch_describe(const mf_batch_plan *plan, int *kernels, long long *items)
  * data-oblivious kernels, taking its work queues from one fixed array of
  * 2 MiB that the library's module holds on every device where it is used,
  * until the library is unloaded.  Limits: at most 256 images, k = 1 or a
- * k the data-oblivious kernels are built for (odd 3 to 25 for every dtype,
- * 27 for 32-bit data), and at most 126,976 work items (one item is one
+ * k the data-oblivious kernels are built for (odd 3 to 27), and at most
+ * 126,976 work items (one item is one
  * thread block's pixels -- lanes x block width x tile width by block height
  * x tile height, as mf_describe reports them: from 64 x 8 (k = 3, 32-bit
  * data) to 256 x 16 (k = 7, 8/16-bit data)); beyond them it returns

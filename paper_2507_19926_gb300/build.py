@@ -55,9 +55,10 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # staging dominates: k = 3 (u8 35.6 -> 25.0 us, u32 56.7 -> 35.4 us at
 # 4096^2) and 32-bit keys up to k = 9 (u32 k = 7 180 -> 121 us, k = 9 280 ->
 # 229 us); with packed 8/16-bit keys it ties at k = 5, 7 and spills at 9.
-# k = 27 is built for 32-bit keys only: 3.64 ms against 7.62 ms for the best
-# data-aware tile (u32 4096^2); for u8 the gain is 4.03 vs 5.02 ms and at
-# k = 29 the data-aware kernel wins for u8 -- not worth the compile time.
+# k = 27: 3.64 ms against 7.62 ms for the best data-aware tile (u32 4096^2),
+# u8 4.03 vs 5.02 ms (one tile a thread on 32-bit keys); at k = 29 the
+# data-aware kernel wins for u8 and the spilling network gains too little
+# for 32-bit keys to pay its compile time.
 O1_VALUE = {3: [(2, 2, 32, 4, -1, 8), (2, 2, 32, 4, -1, 0)],
             5: [(2, 2, 32, 4, -1, 0, 16), (2, 2, 32, 4, -1, 8, 32), (2, 2, 32, 4, -1, 0, 32)],
             7: [(4, 4, 32, 4, -1, 0, 16), (4, 4, 32, 4, -1, 8, 32), (4, 4, 32, 4, -1, 0, 32)],
@@ -68,7 +69,7 @@ O1_VALUE = {3: [(2, 2, 32, 4, -1, 8), (2, 2, 32, 4, -1, 0)],
             21: [(4, 4, 32, 4, 0, 6, 16), (4, 4, 32, 4, 1, 6, 32)],
             23: [(4, 4, 32, 4, 1, 6, 1), (4, 4, 32, 4, 1, 6, 32), (4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 6, 16)],
             25: [(4, 4, 32, 4, 1, 6, 1), (4, 4, 32, 4, 1, 6, 32), (4, 4, 32, 4, 0, 6, 1), (4, 4, 32, 4, 0, 0, 16)],
-            27: [(4, 4, 32, 4, 1, 6, 32)]}
+            27: [(4, 4, 32, 4, 1, 6, 32), (4, 4, 32, 4, 1, 6, 1)]}
 # extra configurations for timing (comma list "k:tw:th:bx:by:U[:R[:keys]]"
 # in MF_O1_EXTRA).  R is the network form, a bit set: 1 = the root extra
 # rows are sorted into shared memory by a stage of their own (netgen.build
