@@ -224,12 +224,16 @@ def kernel_source_hash(fn_name):
     if not os.path.isdir(GEN):
         return None
     needle = "int %s(" % fn_name
+    root = os.path.dirname(HERE)
+    # include paths name this checkout's location: hash them relative to it,
+    # so that every checkout of the same sources gives the same hash
+    flags = [f.replace(root, "<repo>") for f in NVCC_FLAGS + ARCH]
     for name in sorted(os.listdir(GEN)):
         if name.startswith("o1_k") and name.endswith(".cu"):
             path = os.path.join(GEN, name)
             with open(path) as f:
                 if needle in f.read():
-                    return _flags_hash(path, NVCC_FLAGS + ARCH)
+                    return _flags_hash(path, flags)
     return None
 
 
