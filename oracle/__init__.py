@@ -58,6 +58,7 @@ def _load():
             lib = ctypes.CDLL(_LIB)
             vp, i32, u32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32
             lib.or_median_filter.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32]
+            lib.or_median_filter_rect.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32]
             lib.or_median_filter_rows.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, vp, i32, i32]
             lib.or_median_backward.argtypes = [vp, vp, vp, i32, i32, i32]
             lib.or_key.argtypes = [i32, u32]
@@ -83,22 +84,26 @@ def _as_chw(x):
     return x, False
 
 
-def median_filter(x, k, with_idx=False, threads=0):
-    """Clamp-to-edge k x k median of every plane of x ((H, W) or (C, H, W)).
+def median_filter(x, k, with_idx=False, threads=0, kh=None):
+    """Clamp-to-edge k x k median of every plane of x ((H, W) or (C, H, W));
+    with kh, a window of k columns by kh rows (paper Sec. 3.2 states the tile
+    terminology for a k_w x k_h kernel).
 
     Returns the filtered array (same dtype, bit-copied winners), and with
-    ``with_idx`` also the int32 argmedian ys*W + xs per output pixel.
+    ``with_idx`` also the int32 argmedian ys*W + xs per output pixel
+    (window slots row-major: (dy+ry)*k + (dx+rx)).
     """
     lib = _load()
     xc, squeeze = _as_chw(x)
     C, H, W = xc.shape
     out = np.empty_like(xc)
     idx = np.empty((C, H, W), np.int32) if with_idx else None
-    rc = lib.or_median_filter(xc.ctypes.data, out.ctypes.data,
-                              idx.ctypes.data if with_idx else None,
-                              H, W, C, DTYPES[_dtype_name(xc)], int(k), int(threads))
+    kh = k if kh is None else kh
+    rc = lib.or_median_filter_rect(xc.ctypes.data, out.ctypes.data,
+                                   idx.ctypes.data if with_idx else None,
+                                   H, W, C, DTYPES[_dtype_name(xc)], int(k), int(kh), int(threads))
     if rc != 0:
-        raise ValueError("oracle rejected arguments (H=%d W=%d C=%d k=%d)" % (H, W, C, k))
+        raise ValueError("oracle rejected arguments (H=%d W=%d C=%d k=%d kh=%d)" % (H, W, C, k, kh))
     if squeeze:
         out = out[0]
         idx = idx[0] if with_idx else None

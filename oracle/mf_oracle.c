@@ -24,6 +24,12 @@
  * The median value is copied bit-for-bit from the winning source pixel:
  * selection performs no arithmetic.
  *
+ * Rectangular windows (or_median_filter_rect): the paper states its tile
+ * terminology for a k_w x k_h kernel (Sec. 3.2); the same definition with
+ * kw columns and kh rows (both odd) takes the element of 0-based rank
+ * (kw*kh-1)/2 of window slots s = (dy+ry)*kw + (dx+rx), rx = (kw-1)/2,
+ * ry = (kh-1)/2.  k x k is the case kw = kh = k.
+ *
  * Backward (derivative of the filter w.r.t. its input): the median is, piece
  * by piece, the identity on the selected input, so d out[q] / d in[p] is 1
  * when p = idx[q] and 0 otherwise; grad_in[p] = sum of grad_out[q] over the
@@ -103,21 +109,21 @@ static uint64_t select_rank(uint64_t *a, int n, int m)
 /* Median (and argmedian) of one output pixel (y, x) of one plane.
  * win is scratch of k*k entries.  Each entry is the composite
  * (key << 32) | slot, so sorting entries sorts by key, then by slot. */
-static void one_pixel(const void *plane, int H, int W, int dtype, int k, int y, int x,
+static void one_pixel(const void *plane, int H, int W, int dtype, int kw, int kh, int y, int x,
                       uint64_t *win, long *src_index)
 {
-    int r = (k - 1) / 2, s = 0;
-    for (int dy = -r; dy <= r; dy++) {
+    int rx = (kw - 1) / 2, ry = (kh - 1) / 2, s = 0;
+    for (int dy = -ry; dy <= ry; dy++) {
         int ys = clampi(y + dy, 0, H - 1);
-        for (int dx = -r; dx <= r; dx++) {
+        for (int dx = -rx; dx <= rx; dx++) {
             int xs = clampi(x + dx, 0, W - 1);
             win[s] = ((uint64_t)key_at(plane, (long)ys * W + xs, dtype) << 32) | (uint64_t)s;
             s++;
         }
     }
-    uint64_t best = select_rank(win, k * k, (k * k - 1) / 2);
+    uint64_t best = select_rank(win, kw * kh, (kw * kh - 1) / 2);
     int slot = (int)(best & 0xffffffffu);
-    int dy = slot / k - r, dx = slot % k - r;
+    int dy = slot / kw - ry, dx = slot % kw - rx;
     *src_index = (long)clampi(y + dy, 0, H - 1) * W + clampi(x + dx, 0, W - 1);
 }
 
@@ -127,13 +133,14 @@ static int check_args(int H, int W, int C, int dtype, int k)
     return 0;
 }
 
-/* Median filter of C planes of H x W.  dst may be NULL (argmedian only);
- * idx may be NULL (values only).  nthreads <= 0 means the OpenMP default.
- * Returns 0, or -1 on a bad argument. */
-int or_median_filter(const void *src, void *dst, int32_t *idx, int H, int W, int C,
-                     int dtype, int k, int nthreads)
+/* Median filter of C planes of H x W with a kw x kh window (both odd).
+ * dst may be NULL (argmedian only); idx may be NULL (values only).
+ * nthreads <= 0 means the OpenMP default.  Returns 0, or -1 on a bad
+ * argument. */
+int or_median_filter_rect(const void *src, void *dst, int32_t *idx, int H, int W, int C,
+                          int dtype, int kw, int kh, int nthreads)
 {
-    if (check_args(H, W, C, dtype, k)) return -1;
+    if (check_args(H, W, C, dtype, kw) || kh < 1 || (kh & 1) == 0) return -1;
     int es = elem_size(dtype);
     long plane_elems = (long)H * W;
     long rows = (long)C * H;
@@ -142,7 +149,7 @@ int or_median_filter(const void *src, void *dst, int32_t *idx, int H, int W, int
 #pragma omp parallel num_threads(nthreads)
 #endif
     {
-        uint64_t *win = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)k * k);
+        uint64_t *win = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)kw * kh);
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 1)
 #endif
@@ -151,7 +158,7 @@ int or_median_filter(const void *src, void *dst, int32_t *idx, int H, int W, int
             const char *plane = (const char *)src + (size_t)c * plane_elems * es;
             for (int x = 0; x < W; x++) {
                 long si;
-                one_pixel(plane, H, W, dtype, k, y, x, win, &si);
+                one_pixel(plane, H, W, dtype, kw, kh, y, x, win, &si);
                 long o = (long)c * plane_elems + (long)y * W + x;
                 if (dst) memcpy((char *)dst + (size_t)o * es, plane + (size_t)si * es, es);
                 if (idx) idx[o] = (int32_t)si;
@@ -160,6 +167,13 @@ int or_median_filter(const void *src, void *dst, int32_t *idx, int H, int W, int
         free(win);
     }
     return 0;
+}
+
+/* The k x k filter: the square case of or_median_filter_rect. */
+int or_median_filter(const void *src, void *dst, int32_t *idx, int H, int W, int C,
+                     int dtype, int k, int nthreads)
+{
+    return or_median_filter_rect(src, dst, idx, H, W, C, dtype, k, k, nthreads);
 }
 
 /* The same filter evaluated only on the listed rows of every plane.
@@ -188,7 +202,7 @@ int or_median_filter_rows(const void *src, void *dst, int32_t *idx, int H, int W
             const char *plane = (const char *)src + (size_t)c * plane_elems * es;
             for (int x = 0; x < W; x++) {
                 long si;
-                one_pixel(plane, H, W, dtype, k, y, x, win, &si);
+                one_pixel(plane, H, W, dtype, k, k, y, x, win, &si);
                 long o = ((long)c * nrows + i) * W + x;
                 if (dst) memcpy((char *)dst + (size_t)o * es, plane + (size_t)si * es, es);
                 if (idx) idx[o] = (int32_t)si;

@@ -191,3 +191,46 @@ def test_backward_finite_differences():
         scale = float(np.abs(g64[idx == p]).sum()) + 1e-30
         rel_err.append(abs(fd - want) / scale)
     assert max(rel_err) <= 1e-6
+
+
+@pytest.mark.parametrize("dt", ["u8", "u16", "u32", "f32"])
+@pytest.mark.parametrize("kw,kh", [(1, 5), (5, 1), (3, 9), (9, 3), (7, 5), (1, 1)])
+def test_rect_matches_scipy_nearest(dt, kw, kh):
+    """Rectangular windows (kw columns, kh rows) against scipy's median of
+    size (kh, kw): swapped axes or a wrong rank fail it."""
+    scipy_nd = pytest.importorskip("scipy.ndimage")
+    x = synth.uniform((21, 26), dt, 300 + 10 * kw + kh)
+    if dt == "f32":
+        x = synth.normal_f32((21, 26), 300 + 10 * kw + kh)
+    np.testing.assert_array_equal(oracle.median_filter(x, kw, kh=kh),
+                                  scipy_nd.median_filter(x, size=(kh, kw), mode="nearest"))
+
+
+def test_rect_one_row_is_running_sort():
+    """A 1-row window is the running median of each image row: a sort of
+    the clamped k-neighbourhood written out by hand."""
+    x = synth.uniform((4, 19), "u16", 77)
+    k = 5
+    got = oracle.median_filter(x, k, kh=1)
+    for y in range(4):
+        for xx in range(19):
+            nb = sorted(int(x[y, min(max(xx + d, 0), 18)]) for d in range(-2, 3))
+            assert got[y, xx] == nb[2]
+
+
+def test_rect_transpose_symmetry_and_square_case():
+    """Filtering the transpose with kw, kh swapped transposes the result,
+    argmedian slots map through the transpose, and kw = kh is the square
+    filter."""
+    x = synth.levels16((2, 23, 17), "u8", 88)
+    a, ia = oracle.median_filter(x, 7, kh=3, with_idx=True)
+    xt = np.ascontiguousarray(x.transpose(0, 2, 1))
+    b = oracle.median_filter(xt, 3, kh=7)
+    np.testing.assert_array_equal(a, b.transpose(0, 2, 1))
+    np.testing.assert_array_equal(oracle.median_filter(x, 5, kh=5), oracle.median_filter(x, 5))
+    # the argmedian points at a source pixel within the window holding the median value
+    H, W = 23, 17
+    ys, xs = ia // W, ia % W
+    yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    assert (np.abs(ys - yy[None]) <= 1).all() and (np.abs(xs - xx[None]) <= 3).all()
+    assert (np.take_along_axis(x.reshape(2, -1), ia.reshape(2, -1), 1).reshape(a.shape) == a).all()
