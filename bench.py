@@ -380,6 +380,28 @@ def bench_fwd_bwd(dev, stream, flush, reps=5):
     return out
 
 
+def bench_rect(dev, stream, flush, reps=3, cases=(("u8", 31, 7), ("u8", 7, 31), ("u16", 15, 3), ("f32", 1, 25),
+                                                    ("u32", 45, 13))):
+    """4096 x 4096 single-plane images, windows of kw columns by kh rows
+    (mf_median_filter_rect)."""
+    import torch
+    import paper_2507_19926_gb300 as mf
+    from paper_2507_19926_gb300 import synth
+    codes = {"u8": mf.MF_U8, "u16": mf.MF_U16, "u32": mf.MF_U32, "f32": mf.MF_F32}
+    res = []
+    sptr = stream.cuda_stream
+    for dt, kw, kh in cases:
+        x = to_device(synth.uniform((1, 4096, 4096), dt, synth.SEED_BASE + 2), dev)
+        y = torch.empty_like(x)
+        pitch = 4096 * x.element_size()
+        f = lambda: mf.mf_median_filter_rect(x.data_ptr(), y.data_ptr(), 4096, 4096, pitch, 1, codes[dt], kw, kh,
+                                             None, 0, sptr)
+        f()
+        ms = _time_ms(f, stream, reps, flush)
+        res.append({"dtype": dt, "kw": kw, "kh": kh, "ms": round(ms, 4), "mpix_s": round(4096 * 4096 / ms / 1e3, 1)})
+    return res
+
+
 def bench_sweep(dev, stream, flush, reps=3, ks=(3, 5, 9, 15, 21, 31, 45, 75), dts=("u8", "u16", "u32", "f32")):
     """4096 x 4096 single-plane images, uniform values, auto variant."""
     import torch
@@ -533,6 +555,7 @@ def run_ours(args):
         extra["batched_vs_plain"] = bench_batched(dev, stream, flush)
         extra["fwd_bwd_vs_fwd"] = bench_fwd_bwd(dev, stream, flush)
         extra["sweep_4096"] = bench_sweep(dev, stream, flush)
+        extra["rect_4096"] = bench_rect(dev, stream, flush)
     out = {
         "metric": "median filter throughput (output channel-pixels per second)",
         "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

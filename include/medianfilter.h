@@ -91,6 +91,19 @@ int mf_median_filter_ex(const void *src, void *dst, int H, int W, size_t pitch, 
 int mf_median_filter_tile(const void *src, void *dst, int H, int W, size_t pitch, int channels,
                           mf_dtype dtype, int k, int tile, mf_stream_t stream);
 
+/* A window of kw columns by kh rows (both odd, 1..75; the paper states its
+ * tile terminology for a k_w x k_h kernel, Sec. 3.2): out(y, x) is the
+ * element of 0-based rank (kw*kh-1)/2 of the clamp-to-edge window rows
+ * y-(kh-1)/2 .. y+(kh-1)/2 by columns x-(kw-1)/2 .. x+(kw-1)/2.  Square
+ * windows take the mf_median_filter_ex path (MF_AUTO); other shapes run the
+ * data-aware variant (Sec. 5) with a T x T root tile, T at most the shorter
+ * side.  argidx: NULL or as for mf_median_filter_ex (tie rule: lowest
+ * value, then lowest row-major window slot (dy+ry)*kw + (dx+rx)).  Errors
+ * as mf_median_filter_ex. */
+int mf_median_filter_rect(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                          mf_dtype dtype, int kw, int kh, int32_t *argidx, size_t idx_pitch,
+                          mf_stream_t stream);
+
 /* The data-oblivious variant (Sec. 4) with the config-th instantiated
  * network configuration for (k, dtype) (0 = the default; the others are the
  * autotuner's candidates: other network forms, tiles or key widths, all
@@ -224,6 +237,12 @@ int mf_probe_minmax(int kind, int iters, double *instr_per_s, double *ms);
  * is used.  Returns MF_ERR_UNSUPPORTED when no plan exists. */
 int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,
                      int *stats);
+
+/* As mf_d1_plan_check for a window of kw columns by kh rows (both odd; the
+ * footprint is (tile + kh - 1) rows x (strip*tile + kw - 1) columns); a
+ * tile of 1 is allowed (a window one pixel wide or high admits no other). */
+int mf_d1_plan_check_rect(int kw, int kh, int tile, int strip, const uint64_t *footprint,
+                          uint64_t *medians, int *stats);
 
 /* Number of CUDA kernels this library launched since load (all threads). */
 uint64_t mf_kernel_launch_count(void);

@@ -28,6 +28,7 @@ GRAD_MODES = {"atomic": MF_GRAD_ATOMIC, "deterministic": MF_GRAD_DETERMINISTIC}
 
 # C symbols declared in include/medianfilter.h
 EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_tile", "mf_median_filter_config",
+           "mf_median_filter_rect", "mf_d1_plan_check_rect",
            "mf_median_filter_bwd",
            "mf_median_filter_host", "mf_batch_plan_create", "mf_batch_run",
            "mf_batch_plan_destroy", "mf_batch_describe", "mf_batch_run_static", "mf_autotune", "mf_describe", "mf_kernel_launch_count",
@@ -66,6 +67,8 @@ def load_library(path=LIB_PATH):
         lib.mf_median_filter_ex.argtypes = [vp, vp, i, i, sz, i, i, i, i, i, vp, sz, vp]
         lib.mf_median_filter_tile.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp]
         lib.mf_median_filter_config.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp]
+        lib.mf_median_filter_rect.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp, sz, vp]
+        lib.mf_d1_plan_check_rect.argtypes = [i, i, i, i, vp, vp, vp]
         lib.mf_median_filter_bwd.argtypes = [vp, vp, vp, i, i, sz, sz, i, i, i, vp]
         lib.mf_median_filter_host.argtypes = [vp, vp, i, i, sz, i, i, i, i, i, vp]
         lib.mf_batch_plan_create.argtypes = [ctypes.POINTER(ImageDesc), i, ctypes.POINTER(vp)]
@@ -113,6 +116,12 @@ def mf_median_filter_ex(src, dst, H, W, pitch, channels, dtype, k, border, varia
 def mf_median_filter_tile(src, dst, H, W, pitch, channels, dtype, k, tile, stream=None):
     return _check(load_library().mf_median_filter_tile(src, dst, H, W, pitch, channels, dtype, k, tile,
                                                        stream))
+
+
+def mf_median_filter_rect(src, dst, H, W, pitch, channels, dtype, kw, kh, argidx=None, idx_pitch=0,
+                          stream=None):
+    return _check(load_library().mf_median_filter_rect(src, dst, H, W, pitch, channels, dtype, kw, kh, argidx,
+                                                       idx_pitch, stream))
 
 
 def mf_median_filter_config(src, dst, H, W, pitch, channels, dtype, k, config, stream=None):
@@ -183,10 +192,11 @@ def mf_probe_minmax(kind, iters=4096):
     return rate.value, ms.value
 
 
-def mf_d1_plan_check(k, tile, footprint=None, strip=1):
-    """Builds the data-aware schedule for (k, tile, strip); with a uint64
-    footprint of keys ((tile+k-1) x (strip*tile+k-1)) also runs it on the
-    CPU.  Returns (stats dict, tile x strip*tile medians or None)."""
+def mf_d1_plan_check(k, tile, footprint=None, strip=1, kh=None):
+    """Builds the data-aware schedule for (k, tile, strip) -- a window of k
+    columns by kh rows when kh is given; with a uint64 footprint of keys
+    ((tile+kh-1) x (strip*tile+k-1)) also runs it on the CPU.  Returns
+    (stats dict, tile x strip*tile medians or None)."""
     import numpy as np
     st = np.zeros(7, np.int32)
     med = None
@@ -194,8 +204,9 @@ def mf_d1_plan_check(k, tile, footprint=None, strip=1):
     if footprint is not None:
         fp = np.ascontiguousarray(footprint, dtype=np.uint64)
         med = np.zeros(tile * tile * strip, np.uint64)
-    _check(load_library().mf_d1_plan_check(k, tile, strip, fp.ctypes.data if fp is not None else None,
-                                           med.ctypes.data if med is not None else None, st.ctypes.data))
+    _check(load_library().mf_d1_plan_check_rect(k, k if kh is None else kh, tile, strip,
+                                                fp.ctypes.data if fp is not None else None,
+                                                med.ctypes.data if med is not None else None, st.ctypes.data))
     names = ["smem_elems", "phases", "tasks", "work_items", "merged", "sorted", "max_sort"]
     return dict(zip(names, [int(v) for v in st])), med
 
@@ -253,9 +264,10 @@ def _stream_ptr(x):
     return _torch().cuda.current_stream(x.device).cuda_stream
 
 
-def median_filter(x, k, variant="auto", return_idx=False, out=None):
+def median_filter(x, k, variant="auto", return_idx=False, out=None, kh=None):
     """k x k clamp-to-edge median of every (H, W) plane of a CUDA tensor
-    (u8, u16, u32 or f32).  With return_idx also the int32 argmedian."""
+    (u8, u16, u32 or f32); with kh, a window of k columns by kh rows
+    (mf_median_filter_rect).  With return_idx also the int32 argmedian."""
     torch = _torch()
     planes, H, W, pitch = _planes(x)
     if out is None:
@@ -267,9 +279,13 @@ def median_filter(x, k, variant="auto", return_idx=False, out=None):
     if return_idx:
         idx = torch.empty(x.shape, dtype=torch.int32, device=x.device)
     with torch.cuda.device(x.device):
-        mf_median_filter_ex(x.data_ptr(), out.data_ptr(), H, W, pitch, planes, dtype_code(x.dtype), int(k),
-                            MF_BORDER_CLAMP, VARIANTS[variant],
-                            idx.data_ptr() if idx is not None else None, 4 * W, _stream_ptr(x))
+        if kh is not None and int(kh) != int(k):
+            mf_median_filter_rect(x.data_ptr(), out.data_ptr(), H, W, pitch, planes, dtype_code(x.dtype), int(k),
+                                  int(kh), idx.data_ptr() if idx is not None else None, 4 * W, _stream_ptr(x))
+        else:
+            mf_median_filter_ex(x.data_ptr(), out.data_ptr(), H, W, pitch, planes, dtype_code(x.dtype), int(k),
+                                MF_BORDER_CLAMP, VARIANTS[variant],
+                                idx.data_ptr() if idx is not None else None, 4 * W, _stream_ptr(x))
     return (out, idx) if return_idx else out
 
 

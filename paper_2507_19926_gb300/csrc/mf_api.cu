@@ -275,6 +275,30 @@ int mf_median_filter_tile(const void *src, void *dst, int H, int W, size_t pitch
     return d1_launch(a, channels, k, dtype, tile, (cudaStream_t)stream);
 }
 
+int mf_median_filter_rect(const void *src, void *dst, int H, int W, size_t pitch, int channels,
+                          mf_dtype dtype, int kw, int kh, int32_t *argidx, size_t idx_pitch,
+                          mf_stream_t stream) {
+    int rc = check_fwd(src, dst, H, W, pitch, channels, dtype, kw, MF_BORDER_CLAMP, argidx, idx_pitch);
+    if (rc) return rc;
+    if (kh < 1 || kh > 75 || (kh & 1) == 0) { set_error("kh must be odd in 1..75 (got %d)", kh); return MF_ERR_ARG; }
+    if (kw == kh)
+        return run_filter(src, dst, H, W, pitch, channels, dtype, kw, MF_AUTO, argidx, idx_pitch,
+                          (cudaStream_t)stream);
+    ImgArgs a;
+    a.src = (const char *)src;
+    a.dst = (char *)dst;
+    a.idx = argidx;
+    a.H = H;
+    a.W = W;
+    a.y_lo = 0;
+    a.y_hi = H - 1;
+    a.pitch = pitch;
+    a.plane = (size_t)H * pitch;
+    a.idx_pitch = idx_pitch;
+    a.idx_plane = (size_t)H * idx_pitch;
+    return d1_launch(a, channels, kw, dtype, 0, (cudaStream_t)stream, kh);
+}
+
 int mf_median_filter_config(const void *src, void *dst, int H, int W, size_t pitch, int channels,
                             mf_dtype dtype, int k, int config, mf_stream_t stream) {
     int rc = check_fwd(src, dst, H, W, pitch, channels, dtype, k, MF_BORDER_CLAMP, nullptr, 0);

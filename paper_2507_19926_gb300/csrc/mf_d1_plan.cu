@@ -77,7 +77,7 @@ struct ListInfo {
 };
 
 struct Builder {
-    int k, T, FW;
+    int k, T, FW;  // k: window width
     std::vector<ListInfo> lists;
     std::vector<PTask> tasks;
 
@@ -168,26 +168,32 @@ struct Builder {
     }
 };
 
-// Forgetfulness: ranks of the held list that can still be the median.
-static void keep_range(int k, int c, int d, int n_held, int *lo, int *hi) {
-    const int m = (k * k - 1) / 2, u = k * k - c;
+// Forgetfulness: ranks of the held list that can still be the median of a
+// window of n = kw * kh elements.
+static void keep_range(int n, int c, int d, int n_held, int *lo, int *hi) {
+    const int m = (n - 1) / 2, u = n - c;
     *lo = std::max(0, m - d - u);
     *hi = std::min(n_held - 1, m - d);
 }
 
 }  // namespace
 
-bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes) {
-    if (k < 3 || (k & 1) == 0 || T < 2 || (T & (T - 1)) || T > k || T > 32 || NB < 1 || NB > 64) return false;
+bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, int kh) {
+    // k: window width (columns), kh: window height (rows)
+    if (kh == 0) kh = k;
+    const int kw = k, n_win = kw * kh;
+    if (kw < 1 || kh < 1 || (kw & 1) == 0 || (kh & 1) == 0 || n_win < 3 || T < 1 || (T & (T - 1)) || T > kw ||
+        T > kh || T > 32 || NB < 1 || NB > 64)
+        return false;
     Builder B;
-    B.k = k;
+    B.k = kw;
     B.T = T;
-    B.FW = NB * T + k - 1;
-    const int FW = B.FW, FH = T + k - 1;
+    B.FW = NB * T + kw - 1;
+    const int FW = B.FW, FH = T + kh - 1;
     // sorted column segments over the root core rows, for every footprint
     // column of the strip: horizontally adjacent root tiles share them
     std::map<int, Ref> col_strip;
-    for (int fx = 0; fx < FW; fx++) col_strip[fx] = B.sort_gather((T - 1) * FW + fx, FW, k - T + 1);
+    for (int fx = 0; fx < FW; fx++) col_strip[fx] = B.sort_gather((T - 1) * FW + fx, FW, kh - T + 1);
     std::vector<Ref> outs(NB * T * T);
     for (int tb = 0; tb < NB; tb++) {
     const int bx = tb * T;  // strip column of this root tile's footprint
@@ -196,40 +202,40 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes) {
     // ---------------------------------------------------------- initialisation
     int tw = T, th = T;
     std::map<int, Ref> col0;
-    for (int fx = 0; fx < T + k - 1; fx++) col0[fx] = col_strip[bx + fx];
+    for (int fx = 0; fx < T + kw - 1; fx++) col0[fx] = col_strip[bx + fx];
     // sorted extra rows over the root core columns
     std::map<int, Ref> row0;
     for (int fy = 0; fy < FH; fy++)
-        if (fy < T - 1 || fy > k - 1) row0[fy] = B.sort_gather(F(fy, T - 1), 1, k - T + 1);
+        if (fy < T - 1 || fy > kh - 1) row0[fy] = B.sort_gather(F(fy, T - 1), 1, kw - T + 1);
     // root core: multi-way merge of the core columns
     std::vector<Ref> cc;
-    for (int fx = T - 1; fx <= k - 1; fx++) cc.push_back(col0[fx]);
-    int c = (k - T + 1) * (k - T + 1), lo, hi;
-    keep_range(k, c, 0, c, &lo, &hi);
+    for (int fx = T - 1; fx <= kw - 1; fx++) cc.push_back(col0[fx]);
+    int c = (kw - T + 1) * (kh - T + 1), lo, hi;
+    keep_range(n_win, c, 0, c, &lo, &hi);
     int d = lo;
     // per level state
     std::vector<std::vector<Ref>> core(1, std::vector<Ref>(1, B.multiway(cc, lo, hi)));  // [j][i]
     std::vector<std::map<int, Ref>> rows(1, row0);  // [i][fy]
     std::vector<std::map<int, Ref>> cols(1);        // [j][fx]
     for (auto &kv : col0)
-        if (kv.first < T - 1 || kv.first > k - 1) cols[0][kv.first] = kv.second;
+        if (kv.first < T - 1 || kv.first > kw - 1) cols[0][kv.first] = kv.second;
 
     // ---------------------------------------------------------- recursion
     while (tw * th > 1) {
         const int NX = T / tw, NY = T / th;
         if (tw >= th) {  // horizontal split: halve the width
             const int h = tw / 2;
-            const int cw = k - h + 1, ch = k - th + 1;
+            const int cw = kw - h + 1, ch = kh - th + 1;
             c = cw * ch;
             const int K = core[0][0].len;
             const int n_held = K + h * ch;
-            keep_range(k, c, d, n_held, &lo, &hi);
+            keep_range(n_win, c, d, n_held, &lo, &hi);
             std::vector<std::vector<Ref>> ncore(NY, std::vector<Ref>(2 * NX));
             std::vector<std::map<int, Ref>> nrows(2 * NX);
             for (int i = 0; i < NX; i++) {
                 const int x0 = i * tw;
                 for (int s = 0; s < 2; s++) {
-                    const int nx0 = s == 0 ? x0 + h - 1 : x0 + k;  // first new core column
+                    const int nx0 = s == 0 ? x0 + h - 1 : x0 + kw;  // first new core column
                     for (int j = 0; j < NY; j++) {
                         std::vector<Ref> nc;
                         for (int fx = nx0; fx < nx0 + h; fx++) nc.push_back(cols[j].at(fx));
@@ -247,17 +253,17 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes) {
             tw = h;
         } else {  // vertical split: halve the height
             const int h = th / 2;
-            const int cw = k - tw + 1, ch = k - h + 1;
+            const int cw = kw - tw + 1, ch = kh - h + 1;
             c = cw * ch;
             const int K = core[0][0].len;
             const int n_held = K + h * cw;
-            keep_range(k, c, d, n_held, &lo, &hi);
+            keep_range(n_win, c, d, n_held, &lo, &hi);
             std::vector<std::vector<Ref>> ncore(2 * NY, std::vector<Ref>(NX));
             std::vector<std::map<int, Ref>> ncols(2 * NY);
             for (int j = 0; j < NY; j++) {
                 const int y0 = j * th;
                 for (int s = 0; s < 2; s++) {
-                    const int ny0 = s == 0 ? y0 + h - 1 : y0 + k;  // first new core row
+                    const int ny0 = s == 0 ? y0 + h - 1 : y0 + kh;  // first new core row
                     for (int i = 0; i < NX; i++) {
                         std::vector<Ref> nr;
                         for (int fy = ny0; fy < ny0 + h; fy++) nr.push_back(rows[i].at(fy));
@@ -368,7 +374,8 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes) {
     }
 
     // ---------------------------------------------------------- emit
-    plan->k = k;
+    plan->k = kw;
+    plan->kh = kh;
     plan->T = T;
     plan->B = NB;
     plan->FW = FW;
@@ -485,10 +492,10 @@ void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *m
 }  // namespace mf
 
 // Host check of the data-aware schedule (declared in medianfilter.h).
-extern "C" int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,
-                                int *stats) {
+extern "C" int mf_d1_plan_check_rect(int kw, int kh, int tile, int strip, const uint64_t *footprint,
+                                     uint64_t *medians, int *stats) {
     mf::D1Plan plan;
-    if (!mf::d1_build_plan(k, tile, &plan, strip)) return MF_ERR_UNSUPPORTED;
+    if (!mf::d1_build_plan(kw, tile, &plan, strip, 256, 4, kh)) return MF_ERR_UNSUPPORTED;
     if (stats) {
         stats[0] = plan.smem_elems;
         stats[1] = (int)plan.phase_begin.size() - 1;
@@ -500,4 +507,9 @@ extern "C" int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *foot
     }
     if (footprint && medians) mf::d1_run_plan_host(plan, footprint, medians);
     return MF_OK;
+}
+
+extern "C" int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,
+                                int *stats) {
+    return mf_d1_plan_check_rect(k, k, tile, strip, footprint, medians, stats);
 }

@@ -31,10 +31,11 @@ struct D1Task {
 };
 
 struct D1Plan {
-    int k = 0, T = 0;
+    int k = 0, T = 0;                // window k columns by kh rows (kh = k: square)
+    int kh = 0;
     int B = 1;                       // root tiles per strip (side by side horizontally)
     int FW = 0;                      // footprint width B*T + k - 1 (footprint at offset 0, row-major)
-    int FH = 0;                      // footprint height T + k - 1
+    int FH = 0;                      // footprint height T + kh - 1
     int nt = 256;                    // threads per block the chunking targets
     int smem_elems = 0;              // shared-memory list elements needed (footprint included)
     std::vector<D1Task> tasks;       // host form; the device gets them packed (D1Packed)
@@ -46,11 +47,13 @@ struct D1Plan {
     long long sort_elems = 0;
 };
 
-// Builds the plan for a k x k kernel and a strip of B root tiles of T x T
-// (T a power of two, 2 <= T <= min(k, 32); B >= 1), chunking merges for
-// blocks of nt threads.  The strip's footprint columns are sorted once and
-// shared by its tiles (paper Sec. 3.3).  Returns false outside that range.
-bool d1_build_plan(int k, int T, D1Plan *plan, int B = 1, int nt = 256, int key_bytes = 4);
+// Builds the plan for a window of k columns by kh rows (kh = 0: k x k; the
+// paper states its tile terminology for a k_w x k_h kernel, Sec. 3.2) and a
+// strip of B root tiles of T x T (T a power of two, 1 <= T <= min(k, kh,
+// 32); B >= 1), chunking merges for blocks of nt threads.  The strip's
+// footprint columns are sorted once and shared by its tiles (Sec. 3.3).
+// Returns false outside that range.
+bool d1_build_plan(int k, int T, D1Plan *plan, int B = 1, int nt = 256, int key_bytes = 4, int kh = 0);
 
 struct D1Packed;
 // The 16-byte device form of every task (layout in mf_d1_ops.cuh).

@@ -33,7 +33,7 @@ struct D1Dev {
     const int32_t *phase_begin;
     const int32_t *out_off;
     int nphases;
-    int k, T, B, FW, FH;
+    int k, kh, T, B, FW, FH;  // window k columns by kh rows
 };
 
 template <class KT, int N>
@@ -80,15 +80,15 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
     KT *sm = reinterpret_cast<KT *>(d1_smem);
     typedef typename Dt<DT>::E E;
     const int tid = threadIdx.x, NT = blockDim.x;
-    const int T = p.T, FW = p.FW, FH = p.FH, R = (p.k - 1) / 2, SW = p.B * p.T;
+    const int T = p.T, FW = p.FW, FH = p.FH, RX = (p.k - 1) / 2, RY = (p.kh - 1) / 2, SW = p.B * p.T;
     const int x0 = bxi * SW, y0 = byi * T;
     const char *src = a.src + (size_t)z * a.plane;
 
     // footprint of the strip, clamped to the image
     for (int i = tid; i < FW * FH; i += NT) {
         const int fy = i / FW, fx = i - fy * FW;
-        const int y = clampi(y0 - R + fy, a.y_lo, a.y_hi);
-        const int x = clampi(x0 - R + fx, 0, a.W - 1);
+        const int y = clampi(y0 - RY + fy, a.y_lo, a.y_hi);
+        const int x = clampi(x0 - RX + fx, 0, a.W - 1);
         sm[i] = D1Key<DT, KT, ARG>::make(Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, x)), i);
     }
     __syncthreads();
@@ -118,7 +118,7 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
             const int fidx = (int)((unsigned long long)v & ((1ull << IB) - 1));
             const uint32_t key = (uint32_t)((unsigned long long)v >> IB);
             const int fy = fidx / FW, fx = fidx - fy * FW;
-            const int ys = clampi(y0 - R + fy, a.y_lo, a.y_hi), xs = clampi(x0 - R + fx, 0, a.W - 1);
+            const int ys = clampi(y0 - RY + fy, a.y_lo, a.y_hi), xs = clampi(x0 - RX + fx, 0, a.W - 1);
             if (dst) reinterpret_cast<E *>(dst + (size_t)y * a.pitch)[x] = Dt<DT>::val(key);
             if (idx) reinterpret_cast<int32_t *>(idx + (size_t)y * a.idx_pitch)[x] = ys * a.W + xs;
         }
@@ -155,10 +155,10 @@ struct D1Cached {
 };
 
 static std::mutex g_d1_mu;
-typedef std::tuple<int, int, int, int, int> PlanKey;  // k, T, B, nt, key bytes
+typedef std::tuple<int, int, int, int, int, int> PlanKey;  // k, kh, T, B, nt, key bytes
 static std::map<PlanKey, D1Plan *> *g_plans = new std::map<PlanKey, D1Plan *>();
-static std::map<std::tuple<int, int, int, int, int, int>, D1Cached *> *g_d1 =
-    new std::map<std::tuple<int, int, int, int, int, int>, D1Cached *>();
+static std::map<std::tuple<int, int, int, int, int, int, int>, D1Cached *> *g_d1 =
+    new std::map<std::tuple<int, int, int, int, int, int, int>, D1Cached *>();
 
 static size_t key_bytes(int dtype, bool arg) {
     const bool wide = dtype == MF_U32 || dtype == MF_F32;
@@ -166,14 +166,16 @@ static size_t key_bytes(int dtype, bool arg) {
     return wide ? 4 : 2;
 }
 
-// Host plan; nullptr if none exists.  No device work.
-static const D1Plan *host_plan(int k, int T, int B, int nt, int kb) {
+// Host plan for a window of k columns by kh rows (kh = 0: square); nullptr
+// if none exists.  No device work.
+static const D1Plan *host_plan(int k, int T, int B, int nt, int kb, int kh = 0) {
+    if (kh == 0) kh = k;
     std::lock_guard<std::mutex> lk(g_d1_mu);
-    const PlanKey key(k, T, B, nt, kb);
+    const PlanKey key(k, kh, T, B, nt, kb);
     auto it = g_plans->find(key);
     if (it != g_plans->end()) return it->second;
     D1Plan *pl = new D1Plan();
-    if (!d1_build_plan(k, T, pl, B, nt, kb)) {
+    if (!d1_build_plan(k, T, pl, B, nt, kb, kh)) {
         delete pl;
         pl = nullptr;
     }
@@ -184,11 +186,16 @@ static const D1Plan *host_plan(int k, int T, int B, int nt, int kb) {
 // Strip width and block size for a root tile: the widest strip (sharing the
 // most column sorts) whose state fits the small budget runs with 256 threads
 // and several blocks per SM; otherwise one tile with 512 threads.
-static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt) {
-    if (k < 3 || k > 75 || !(k & 1) || T < 2 || T > 32 || (T & (T - 1)) || T > k) return false;
+static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt, int kh = 0) {
+    if (kh == 0) kh = k;
+    const int kmin = k < kh ? k : kh;
+    // a 1 x 1 root tile only where the window is one pixel wide or high
+    if (k < 1 || k > 75 || !(k & 1) || kh < 1 || kh > 75 || !(kh & 1) || k * kh < 3 || T < (kmin < 3 ? 1 : 2) ||
+        T > 32 || (T & (T - 1)) || T > kmin)
+        return false;
     const int kb = (int)key_bytes(dtype, arg);
     for (int b = 8; b >= 1; b /= 2) {
-        const D1Plan *p = host_plan(k, T, b, 256, kb);
+        const D1Plan *p = host_plan(k, T, b, 256, kb, kh);
         if (p && (size_t)p->smem_elems * kb <= D1_SMEM_SMALL) {
             *B = b;
             *nt = 256;
@@ -197,13 +204,13 @@ static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt) {
     }
     // one tile per block: 512 threads when two blocks share an SM, else
     // 1024 threads (32 warps) in a block of its own
-    const D1Plan *p5 = host_plan(k, T, 1, 512, kb);
+    const D1Plan *p5 = host_plan(k, T, 1, 512, kb, kh);
     if (p5 && 2 * ((size_t)p5->smem_elems * kb + 1024) <= 227 * 1024) {
         *B = 1;
         *nt = 512;
         return true;
     }
-    const D1Plan *p = host_plan(k, T, 1, 1024, kb);
+    const D1Plan *p = host_plan(k, T, 1, 1024, kb, kh);
     if (p && (size_t)p->smem_elems * kb <= D1_SMEM_BUDGET) {
         *B = 1;
         *nt = 1024;
@@ -213,8 +220,9 @@ static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt) {
 }
 
 // Plan uploaded to the current device (once per device).
-static D1Cached *get_plan(int k, int T, int B, int nt, int kb) {
-    const D1Plan *hp = host_plan(k, T, B, nt, kb);
+static D1Cached *get_plan(int k, int T, int B, int nt, int kb, int kh = 0) {
+    if (kh == 0) kh = k;
+    const D1Plan *hp = host_plan(k, T, B, nt, kb, kh);
     if (!hp) return nullptr;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -222,7 +230,7 @@ static D1Cached *get_plan(int k, int T, int B, int nt, int kb) {
         return nullptr;
     }
     std::lock_guard<std::mutex> lk(g_d1_mu);
-    auto key = std::make_tuple(k, T, B, nt, kb, dev);
+    auto key = std::make_tuple(k, kh, T, B, nt, kb, dev);
     auto it = g_d1->find(key);
     if (it != g_d1->end()) return it->second;
     D1Cached *c = new D1Cached();
@@ -254,6 +262,7 @@ static D1Cached *get_plan(int k, int T, int B, int nt, int kb) {
     c->dev.out_off = (const int32_t *)(m + bt + bw + bp);
     c->dev.nphases = (int)pl.phase_begin.size() - 1;
     c->dev.k = k;
+    c->dev.kh = hp->kh;
     c->dev.T = T;
     c->dev.B = B;
     c->dev.FW = pl.FW;
@@ -262,26 +271,29 @@ static D1Cached *get_plan(int k, int T, int B, int nt, int kb) {
     return c;
 }
 
-int d1_supported_tile(int k, int dtype, bool arg, int T) {
+int d1_supported_tile(int k, int dtype, bool arg, int T, int kh) {
     int B, nt;
-    return choose_config(k, dtype, arg, T, &B, &nt) ? 1 : 0;
+    return choose_config(k, dtype, arg, T, &B, &nt, kh) ? 1 : 0;
 }
 
-int d1_default_tile(int k, int dtype, bool arg) {
-    const int tuned = tune_lookup(k, dtype, arg) == MF_DATA_AWARE ? tune_tile(k, dtype, arg) : 0;
+int d1_default_tile(int k, int dtype, bool arg, int kh) {
+    const bool square = kh == 0 || kh == k;
+    const int tuned = square && tune_lookup(k, dtype, arg) == MF_DATA_AWARE ? tune_tile(k, dtype, arg) : 0;
     if (tuned && d1_supported_tile(k, dtype, arg, tuned)) return tuned;
-    // root-tile heuristic t(k) = 2^(floor(log2 k) - 1) (paper Sec. 4.2), at
-    // least 2 and at most 16, lowered until the tree's state fits in shared
+    // root-tile heuristic t(k) = 2^(floor(log2 k) - 1) (paper Sec. 4.2) on
+    // the shorter window side, at least 2 (1 for a window one pixel wide or
+    // high) and at most 16, lowered until the tree's state fits in shared
     // memory
+    const int kmin = square ? k : (k < kh ? k : kh);
     int t = 1;
-    while (t * 4 <= k) t *= 2;
-    if (t < 2) t = 2;
+    while (t * 4 <= kmin) t *= 2;
+    if (t < 2 && kmin >= 3) t = 2;
     if (t > 16) t = 16;
     // 2-byte keys: the 16 x 16 tree measured faster from k = 27 on
     // (u8 4096^2: 5.02 vs 5.61 ms at k = 27, 6.25 vs 6.40 ms at k = 31)
-    if (key_bytes(dtype, arg) == 2 && k >= 27) t = 16;
-    for (; t >= 2; t /= 2)
-        if (d1_supported_tile(k, dtype, arg, t)) return t;
+    if (key_bytes(dtype, arg) == 2 && kmin >= 27) t = 16;
+    for (; t >= 1; t /= 2)
+        if (d1_supported_tile(k, dtype, arg, t, kh)) return t;
     return 0;
 }
 
@@ -313,15 +325,15 @@ static int d1_launch_t(const ImgArgs &a, int C, const D1Cached *c, int nt, cudaS
     return d1_launch_n<KT, DT, ARG, 32>(a, C, c, nt, s);
 }
 
-int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s) {
+int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s, int kh) {
     const bool arg = a.idx != nullptr;
-    if (T == 0) T = d1_default_tile(k, dtype, arg);
+    if (T == 0) T = d1_default_tile(k, dtype, arg, kh);
     int B, nt;
-    if (!choose_config(k, dtype, arg, T, &B, &nt)) {
-        set_error("no data-aware plan for k=%d tile=%d", k, T);
+    if (!choose_config(k, dtype, arg, T, &B, &nt, kh)) {
+        set_error("no data-aware plan for a %dx%d window, tile=%d", k, kh ? kh : k, T);
         return MF_ERR_UNSUPPORTED;
     }
-    const D1Cached *c = get_plan(k, T, B, nt, (int)key_bytes(dtype, arg));
+    const D1Cached *c = get_plan(k, T, B, nt, (int)key_bytes(dtype, arg), kh);
     if (!c) {
         set_error("cannot allocate or upload the data-aware plan for k=%d tile=%d", k, T);
         return MF_ERR_ALLOC;

@@ -32,9 +32,10 @@ const O1Entry *find_o1_nth(int k, int dtype, bool arg, int nth);
 
 // Data-aware variant (mf_data_aware.cu).
 int d1_supported(int k, int dtype, bool arg);
-int d1_launch(const ImgArgs &a, int channels, int k, int dtype, int tile, cudaStream_t s);
-int d1_default_tile(int k, int dtype, bool arg);
-int d1_supported_tile(int k, int dtype, bool arg, int tile);
+// kh: window height for a k-wide, kh-high window (0: k x k)
+int d1_launch(const ImgArgs &a, int channels, int k, int dtype, int tile, cudaStream_t s, int kh = 0);
+int d1_default_tile(int k, int dtype, bool arg, int kh = 0);
+int d1_supported_tile(int k, int dtype, bool arg, int tile, int kh = 0);
 int d1_describe(int k, int dtype, bool arg, int tile, char *buf, size_t n);
 void d1_release_all();
 // Persistent data-aware launch over a device work list for (k, dtype); the

@@ -74,3 +74,37 @@ def test_work_per_pixel_linear_in_k():
         st, _ = mf.mf_d1_plan_check(k, 16)
         per.append(st["merged"] / 256 / k)
     assert max(per) / min(per) < 2.0
+
+
+RECT = [(1, 5, 1, 1), (5, 1, 1, 1), (3, 9, 2, 1), (9, 3, 2, 2), (7, 5, 4, 1), (15, 5, 4, 2), (5, 31, 4, 1),
+        (31, 9, 8, 1), (25, 13, 8, 2), (3, 75, 2, 1), (75, 3, 2, 1)]
+
+
+@pytest.mark.parametrize("kw,kh,T,B", RECT)
+def test_rect_plan_matches_oracle(kw, kh, T, B):
+    """Windows of kw columns by kh rows (paper Sec. 3.2 terminology for a
+    k_w x k_h kernel): the planned tree's medians for a strip's footprint
+    against the oracle's rectangular filter."""
+    FH, FW = T + kh - 1, B * T + kw - 1
+    rx, ry = kw // 2, kh // 2
+    for s in range(2):
+        gen = synth.levels16 if s else synth.uniform
+        img = gen((FH, FW), "u16", 13 * kw + kh + T + s)
+        st, med = mf.mf_d1_plan_check(kw, T, img.astype(np.uint64).ravel(), strip=B, kh=kh)
+        want = oracle.median_filter(img, kw, kh=kh)[ry:ry + T, rx:rx + B * T].ravel()
+        assert np.array_equal(med.astype(np.uint16), want), (kw, kh, T, B, s)
+
+
+def test_rect_plan_square_case_unchanged():
+    """kh = k plans exactly the k x k schedule."""
+    for k, T in [(9, 4), (17, 8), (31, 16)]:
+        a, _ = mf.mf_d1_plan_check(k, T)
+        b, _ = mf.mf_d1_plan_check(k, T, kh=k)
+        assert a == b
+
+
+def test_rect_plan_rejects_tiles_beyond_the_short_side():
+    with pytest.raises(mf.MedianFilterError):
+        mf.mf_d1_plan_check(9, 4, kh=3)
+    with pytest.raises(mf.MedianFilterError):
+        mf.mf_d1_plan_check(1, 2, kh=9)
