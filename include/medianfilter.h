@@ -238,10 +238,11 @@ int mf_probe_minmax(int kind, int iters, double *instr_per_s, double *ms);
 int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,
                      int *stats);
 
-/* As mf_d1_plan_check for a window of kw columns by kh rows (both odd; the
- * footprint is (tile + kh - 1) rows x (strip*tile + kw - 1) columns); a
- * tile of 1 is allowed (a window one pixel wide or high admits no other). */
-int mf_d1_plan_check_rect(int kw, int kh, int tile, int strip, const uint64_t *footprint,
+/* As mf_d1_plan_check for a window of kw columns by kh rows (both odd) and
+ * root tiles of tile_w columns by tile_h rows (powers of two, at most the
+ * window side, 1 allowed); the footprint is (tile_h + kh - 1) rows x
+ * (strip*tile_w + kw - 1) columns, the medians tile_h x strip*tile_w. */
+int mf_d1_plan_check_rect(int kw, int kh, int tile_w, int tile_h, int strip, const uint64_t *footprint,
                           uint64_t *medians, int *stats);
 
 /* Number of CUDA kernels this library launched since load (all threads). */

@@ -68,7 +68,7 @@ def load_library(path=LIB_PATH):
         lib.mf_median_filter_tile.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp]
         lib.mf_median_filter_config.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp]
         lib.mf_median_filter_rect.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp, sz, vp]
-        lib.mf_d1_plan_check_rect.argtypes = [i, i, i, i, vp, vp, vp]
+        lib.mf_d1_plan_check_rect.argtypes = [i, i, i, i, i, vp, vp, vp]
         lib.mf_median_filter_bwd.argtypes = [vp, vp, vp, i, i, sz, sz, i, i, i, vp]
         lib.mf_median_filter_host.argtypes = [vp, vp, i, i, sz, i, i, i, i, i, vp]
         lib.mf_batch_plan_create.argtypes = [ctypes.POINTER(ImageDesc), i, ctypes.POINTER(vp)]
@@ -192,19 +192,21 @@ def mf_probe_minmax(kind, iters=4096):
     return rate.value, ms.value
 
 
-def mf_d1_plan_check(k, tile, footprint=None, strip=1, kh=None):
+def mf_d1_plan_check(k, tile, footprint=None, strip=1, kh=None, tile_h=None):
     """Builds the data-aware schedule for (k, tile, strip) -- a window of k
-    columns by kh rows when kh is given; with a uint64 footprint of keys
-    ((tile+kh-1) x (strip*tile+k-1)) also runs it on the CPU.  Returns
-    (stats dict, tile x strip*tile medians or None)."""
+    columns by kh rows and root tiles of tile columns by tile_h rows when
+    given; with a uint64 footprint of keys ((tile_h+kh-1) x
+    (strip*tile+k-1)) also runs it on the CPU.  Returns (stats dict,
+    tile_h x strip*tile medians or None)."""
     import numpy as np
     st = np.zeros(7, np.int32)
     med = None
     fp = None
+    th = tile if tile_h is None else tile_h
     if footprint is not None:
         fp = np.ascontiguousarray(footprint, dtype=np.uint64)
-        med = np.zeros(tile * tile * strip, np.uint64)
-    _check(load_library().mf_d1_plan_check_rect(k, k if kh is None else kh, tile, strip,
+        med = np.zeros(tile * th * strip, np.uint64)
+    _check(load_library().mf_d1_plan_check_rect(k, k if kh is None else kh, tile, th, strip,
                                                 fp.ctypes.data if fp is not None else None,
                                                 med.ctypes.data if med is not None else None, st.ctypes.data))
     names = ["smem_elems", "phases", "tasks", "work_items", "merged", "sorted", "max_sort"]

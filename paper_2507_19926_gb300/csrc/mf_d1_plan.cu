@@ -178,39 +178,41 @@ static void keep_range(int n, int c, int d, int n_held, int *lo, int *hi) {
 
 }  // namespace
 
-bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, int kh) {
-    // k: window width (columns), kh: window height (rows)
+bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, int kh, int TH) {
+    // k: window width (columns), kh: window height (rows); root tile T
+    // columns by TH rows
     if (kh == 0) kh = k;
-    const int kw = k, n_win = kw * kh;
-    if (kw < 1 || kh < 1 || (kw & 1) == 0 || (kh & 1) == 0 || n_win < 3 || T < 1 || (T & (T - 1)) || T > kw ||
-        T > kh || T > 32 || NB < 1 || NB > 64)
+    if (TH == 0) TH = T;
+    const int kw = k, n_win = kw * kh, TW = T;
+    if (kw < 1 || kh < 1 || (kw & 1) == 0 || (kh & 1) == 0 || n_win < 3 || TW < 1 || (TW & (TW - 1)) || TW > kw ||
+        TH < 1 || (TH & (TH - 1)) || TH > kh || TW > 32 || TH > 32 || NB < 1 || NB > 64)
         return false;
     Builder B;
     B.k = kw;
-    B.T = T;
-    B.FW = NB * T + kw - 1;
-    const int FW = B.FW, FH = T + kh - 1;
+    B.T = TW;
+    B.FW = NB * TW + kw - 1;
+    const int FW = B.FW, FH = TH + kh - 1;
     // sorted column segments over the root core rows, for every footprint
     // column of the strip: horizontally adjacent root tiles share them
     std::map<int, Ref> col_strip;
-    for (int fx = 0; fx < FW; fx++) col_strip[fx] = B.sort_gather((T - 1) * FW + fx, FW, kh - T + 1);
-    std::vector<Ref> outs(NB * T * T);
+    for (int fx = 0; fx < FW; fx++) col_strip[fx] = B.sort_gather((TH - 1) * FW + fx, FW, kh - TH + 1);
+    std::vector<Ref> outs(NB * TW * TH);
     for (int tb = 0; tb < NB; tb++) {
-    const int bx = tb * T;  // strip column of this root tile's footprint
+    const int bx = tb * TW;  // strip column of this root tile's footprint
     auto F = [&](int fy, int fx) { return fy * FW + bx + fx; };
 
     // ---------------------------------------------------------- initialisation
-    int tw = T, th = T;
+    int tw = TW, th = TH;
     std::map<int, Ref> col0;
-    for (int fx = 0; fx < T + kw - 1; fx++) col0[fx] = col_strip[bx + fx];
+    for (int fx = 0; fx < TW + kw - 1; fx++) col0[fx] = col_strip[bx + fx];
     // sorted extra rows over the root core columns
     std::map<int, Ref> row0;
     for (int fy = 0; fy < FH; fy++)
-        if (fy < T - 1 || fy > kh - 1) row0[fy] = B.sort_gather(F(fy, T - 1), 1, kw - T + 1);
+        if (fy < TH - 1 || fy > kh - 1) row0[fy] = B.sort_gather(F(fy, TW - 1), 1, kw - TW + 1);
     // root core: multi-way merge of the core columns
     std::vector<Ref> cc;
-    for (int fx = T - 1; fx <= kw - 1; fx++) cc.push_back(col0[fx]);
-    int c = (kw - T + 1) * (kh - T + 1), lo, hi;
+    for (int fx = TW - 1; fx <= kw - 1; fx++) cc.push_back(col0[fx]);
+    int c = (kw - TW + 1) * (kh - TH + 1), lo, hi;
     keep_range(n_win, c, 0, c, &lo, &hi);
     int d = lo;
     // per level state
@@ -218,11 +220,11 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
     std::vector<std::map<int, Ref>> rows(1, row0);  // [i][fy]
     std::vector<std::map<int, Ref>> cols(1);        // [j][fx]
     for (auto &kv : col0)
-        if (kv.first < T - 1 || kv.first > kw - 1) cols[0][kv.first] = kv.second;
+        if (kv.first < TW - 1 || kv.first > kw - 1) cols[0][kv.first] = kv.second;
 
     // ---------------------------------------------------------- recursion
     while (tw * th > 1) {
-        const int NX = T / tw, NY = T / th;
+        const int NX = TW / tw, NY = TH / th;
         if (tw >= th) {  // horizontal split: halve the width
             const int h = tw / 2;
             const int cw = kw - h + 1, ch = kh - th + 1;
@@ -283,8 +285,8 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
         d += lo;
     }
 
-    for (int j = 0; j < T; j++)
-        for (int i = 0; i < T; i++) outs[j * NB * T + bx + i] = core[j][i];
+    for (int j = 0; j < TH; j++)
+        for (int i = 0; i < TW; i++) outs[j * NB * TW + bx + i] = core[j][i];
     }  // root tiles of the strip
 
     // ---------------------------------------------------------- liveness
@@ -376,7 +378,8 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
     // ---------------------------------------------------------- emit
     plan->k = kw;
     plan->kh = kh;
-    plan->T = T;
+    plan->T = TW;
+    plan->TH = TH;
     plan->B = NB;
     plan->FW = FW;
     plan->FH = FH;
@@ -442,8 +445,8 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
         }
     }
     plan->phase_begin.push_back((int)plan->work.size());
-    plan->out_off.resize(NB * T * T);
-    for (int i = 0; i < NB * T * T; i++) plan->out_off[i] = resolve(outs[i]);
+    plan->out_off.resize(NB * TW * TH);
+    for (int i = 0; i < NB * TW * TH; i++) plan->out_off[i] = resolve(outs[i]);
     // limits of the packed device form
     for (const D1Task &t : plan->tasks)
         if (t.a_off >= (1 << 17) || t.b_off >= (1 << 17) || t.out_off >= (1 << 17) || t.a_len >= (1 << 13) ||
@@ -486,16 +489,16 @@ void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *m
             }
         }
     }
-    for (int i = 0; i < plan.B * plan.T * plan.T; i++) medians[i] = sm[plan.out_off[i]];
+    for (int i = 0; i < plan.B * plan.T * plan.TH; i++) medians[i] = sm[plan.out_off[i]];
 }
 
 }  // namespace mf
 
 // Host check of the data-aware schedule (declared in medianfilter.h).
-extern "C" int mf_d1_plan_check_rect(int kw, int kh, int tile, int strip, const uint64_t *footprint,
-                                     uint64_t *medians, int *stats) {
+extern "C" int mf_d1_plan_check_rect(int kw, int kh, int tile_w, int tile_h, int strip,
+                                     const uint64_t *footprint, uint64_t *medians, int *stats) {
     mf::D1Plan plan;
-    if (!mf::d1_build_plan(kw, tile, &plan, strip, 256, 4, kh)) return MF_ERR_UNSUPPORTED;
+    if (!mf::d1_build_plan(kw, tile_w, &plan, strip, 256, 4, kh, tile_h)) return MF_ERR_UNSUPPORTED;
     if (stats) {
         stats[0] = plan.smem_elems;
         stats[1] = (int)plan.phase_begin.size() - 1;
@@ -511,5 +514,5 @@ extern "C" int mf_d1_plan_check_rect(int kw, int kh, int tile, int strip, const 
 
 extern "C" int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,
                                 int *stats) {
-    return mf_d1_plan_check_rect(k, k, tile, strip, footprint, medians, stats);
+    return mf_d1_plan_check_rect(k, k, tile, tile, strip, footprint, medians, stats);
 }

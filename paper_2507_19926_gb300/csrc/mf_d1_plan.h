@@ -33,27 +33,30 @@ struct D1Task {
 struct D1Plan {
     int k = 0, T = 0;                // window k columns by kh rows (kh = k: square)
     int kh = 0;
+    int TH = 0;                      // root tile T columns by TH rows (TH = T: square)
     int B = 1;                       // root tiles per strip (side by side horizontally)
     int FW = 0;                      // footprint width B*T + k - 1 (footprint at offset 0, row-major)
-    int FH = 0;                      // footprint height T + kh - 1
+    int FH = 0;                      // footprint height TH + kh - 1
     int nt = 256;                    // threads per block the chunking targets
     int smem_elems = 0;              // shared-memory list elements needed (footprint included)
     std::vector<D1Task> tasks;       // host form; the device gets them packed (D1Packed)
     std::vector<uint32_t> work;      // task << 12 | chunk, grouped by phase
     std::vector<int32_t> phase_begin;  // phases + 1 entries into work
-    std::vector<int32_t> out_off;    // T * B*T: offset of each pixel's median (row-major in the strip)
+    std::vector<int32_t> out_off;    // TH * B*T: offset of each pixel's median (row-major in the strip)
     int max_sort = 0;                // longest SORT task
     long long merge_outputs = 0;     // total merged elements (work measure)
     long long sort_elems = 0;
 };
 
 // Builds the plan for a window of k columns by kh rows (kh = 0: k x k; the
-// paper states its tile terminology for a k_w x k_h kernel, Sec. 3.2) and a
-// strip of B root tiles of T x T (T a power of two, 1 <= T <= min(k, kh,
-// 32); B >= 1), chunking merges for blocks of nt threads.  The strip's
-// footprint columns are sorted once and shared by its tiles (Sec. 3.3).
-// Returns false outside that range.
-bool d1_build_plan(int k, int T, D1Plan *plan, int B = 1, int nt = 256, int key_bytes = 4, int kh = 0);
+// paper states its tile terminology for a k_w x k_h kernel and t_w x t_h
+// tiles, Sec. 3.2) and a strip of B root tiles of T columns by TH rows
+// (TH = 0: T; powers of two, 1 <= T <= min(k, 32), 1 <= TH <= min(kh, 32);
+// B >= 1), chunking merges for blocks of nt threads.  The strip's footprint
+// columns are sorted once and shared by its tiles (Sec. 3.3).  Returns
+// false outside that range.
+bool d1_build_plan(int k, int T, D1Plan *plan, int B = 1, int nt = 256, int key_bytes = 4, int kh = 0,
+                   int TH = 0);
 
 struct D1Packed;
 // The 16-byte device form of every task (layout in mf_d1_ops.cuh).

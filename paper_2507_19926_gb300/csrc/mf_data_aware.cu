@@ -33,7 +33,7 @@ struct D1Dev {
     const int32_t *phase_begin;
     const int32_t *out_off;
     int nphases;
-    int k, kh, T, B, FW, FH;  // window k columns by kh rows
+    int k, kh, T, TH, B, FW, FH;  // window k columns by kh rows; root tile T columns by TH rows
 };
 
 template <class KT, int N>
@@ -80,8 +80,8 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
     KT *sm = reinterpret_cast<KT *>(d1_smem);
     typedef typename Dt<DT>::E E;
     const int tid = threadIdx.x, NT = blockDim.x;
-    const int T = p.T, FW = p.FW, FH = p.FH, RX = (p.k - 1) / 2, RY = (p.kh - 1) / 2, SW = p.B * p.T;
-    const int x0 = bxi * SW, y0 = byi * T;
+    const int TH = p.TH, FW = p.FW, FH = p.FH, RX = (p.k - 1) / 2, RY = (p.kh - 1) / 2, SW = p.B * p.T;
+    const int x0 = bxi * SW, y0 = byi * TH;
     const char *src = a.src + (size_t)z * a.plane;
 
     // footprint of the strip, clamped to the image
@@ -106,7 +106,7 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
 
     char *dst = a.dst ? a.dst + (size_t)z * a.plane : nullptr;
     char *idx = a.idx ? reinterpret_cast<char *>(a.idx) + (size_t)z * a.idx_plane : nullptr;
-    for (int i = tid; i < T * SW; i += NT) {
+    for (int i = tid; i < TH * SW; i += NT) {
         const int py = i / SW, px = i - py * SW;
         const int y = y0 + py, x = x0 + px;
         if (y >= a.H || x >= a.W) continue;
@@ -155,10 +155,10 @@ struct D1Cached {
 };
 
 static std::mutex g_d1_mu;
-typedef std::tuple<int, int, int, int, int, int> PlanKey;  // k, kh, T, B, nt, key bytes
+typedef std::tuple<int, int, int, int, int, int, int> PlanKey;  // k, kh, T, TH, B, nt, key bytes
 static std::map<PlanKey, D1Plan *> *g_plans = new std::map<PlanKey, D1Plan *>();
-static std::map<std::tuple<int, int, int, int, int, int, int>, D1Cached *> *g_d1 =
-    new std::map<std::tuple<int, int, int, int, int, int, int>, D1Cached *>();
+static std::map<std::tuple<int, int, int, int, int, int, int, int>, D1Cached *> *g_d1 =
+    new std::map<std::tuple<int, int, int, int, int, int, int, int>, D1Cached *>();
 
 static size_t key_bytes(int dtype, bool arg) {
     const bool wide = dtype == MF_U32 || dtype == MF_F32;
@@ -168,14 +168,15 @@ static size_t key_bytes(int dtype, bool arg) {
 
 // Host plan for a window of k columns by kh rows (kh = 0: square); nullptr
 // if none exists.  No device work.
-static const D1Plan *host_plan(int k, int T, int B, int nt, int kb, int kh = 0) {
+static const D1Plan *host_plan(int k, int T, int B, int nt, int kb, int kh = 0, int TH = 0) {
     if (kh == 0) kh = k;
+    if (TH == 0) TH = T;
     std::lock_guard<std::mutex> lk(g_d1_mu);
-    const PlanKey key(k, kh, T, B, nt, kb);
+    const PlanKey key(k, kh, T, TH, B, nt, kb);
     auto it = g_plans->find(key);
     if (it != g_plans->end()) return it->second;
     D1Plan *pl = new D1Plan();
-    if (!d1_build_plan(k, T, pl, B, nt, kb, kh)) {
+    if (!d1_build_plan(k, T, pl, B, nt, kb, kh, TH)) {
         delete pl;
         pl = nullptr;
     }
@@ -186,16 +187,18 @@ static const D1Plan *host_plan(int k, int T, int B, int nt, int kb, int kh = 0) 
 // Strip width and block size for a root tile: the widest strip (sharing the
 // most column sorts) whose state fits the small budget runs with 256 threads
 // and several blocks per SM; otherwise one tile with 512 threads.
-static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt, int kh = 0) {
+static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt, int kh = 0, int TH = 0) {
     if (kh == 0) kh = k;
-    const int kmin = k < kh ? k : kh;
-    // a 1 x 1 root tile only where the window is one pixel wide or high
-    if (k < 1 || k > 75 || !(k & 1) || kh < 1 || kh > 75 || !(kh & 1) || k * kh < 3 || T < (kmin < 3 ? 1 : 2) ||
-        T > 32 || (T & (T - 1)) || T > kmin)
+    if (TH == 0) TH = T;
+    // square windows keep root tiles of at least 2 x 2; a side of 1 only
+    // where the window is that thin
+    const bool square = kh == k && TH == T;
+    if (k < 1 || k > 75 || !(k & 1) || kh < 1 || kh > 75 || !(kh & 1) || k * kh < 3 || T < 1 || TH < 1 ||
+        (square && T < 2) || T > 32 || TH > 32 || (T & (T - 1)) || (TH & (TH - 1)) || T > k || TH > kh)
         return false;
     const int kb = (int)key_bytes(dtype, arg);
     for (int b = 8; b >= 1; b /= 2) {
-        const D1Plan *p = host_plan(k, T, b, 256, kb, kh);
+        const D1Plan *p = host_plan(k, T, b, 256, kb, kh, TH);
         if (p && (size_t)p->smem_elems * kb <= D1_SMEM_SMALL) {
             *B = b;
             *nt = 256;
@@ -204,13 +207,13 @@ static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt, in
     }
     // one tile per block: 512 threads when two blocks share an SM, else
     // 1024 threads (32 warps) in a block of its own
-    const D1Plan *p5 = host_plan(k, T, 1, 512, kb, kh);
+    const D1Plan *p5 = host_plan(k, T, 1, 512, kb, kh, TH);
     if (p5 && 2 * ((size_t)p5->smem_elems * kb + 1024) <= 227 * 1024) {
         *B = 1;
         *nt = 512;
         return true;
     }
-    const D1Plan *p = host_plan(k, T, 1, 1024, kb, kh);
+    const D1Plan *p = host_plan(k, T, 1, 1024, kb, kh, TH);
     if (p && (size_t)p->smem_elems * kb <= D1_SMEM_BUDGET) {
         *B = 1;
         *nt = 1024;
@@ -220,9 +223,10 @@ static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt, in
 }
 
 // Plan uploaded to the current device (once per device).
-static D1Cached *get_plan(int k, int T, int B, int nt, int kb, int kh = 0) {
+static D1Cached *get_plan(int k, int T, int B, int nt, int kb, int kh = 0, int TH = 0) {
     if (kh == 0) kh = k;
-    const D1Plan *hp = host_plan(k, T, B, nt, kb, kh);
+    if (TH == 0) TH = T;
+    const D1Plan *hp = host_plan(k, T, B, nt, kb, kh, TH);
     if (!hp) return nullptr;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -230,7 +234,7 @@ static D1Cached *get_plan(int k, int T, int B, int nt, int kb, int kh = 0) {
         return nullptr;
     }
     std::lock_guard<std::mutex> lk(g_d1_mu);
-    auto key = std::make_tuple(k, kh, T, B, nt, kb, dev);
+    auto key = std::make_tuple(k, kh, T, TH, B, nt, kb, dev);
     auto it = g_d1->find(key);
     if (it != g_d1->end()) return it->second;
     D1Cached *c = new D1Cached();
@@ -264,6 +268,7 @@ static D1Cached *get_plan(int k, int T, int B, int nt, int kb, int kh = 0) {
     c->dev.k = k;
     c->dev.kh = hp->kh;
     c->dev.T = T;
+    c->dev.TH = hp->TH;
     c->dev.B = B;
     c->dev.FW = pl.FW;
     c->dev.FH = pl.FH;
@@ -299,6 +304,32 @@ int d1_default_tile(int k, int dtype, bool arg, int kh) {
 
 int d1_supported(int k, int dtype, bool arg) { return d1_default_tile(k, dtype, arg) != 0; }
 
+// Root tile for a window of kw columns by kh rows: t(k) = 2^(floor(log2 k) - 1)
+// (paper Sec. 4.2) per side, at least 1 and at most 16 (16 for 2-byte keys
+// from a side of 27), the longer tile side halved until the tree's state
+// fits in shared memory.
+static bool rect_tiles(int kw, int kh, int dtype, bool arg, int *TW, int *TH) {
+    auto t_of = [&](int k) {
+        int t = 1;
+        while (t * 4 <= k) t *= 2;
+        if (t > 16) t = 16;
+        if (key_bytes(dtype, arg) == 2 && k >= 27) t = 16;
+        return t;
+    };
+    int tw = t_of(kw), th = t_of(kh);
+    for (;;) {
+        int B, nt;
+        if (choose_config(kw, dtype, arg, tw, &B, &nt, kh, th)) {
+            *TW = tw;
+            *TH = th;
+            return true;
+        }
+        if (tw == 1 && th == 1) return false;
+        if (tw >= th) tw /= 2;
+        else th /= 2;
+    }
+}
+
 template <class KT, int DT, bool ARG, int NMAX>
 static int d1_launch_n(const ImgArgs &a, int C, const D1Cached *c, int nt, cudaStream_t s) {
     const size_t smem = (size_t)c->plan.smem_elems * sizeof(KT);
@@ -311,7 +342,7 @@ static int d1_launch_n(const ImgArgs &a, int C, const D1Cached *c, int nt, cudaS
         configured = true;
     }
     const int SW = c->plan.B * c->plan.T;
-    dim3 grid((a.W + SW - 1) / SW, (a.H + c->plan.T - 1) / c->plan.T, C);
+    dim3 grid((a.W + SW - 1) / SW, (a.H + c->plan.TH - 1) / c->plan.TH, C);
     kern<<<grid, nt, smem, s>>>(a, c->dev);
     count_launch();
     return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;
@@ -327,13 +358,20 @@ static int d1_launch_t(const ImgArgs &a, int C, const D1Cached *c, int nt, cudaS
 
 int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s, int kh) {
     const bool arg = a.idx != nullptr;
+    int TH = 0;
+    if (kh != 0 && kh != k && T == 0) {  // rectangular window: rectangular root tile
+        if (!rect_tiles(k, kh, dtype, arg, &T, &TH)) {
+            set_error("no data-aware plan for a %dx%d window", k, kh);
+            return MF_ERR_UNSUPPORTED;
+        }
+    }
     if (T == 0) T = d1_default_tile(k, dtype, arg, kh);
     int B, nt;
-    if (!choose_config(k, dtype, arg, T, &B, &nt, kh)) {
+    if (!choose_config(k, dtype, arg, T, &B, &nt, kh, TH)) {
         set_error("no data-aware plan for a %dx%d window, tile=%d", k, kh ? kh : k, T);
         return MF_ERR_UNSUPPORTED;
     }
-    const D1Cached *c = get_plan(k, T, B, nt, (int)key_bytes(dtype, arg), kh);
+    const D1Cached *c = get_plan(k, T, B, nt, (int)key_bytes(dtype, arg), kh, TH);
     if (!c) {
         set_error("cannot allocate or upload the data-aware plan for k=%d tile=%d", k, T);
         return MF_ERR_ALLOC;

@@ -76,23 +76,27 @@ def test_work_per_pixel_linear_in_k():
     assert max(per) / min(per) < 2.0
 
 
-RECT = [(1, 5, 1, 1), (5, 1, 1, 1), (3, 9, 2, 1), (9, 3, 2, 2), (7, 5, 4, 1), (15, 5, 4, 2), (5, 31, 4, 1),
-        (31, 9, 8, 1), (25, 13, 8, 2), (3, 75, 2, 1), (75, 3, 2, 1)]
+RECT = [(1, 5, 1, 1, 1), (5, 1, 1, 1, 1), (3, 9, 2, 2, 1), (9, 3, 2, 2, 2), (7, 5, 4, 4, 1), (15, 5, 4, 4, 2),
+        (5, 31, 4, 4, 1), (31, 9, 8, 8, 1), (25, 13, 8, 8, 2), (3, 75, 2, 2, 1), (75, 3, 2, 2, 1),
+        # rectangular root tiles (t_w x t_h, Sec. 3.2)
+        (31, 7, 8, 1, 1), (31, 7, 8, 2, 2), (7, 31, 1, 8, 1), (7, 31, 2, 8, 2), (1, 25, 1, 8, 1),
+        (25, 1, 8, 1, 2), (15, 3, 4, 1, 1), (45, 13, 16, 4, 1), (9, 17, 2, 4, 3)]
 
 
-@pytest.mark.parametrize("kw,kh,T,B", RECT)
-def test_rect_plan_matches_oracle(kw, kh, T, B):
-    """Windows of kw columns by kh rows (paper Sec. 3.2 terminology for a
-    k_w x k_h kernel): the planned tree's medians for a strip's footprint
-    against the oracle's rectangular filter."""
-    FH, FW = T + kh - 1, B * T + kw - 1
+@pytest.mark.parametrize("kw,kh,TW,TH,B", RECT)
+def test_rect_plan_matches_oracle(kw, kh, TW, TH, B):
+    """Windows of kw columns by kh rows and root tiles of TW x TH (paper
+    Sec. 3.2 terminology for a k_w x k_h kernel and t_w x t_h tiles): the
+    planned tree's medians for a strip's footprint against the oracle's
+    rectangular filter."""
+    FH, FW = TH + kh - 1, B * TW + kw - 1
     rx, ry = kw // 2, kh // 2
     for s in range(2):
         gen = synth.levels16 if s else synth.uniform
-        img = gen((FH, FW), "u16", 13 * kw + kh + T + s)
-        st, med = mf.mf_d1_plan_check(kw, T, img.astype(np.uint64).ravel(), strip=B, kh=kh)
-        want = oracle.median_filter(img, kw, kh=kh)[ry:ry + T, rx:rx + B * T].ravel()
-        assert np.array_equal(med.astype(np.uint16), want), (kw, kh, T, B, s)
+        img = gen((FH, FW), "u16", 13 * kw + kh + TW + TH + s)
+        st, med = mf.mf_d1_plan_check(kw, TW, img.astype(np.uint64).ravel(), strip=B, kh=kh, tile_h=TH)
+        want = oracle.median_filter(img, kw, kh=kh)[ry:ry + TH, rx:rx + B * TW].ravel()
+        assert np.array_equal(med.astype(np.uint16), want), (kw, kh, TW, TH, B, s)
 
 
 def test_rect_plan_square_case_unchanged():
