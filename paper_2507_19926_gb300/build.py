@@ -216,24 +216,51 @@ def generate():
     return tus
 
 
+def _includes(path, seen):
+    """path and every file it includes with #include "..." (transitively),
+    resolved like the build's -I list."""
+    if path in seen:
+        return
+    seen.append(path)
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line.startswith("#include \""):
+                name = line.split('"')[1]
+                for d in (os.path.dirname(path), INCLUDE, CSRC, GEN):
+                    cand = os.path.normpath(os.path.join(d, name))
+                    if os.path.exists(cand):
+                        _includes(cand, seen)
+                        break
+
+
 def kernel_source_hash(fn_name):
-    """Build hash (generated translation unit + headers + flags) of the TU
-    that defines the registry launch function fn_name, or None: profiles
-    record it beside ncu counters, so a reader can tell whether the counters
-    still describe the kernel that is built."""
+    """Hash of the sources of the registry launch function fn_name -- its
+    generated translation unit, every file that includes (transitively) and
+    the compiler flags -- or None: profiles record it beside ncu counters,
+    so a reader can tell whether the counters still describe the kernel
+    that is built."""
     if not os.path.isdir(GEN):
         return None
     needle = "int %s(" % fn_name
     root = os.path.dirname(HERE)
-    # include paths name this checkout's location: hash them relative to it,
-    # so that every checkout of the same sources gives the same hash
-    flags = [f.replace(root, "<repo>") for f in NVCC_FLAGS + ARCH]
     for name in sorted(os.listdir(GEN)):
         if name.startswith("o1_k") and name.endswith(".cu"):
             path = os.path.join(GEN, name)
             with open(path) as f:
-                if needle in f.read():
-                    return _flags_hash(path, flags)
+                if needle not in f.read():
+                    continue
+            files = []
+            _includes(path, files)
+            h = hashlib.sha1()
+            # include paths name this checkout's location: hash them relative
+            # to it, so that every checkout of the same sources agrees
+            h.update(" ".join(f.replace(root, "<repo>") for f in NVCC_FLAGS + ARCH).encode())
+            for fp in files:
+                h.update(os.path.relpath(fp, root).encode())
+                with open(fp, "rb") as f:
+                    h.update(f.read())
+            return h.hexdigest()[:16]
     return None
 
 
