@@ -16,7 +16,10 @@ Parity status: pinned.  The value path is pinned by hand-worked fixtures,
 scipy.ndimage's median filter, the counting characterisation of a rank,
 k=1, constant images and monotone remaps; the argmedian tie rule by
 hand-worked fixtures with ties; the backward by a hand-worked case and
-central finite differences.
+central finite differences.  The volumetric k x k x k filter
+(``median_filter_3d``) is pinned by scipy.ndimage's 3D median, a numpy brute
+force over an edge-padded volume, the one-slice reduction to the 2D filter,
+axis permutations, constants and k = 1.
 """
 import ctypes
 import os
@@ -61,6 +64,7 @@ def _load():
             lib.or_median_filter_rect.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, i32, i32]
             lib.or_median_filter_rows.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, vp, i32, i32]
             lib.or_median_backward.argtypes = [vp, vp, vp, i32, i32, i32]
+            lib.or_median_filter_3d.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, i32]
             lib.or_key.argtypes = [i32, u32]
             lib.or_key.restype = u32
             lib.or_max_threads.restype = i32
@@ -128,6 +132,26 @@ def median_filter_rows(x, k, rows, with_idx=False, threads=0):
         out = out[0]
         idx = idx[0] if with_idx else None
     return (out, idx) if with_idx else out
+
+
+def median_filter_3d(x, k, threads=0):
+    """Clamp-to-edge k x k x k median of a volume (D, H, W) or of volumes
+    (V, D, H, W): the 3D extension of the filter that the paper names as
+    future work (Sec. 7.2).  Values only."""
+    lib = _load()
+    x = np.ascontiguousarray(x)
+    squeeze = x.ndim == 3
+    if squeeze:
+        x = x[None]
+    if x.ndim != 4:
+        raise ValueError("expected (D, H, W) or (V, D, H, W)")
+    V, D, H, W = x.shape
+    out = np.empty_like(x)
+    rc = lib.or_median_filter_3d(x.ctypes.data, out.ctypes.data, D, H, W, V, DTYPES[_dtype_name(x)],
+                                 int(k), int(threads))
+    if rc != 0:
+        raise ValueError("oracle rejected arguments (D=%d H=%d W=%d k=%d)" % (D, H, W, k))
+    return out[0] if squeeze else out
 
 
 def median_backward(grad_out, idx):

@@ -213,6 +213,59 @@ int or_median_filter_rows(const void *src, void *dst, int32_t *idx, int H, int W
     return 0;
 }
 
+/* Volumetric k x k x k median (the extension of hierarchical tiling to 3D
+ * that the paper names as future work, Sec. 7.2, for medical volumes).
+ * Definition: voxel (z, y, x) of a D x H x W volume is replaced by the
+ * element of 0-based rank (k^3 - 1)/2 of the multiset of the k^3 values
+ * src[clamp(z+dz)][clamp(y+dy)][clamp(x+dx)], dz, dy, dx in [-r, r],
+ * under the same order keys as the 2D filter; borders clamp to the edge on
+ * every axis.  Values only.  V volumes, each D*H*W elements contiguous,
+ * slice-major then row-major.  Returns 0, or -1 on a bad argument. */
+int or_median_filter_3d(const void *src, void *dst, int D, int H, int W, int V, int dtype, int k,
+                        int nthreads)
+{
+    if (check_args(H, W, V, dtype, k) || D < 1) return -1;
+    int es = elem_size(dtype), r = (k - 1) / 2;
+    long vol = (long)D * H * W, n = (long)k * k * k;
+    long rows = (long)V * D * H;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel num_threads(nthreads)
+#endif
+    {
+        uint64_t *win = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (long row = 0; row < rows; row++) {
+            int v = (int)(row / ((long)D * H)), z = (int)((row / H) % D), y = (int)(row % H);
+            const char *base = (const char *)src + (size_t)v * vol * es;
+            for (int x = 0; x < W; x++) {
+                int s = 0;
+                for (int dz = -r; dz <= r; dz++)
+                    for (int dy = -r; dy <= r; dy++)
+                        for (int dx = -r; dx <= r; dx++) {
+                            long si = ((long)clampi(z + dz, 0, D - 1) * H + clampi(y + dy, 0, H - 1)) * W +
+                                      clampi(x + dx, 0, W - 1);
+                            win[s] = ((uint64_t)key_at(base, si, dtype) << 32) | (uint64_t)s;
+                            s++;
+                        }
+                /* entries are distinct (slot s breaks key ties); the winner's
+                 * slot gives back its source voxel */
+                uint64_t best = select_rank(win, (int)n, (int)((n - 1) / 2));
+                int bs = (int)(best & 0xffffffffu);
+                int dz = bs / (k * k) - r, dy = (bs / k) % k - r, dx = bs % k - r;
+                long si = ((long)clampi(z + dz, 0, D - 1) * H + clampi(y + dy, 0, H - 1)) * W +
+                          clampi(x + dx, 0, W - 1);
+                long o = (long)v * vol + ((long)z * H + y) * W + x;
+                memcpy((char *)dst + (size_t)o * es, base + (size_t)si * es, es);
+            }
+        }
+        free(win);
+    }
+    return 0;
+}
+
 /* Gradient of the filter: grad_in = 0, then for every plane and every
  * output q in row-major order, grad_in[idx[q]] += grad_out[q] (f32). */
 int or_median_backward(const float *grad_out, const int32_t *idx, float *grad_in,

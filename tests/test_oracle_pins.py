@@ -234,3 +234,64 @@ def test_rect_transpose_symmetry_and_square_case():
     yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
     assert (np.abs(ys - yy[None]) <= 1).all() and (np.abs(xs - xx[None]) <= 3).all()
     assert (np.take_along_axis(x.reshape(2, -1), ia.reshape(2, -1), 1).reshape(a.shape) == a).all()
+
+
+# ---------------------------------------------------------------- volumes
+# The k x k x k median of a volume (the 3D extension of hierarchical tiling,
+# Sec. 7.2).  Pins: scipy's 3D median with nearest borders, a numpy brute
+# force over an edge-padded volume, one slice reducing to the 2D filter, the
+# cube's symmetry under axis permutations, constants and k = 1.
+
+
+@pytest.mark.parametrize("dt", ["u8", "u16", "u32", "f32"])
+@pytest.mark.parametrize("k", [3, 5, 7])
+def test_volume_matches_scipy_nearest(dt, k):
+    scipy_nd = pytest.importorskip("scipy.ndimage")
+    shape = (6, 9, 13) if k < 7 else (5, 8, 11)
+    x = synth.normal_f32(shape, 300 + k) if dt == "f32" else synth.uniform(shape, dt, 300 + k)
+    np.testing.assert_array_equal(oracle.median_filter_3d(x, k),
+                                  scipy_nd.median_filter(x, size=k, mode="nearest"))
+    xl = synth.levels16(shape, dt, 400 + k)
+    np.testing.assert_array_equal(oracle.median_filter_3d(xl, k),
+                                  scipy_nd.median_filter(xl, size=k, mode="nearest"))
+
+
+def test_volume_brute_force_edge_padded():
+    """Rank (k^3-1)/2 of the window gathered from an edge-padded volume."""
+    for k, shape, seed in ((3, (4, 5, 6), 1), (5, (3, 7, 4), 2), (3, (1, 1, 9), 3)):
+        x = synth.levels16(shape, "u16", 500 + seed)
+        r = k // 2
+        p = np.pad(x, r, mode="edge")
+        want = np.empty_like(x)
+        for z in range(shape[0]):
+            for y in range(shape[1]):
+                for xx in range(shape[2]):
+                    w = np.sort(p[z:z + k, y:y + k, xx:xx + k].ravel())
+                    want[z, y, xx] = w[(k ** 3 - 1) // 2]
+        np.testing.assert_array_equal(oracle.median_filter_3d(x, k), want)
+
+
+@pytest.mark.parametrize("k", [3, 5, 9])
+def test_volume_single_slice_is_2d_filter(k):
+    """With one slice, clamping repeats it k times: each value of the 2D
+    window appears k times, and rank (k^3-1)/2 = k*(k^2-1)/2 + (k-1)/2 falls
+    in the block of copies of the 2D median (rank (k^2-1)/2)."""
+    x = synth.uniform((1, 21, 34), "u8", 600 + k)
+    np.testing.assert_array_equal(oracle.median_filter_3d(x, k)[0], oracle.median_filter(x[0], k))
+
+
+def test_volume_axis_permutations_commute():
+    x = synth.uniform((7, 10, 12), "u32", 700)
+    base = oracle.median_filter_3d(x, 5)
+    for perm in ((1, 0, 2), (2, 1, 0), (0, 2, 1), (1, 2, 0)):
+        got = oracle.median_filter_3d(np.ascontiguousarray(x.transpose(perm)), 5)
+        np.testing.assert_array_equal(got, base.transpose(perm))
+
+
+def test_volume_constant_and_identity():
+    c = np.full((5, 6, 7), 77, np.uint16)
+    np.testing.assert_array_equal(oracle.median_filter_3d(c, 5), c)
+    x = synth.uniform((2, 4, 5, 6), "f32", 800)
+    np.testing.assert_array_equal(oracle.median_filter_3d(x, 1).view(np.uint32), x.view(np.uint32))
+    with pytest.raises(ValueError):
+        oracle.median_filter_3d(x, 4)
