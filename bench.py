@@ -424,6 +424,29 @@ def bench_sweep(dev, stream, flush, reps=3, ks=(3, 5, 9, 15, 21, 31, 45, 75), dt
     return res
 
 
+def bench_volume(dev, stream, flush, reps=3, cases=(("u8", 3), ("u8", 5), ("u8", 7), ("u8", 9), ("u8", 15),
+                                                      ("u8", 19), ("u16", 7), ("f32", 3), ("f32", 7), ("f32", 19))):
+    """256^3 single volumes, uniform values: the k x k x k median by
+    hierarchical tiling in 3D (mf_median_filter_3d)."""
+    import torch
+    import paper_2507_19926_gb300 as mf
+    from paper_2507_19926_gb300 import synth
+    codes = {"u8": mf.MF_U8, "u16": mf.MF_U16, "u32": mf.MF_U32, "f32": mf.MF_F32}
+    res = []
+    sptr = stream.cuda_stream
+    n = 256
+    for dt, k in cases:
+        x = to_device(synth.uniform((n, n, n), dt, synth.SEED_BASE + 5), dev)
+        y = torch.empty_like(x)
+        pitch = n * x.element_size()
+        f = lambda: mf.mf_median_filter_3d(x.data_ptr(), y.data_ptr(), n, n, n, pitch, 1, codes[dt], k, sptr)
+        f()
+        ms = _time_ms(f, stream, reps, flush)
+        res.append({"dtype": dt, "k": k, "ms": round(ms, 4), "mvox_s": round(n ** 3 / ms / 1e3, 1),
+                    "plan": mf.mf_median_filter_3d_describe(k, codes[dt])})
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -556,6 +579,7 @@ def run_ours(args):
         extra["fwd_bwd_vs_fwd"] = bench_fwd_bwd(dev, stream, flush)
         extra["sweep_4096"] = bench_sweep(dev, stream, flush)
         extra["rect_4096"] = bench_rect(dev, stream, flush)
+        extra["volume_256"] = bench_volume(dev, stream, flush)
     out = {
         "metric": "median filter throughput (output channel-pixels per second)",
         "value": value, "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

@@ -26,14 +26,16 @@ MF_GRAD_ATOMIC, MF_GRAD_DETERMINISTIC = 0, 1
 VARIANTS = {"auto": MF_AUTO, "oblivious": MF_OBLIVIOUS, "data_aware": MF_DATA_AWARE}
 GRAD_MODES = {"atomic": MF_GRAD_ATOMIC, "deterministic": MF_GRAD_DETERMINISTIC}
 
-# C symbols declared in include/medianfilter.h
+# C symbols declared in include/medianfilter.h and include/medianfilter_volume.h
 EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_tile", "mf_median_filter_config",
            "mf_median_filter_rect", "mf_d1_plan_check_rect",
            "mf_median_filter_bwd",
            "mf_median_filter_host", "mf_batch_plan_create", "mf_batch_run",
            "mf_batch_plan_destroy", "mf_batch_describe", "mf_batch_run_static", "mf_autotune", "mf_describe", "mf_kernel_launch_count",
            "mf_status_string", "mf_last_error", "mf_version", "mf_shutdown", "mf_probe_minmax",
-           "mf_d1_plan_check"]
+           "mf_d1_plan_check",
+           # include/medianfilter_volume.h
+           "mf_median_filter_3d", "mf_median_filter_3d_describe", "mf_d3_plan_check"]
 
 
 class MedianFilterError(RuntimeError):
@@ -81,6 +83,9 @@ def load_library(path=LIB_PATH):
         lib.mf_kernel_launch_count.restype = u64
         lib.mf_probe_minmax.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         lib.mf_d1_plan_check.argtypes = [i, i, i, vp, vp, vp]
+        lib.mf_median_filter_3d.argtypes = [vp, vp, i, i, i, sz, i, i, i, vp]
+        lib.mf_median_filter_3d_describe.argtypes = [i, i, ctypes.c_char_p, sz]
+        lib.mf_d3_plan_check.argtypes = [i, i, vp, vp, vp]
         lib.mf_status_string.argtypes = [i]
         lib.mf_status_string.restype = ctypes.c_char_p
         lib.mf_last_error.restype = ctypes.c_char_p
@@ -213,6 +218,33 @@ def mf_d1_plan_check(k, tile, footprint=None, strip=1, kh=None, tile_h=None):
     return dict(zip(names, [int(v) for v in st])), med
 
 
+def mf_median_filter_3d(src, dst, D, H, W, pitch, volumes, dtype, k, stream=None):
+    return _check(load_library().mf_median_filter_3d(src, dst, D, H, W, pitch, volumes, dtype, k, stream))
+
+
+def mf_median_filter_3d_describe(k, dtype):
+    buf = ctypes.create_string_buffer(512)
+    _check(load_library().mf_median_filter_3d_describe(k, dtype, buf, 512))
+    return buf.value.decode()
+
+
+def mf_d3_plan_check(k, tile, footprint=None):
+    """Builds the volumetric schedule for (k, tile); with a uint64 footprint
+    of keys (F = tile + k - 1 a side, element (fx, fy, fz) at
+    (fy*F + fx)*F + fz) also runs it on the CPU.  Returns (stats dict,
+    tile^3 medians in (z, y, x) order or None)."""
+    import numpy as np
+    st = np.zeros(7, np.int32)
+    med = fp = None
+    if footprint is not None:
+        fp = np.ascontiguousarray(footprint, dtype=np.uint64)
+        med = np.zeros(tile ** 3, np.uint64)
+    _check(load_library().mf_d3_plan_check(k, tile, fp.ctypes.data if fp is not None else None,
+                                           med.ctypes.data if med is not None else None, st.ctypes.data))
+    names = ["smem_elems", "phases", "tasks", "work_items", "merged", "sorted", "max_sort"]
+    return dict(zip(names, [int(v) for v in st])), med
+
+
 def mf_version():
     return load_library().mf_version().decode()
 
@@ -289,6 +321,24 @@ def median_filter(x, k, variant="auto", return_idx=False, out=None, kh=None):
                                 MF_BORDER_CLAMP, VARIANTS[variant],
                                 idx.data_ptr() if idx is not None else None, 4 * W, _stream_ptr(x))
     return (out, idx) if return_idx else out
+
+
+def median_filter_3d(x, k, out=None):
+    """k x k x k clamp-to-edge median of every (D, H, W) volume of a CUDA
+    tensor (..., D, H, W) of u8, u16, u32 or f32 (mf_median_filter_3d)."""
+    torch = _torch()
+    if x.dim() < 3:
+        raise MedianFilterError("need (..., D, H, W)")
+    slices, H, W, pitch = _planes(x)
+    D = int(x.shape[-3])
+    if out is None:
+        out = torch.empty_like(x, memory_format=torch.contiguous_format)
+    if _planes(out) != (slices, H, W, pitch):
+        raise MedianFilterError("out must have the layout of x")
+    with torch.cuda.device(x.device):
+        mf_median_filter_3d(x.data_ptr(), out.data_ptr(), D, H, W, pitch, slices // D, dtype_code(x.dtype), int(k),
+                            _stream_ptr(x))
+    return out
 
 
 def median_filter_backward(grad_out, idx, k, mode="atomic"):

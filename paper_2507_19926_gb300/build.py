@@ -274,8 +274,10 @@ def _flags_hash(src, flags):
         if name.endswith((".cuh", ".h")):
             with open(os.path.join(CSRC, name), "rb") as f:
                 h.update(f.read())
-    with open(os.path.join(INCLUDE, "medianfilter.h"), "rb") as f:
-        h.update(f.read())
+    for name in sorted(os.listdir(INCLUDE)):
+        if name.endswith(".h"):
+            with open(os.path.join(INCLUDE, name), "rb") as f:
+                h.update(f.read())
     for name in sorted(os.listdir(GEN)):
         if name.endswith(".cuh"):
             with open(os.path.join(GEN, name), "rb") as f:

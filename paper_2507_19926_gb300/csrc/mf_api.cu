@@ -505,6 +505,7 @@ int mf_shutdown(void) {
         g_stage_events[i] = nullptr;
     }
     d1_release_all();
+    d3_release_all();
     return MF_OK;
 }
 

@@ -25,6 +25,7 @@
 #include <cstdio>
 #include <functional>
 #include <map>
+#include <tuple>
 
 #include "../../include/medianfilter.h"
 #include "mf_d1_ops.cuh"
@@ -178,6 +179,8 @@ static void keep_range(int n, int c, int d, int n_held, int *lo, int *hi) {
 
 }  // namespace
 
+static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int nt, int key_bytes, D1Plan *plan);
+
 bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, int kh, int TH) {
     // k: window width (columns), kh: window height (rows); root tile T
     // columns by TH rows
@@ -289,6 +292,23 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
         for (int i = 0; i < TW; i++) outs[j * NB * TW + bx + i] = core[j][i];
     }  // root tiles of the strip
 
+    plan->k = kw;
+    plan->kh = kh;
+    plan->T = TW;
+    plan->TH = TH;
+    plan->B = NB;
+    plan->FW = FW;
+    plan->FH = FH;
+    plan->FD = 1;
+    plan->TD = 1;
+    return finish_plan(B, outs, FW * FH, nt, key_bytes, plan);
+}
+
+// Liveness, phases, shared-memory allocation and the emitted task list of a
+// built tree (outs: the list holding each output's median, in output order;
+// the footprint occupies the first `base` elements).  The geometry fields of
+// `plan` are set by the caller.
+static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int nt, int key_bytes, D1Plan *plan) {
     // ---------------------------------------------------------- liveness
     for (const Ref &r : outs) {
         if (r.len != 1) return false;
@@ -329,7 +349,6 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
 
     // ---------------------------------------------------------- allocation
     // first fit over a free list, phase by phase; the footprint sits at 0
-    const int base = FW * FH;
     std::vector<std::pair<int, int>> freel;  // (off, len), sorted by off
     int top = base;
     std::vector<std::vector<int>> prod(nph + 1), dies(nph + 2);
@@ -376,13 +395,6 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
     }
 
     // ---------------------------------------------------------- emit
-    plan->k = kw;
-    plan->kh = kh;
-    plan->T = TW;
-    plan->TH = TH;
-    plan->B = NB;
-    plan->FW = FW;
-    plan->FH = FH;
     plan->nt = nt;
     plan->smem_elems = top;
     plan->tasks.clear();
@@ -445,15 +457,178 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
         }
     }
     plan->phase_begin.push_back((int)plan->work.size());
-    plan->out_off.resize(NB * TW * TH);
-    for (int i = 0; i < NB * TW * TH; i++) plan->out_off[i] = resolve(outs[i]);
+    plan->out_off.resize(outs.size());
+    for (size_t i = 0; i < outs.size(); i++) plan->out_off[i] = resolve(outs[i]);
     // limits of the packed device form
     for (const D1Task &t : plan->tasks)
         if (t.a_off >= (1 << 17) || t.b_off >= (1 << 17) || t.out_off >= (1 << 17) || t.a_len >= (1 << 13) ||
             t.b_len >= (1 << 13) || t.lo >= (1 << 13) || t.hi >= (1 << 13) || t.chunk >= 64 ||
-            (t.type == D1_SORT && t.a_stride != 1 && t.a_stride != FW))
+            (t.type == D1_SORT && t.a_stride != 1 && t.a_stride != plan->FW))
             return false;
     return plan->tasks.size() < (1u << 20);
+}
+
+// ---------------------------------------------------------------- volumes
+// Hierarchical tiling of a k x k x k window over a T x T x T root tile of
+// voxels (the extension to 3D that the paper names as future work, Sec. 7.2).
+// A node is a box of tx x ty x tz outputs; its core is the box of window
+// positions all of them share, (k - tx + 1) x (k - ty + 1) x (k - tz + 1),
+// kept sorted and pruned to the ranks that can still hold the median
+// (forgetfulness, Sec. 2.2: with n = k^3, core size c and d values dropped
+// below, held ranks [max(0, m - d - (n - c)), min(held - 1, m - d)]).  A split
+// halves the longest side (x, then y, then z on ties -- the 2D rule of
+// Sec. 3.1 extended by one axis); each child's core grows by the h = t/2
+// planes of window positions on its side, over the parent core's other two
+// ranges (Sec. 3.4: the new columns or rows merged into the core).  Sorted
+// planes are assembled from sorted lines of the footprint (z pillars, or x
+// lines for planes one voxel deep) and memoised by box, so a plane that a
+// node of a deeper level needs over wider ranges extends the narrower copy
+// an earlier level sorted, the way sorted extra rows and columns are
+// extended by their corners in 2D.
+//
+// Footprint layout: F = T + k - 1 per side, element (fx, fy, fz) at
+// (fy * F + fx) * F + fz (z innermost), so z pillars are contiguous and x
+// lines have stride F (the plan's FW).  Output (ox, oy, oz) of the root
+// tile is entry (oz * T + oy) * T + ox of out_off.
+namespace {
+struct Box {
+    int x0, x1, y0, y1, z0, z1;  // inclusive ranges in footprint coordinates
+    long long vol() const { return (long long)(x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1); }
+    bool inside(const Box &o) const {
+        return x0 >= o.x0 && x1 <= o.x1 && y0 >= o.y0 && y1 <= o.y1 && z0 >= o.z0 && z1 <= o.z1;
+    }
+    std::tuple<int, int, int, int, int, int> key() const { return std::make_tuple(x0, x1, y0, y1, z0, z1); }
+};
+}  // namespace
+
+bool d3_build_plan(int k, int T, D1Plan *plan, int nt, int key_bytes) {
+    if (k < 3 || k > D3_MAX_K || (k & 1) == 0 || T < 1 || (T & (T - 1)) || T > k || T > 16) return false;
+    const int F = T + k - 1;
+    const long long n_win = (long long)k * k * k;
+    Builder B;
+    B.k = k;
+    B.T = T;
+    B.FW = F;
+    auto off = [&](int fx, int fy, int fz) { return (fy * F + fx) * F + fz; };
+    std::map<std::tuple<int, int, int, int, int, int>, std::pair<Box, Ref>> memo;
+
+    // sorted list of every window position in box b (full, never pruned)
+    std::function<Ref(const Box &)> get = [&](const Box &b) -> Ref {
+        auto it = memo.find(b.key());
+        if (it != memo.end()) return it->second.second;
+        Ref r;
+        if (b.x0 == b.x1 && b.y0 == b.y1) {
+            r = B.sort_gather(off(b.x0, b.y0, b.z0), 1, b.z1 - b.z0 + 1);
+        } else if (b.y0 == b.y1 && b.z0 == b.z1) {
+            r = B.sort_gather(off(b.x0, b.y0, b.z0), F, b.x1 - b.x0 + 1);
+        } else {
+            // the largest box already sorted inside b, if it is more than one line
+            const long long line = std::max(b.z1 - b.z0 + 1, b.x1 - b.x0 + 1);
+            const Box *best = nullptr;
+            Ref best_ref{-2, 0, 0};
+            long long best_vol = line;
+            for (const auto &kv : memo)
+                if (kv.second.first.inside(b) && kv.second.first.vol() > best_vol) {
+                    best = &kv.second.first;
+                    best_ref = kv.second.second;
+                    best_vol = best->vol();
+                }
+            std::vector<Ref> parts;
+            if (best) {
+                const Box c = *best;
+                std::vector<Box> rest;
+                if (b.x0 < c.x0) rest.push_back(Box{b.x0, c.x0 - 1, b.y0, b.y1, b.z0, b.z1});
+                if (c.x1 < b.x1) rest.push_back(Box{c.x1 + 1, b.x1, b.y0, b.y1, b.z0, b.z1});
+                if (b.y0 < c.y0) rest.push_back(Box{c.x0, c.x1, b.y0, c.y0 - 1, b.z0, b.z1});
+                if (c.y1 < b.y1) rest.push_back(Box{c.x0, c.x1, c.y1 + 1, b.y1, b.z0, b.z1});
+                if (b.z0 < c.z0) rest.push_back(Box{c.x0, c.x1, c.y0, c.y1, b.z0, c.z0 - 1});
+                if (c.z1 < b.z1) rest.push_back(Box{c.x0, c.x1, c.y0, c.y1, c.z1 + 1, b.z1});
+                for (const Box &q : rest) parts.push_back(get(q));
+                const Ref small = B.multiway(parts, 0, 1 << 30);
+                r = B.merge_full(best_ref, small);
+            } else {
+                if (b.z1 - b.z0 >= b.x1 - b.x0) {  // z pillars
+                    for (int y = b.y0; y <= b.y1; y++)
+                        for (int x = b.x0; x <= b.x1; x++) parts.push_back(get(Box{x, x, y, y, b.z0, b.z1}));
+                } else {  // x lines
+                    for (int z = b.z0; z <= b.z1; z++)
+                        for (int y = b.y0; y <= b.y1; y++) parts.push_back(get(Box{b.x0, b.x1, y, y, z, z}));
+                }
+                r = B.multiway(parts, 0, 1 << 30);
+            }
+        }
+        memo[b.key()] = std::make_pair(b, r);
+        return r;
+    };
+
+    // ---------------------------------------------------------- initialisation
+    struct Node {
+        int o[3];  // output origin (x, y, z) in the root tile
+        Ref core;
+    };
+    int t[3] = {T, T, T};
+    const Box root_core{T - 1, k - 1, T - 1, k - 1, T - 1, k - 1};
+    long long c = root_core.vol();
+    int lo, hi;
+    keep_range((int)n_win, (int)c, 0, (int)c, &lo, &hi);
+    int d = lo;
+    std::vector<Node> nodes;
+    {
+        std::vector<Ref> pillars;
+        for (int y = T - 1; y <= k - 1; y++)
+            for (int x = T - 1; x <= k - 1; x++) pillars.push_back(get(Box{x, x, y, y, T - 1, k - 1}));
+        nodes.push_back(Node{{0, 0, 0}, B.multiway(pillars, lo, hi)});
+    }
+
+    // ---------------------------------------------------------- recursion
+    while (t[0] * t[1] * t[2] > 1) {
+        const int ax = (t[0] >= t[1] && t[0] >= t[2]) ? 0 : (t[1] >= t[2] ? 1 : 2);
+        const int h = t[ax] / 2;
+        long long other = 1;
+        for (int a = 0; a < 3; a++)
+            if (a != ax) other *= k - t[a] + 1;
+        const int held = nodes[0].core.len;
+        c += (long long)h * other;
+        keep_range((int)n_win, (int)c, d, held + (int)(h * other), &lo, &hi);
+        std::vector<Node> next;
+        for (const Node &nd : nodes) {
+            int cr[3][2];  // the parent core's ranges
+            for (int a = 0; a < 3; a++) {
+                cr[a][0] = nd.o[a] + t[a] - 1;
+                cr[a][1] = nd.o[a] + k - 1;
+            }
+            for (int s = 0; s < 2; s++) {
+                const int u0 = s == 0 ? nd.o[ax] + h - 1 : nd.o[ax] + k;  // first new plane
+                std::vector<Ref> planes;
+                for (int u = u0; u < u0 + h; u++) {
+                    int rg[3][2] = {{cr[0][0], cr[0][1]}, {cr[1][0], cr[1][1]}, {cr[2][0], cr[2][1]}};
+                    rg[ax][0] = rg[ax][1] = u;
+                    planes.push_back(get(Box{rg[0][0], rg[0][1], rg[1][0], rg[1][1], rg[2][0], rg[2][1]}));
+                }
+                const Ref slab = B.multiway(planes, 0, 1 << 30);
+                Node ch = nd;
+                ch.o[ax] = nd.o[ax] + s * h;
+                ch.core = B.merge_range(nd.core, slab, lo, hi);
+                next.push_back(ch);
+            }
+        }
+        nodes.swap(next);
+        t[ax] = h;
+        d += lo;
+    }
+
+    std::vector<Ref> outs(T * T * T);
+    for (const Node &nd : nodes) outs[(nd.o[2] * T + nd.o[1]) * T + nd.o[0]] = nd.core;
+    plan->k = k;
+    plan->kh = k;
+    plan->T = T;
+    plan->TH = T;
+    plan->TD = T;
+    plan->B = 1;
+    plan->FW = F;
+    plan->FH = F;
+    plan->FD = F;
+    return finish_plan(B, outs, F * F * F, nt, key_bytes, plan);
 }
 
 void d1_pack_tasks(const D1Plan &plan, std::vector<D1Packed> *out) {
@@ -471,7 +646,7 @@ void d1_pack_tasks(const D1Plan &plan, std::vector<D1Packed> *out) {
 
 void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *medians) {
     std::vector<uint64_t> sm(plan.smem_elems, 0xdeadbeefdeadbeefull);
-    std::copy(footprint, footprint + plan.FW * plan.FH, sm.begin());
+    std::copy(footprint, footprint + (size_t)plan.FW * plan.FH * plan.FD, sm.begin());
     const int nph = (int)plan.phase_begin.size() - 1;
     std::vector<D1Packed> packed;
     d1_pack_tasks(plan, &packed);
@@ -489,7 +664,7 @@ void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *m
             }
         }
     }
-    for (int i = 0; i < plan.B * plan.T * plan.TH; i++) medians[i] = sm[plan.out_off[i]];
+    for (size_t i = 0; i < plan.out_off.size(); i++) medians[i] = sm[plan.out_off[i]];
 }
 
 }  // namespace mf
@@ -515,4 +690,21 @@ extern "C" int mf_d1_plan_check_rect(int kw, int kh, int tile_w, int tile_h, int
 extern "C" int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,
                                 int *stats) {
     return mf_d1_plan_check_rect(k, k, tile, tile, strip, footprint, medians, stats);
+}
+
+// Host check of the volumetric schedule (declared in medianfilter.h).
+extern "C" int mf_d3_plan_check(int k, int tile, const uint64_t *footprint, uint64_t *medians, int *stats) {
+    mf::D1Plan plan;
+    if (!mf::d3_build_plan(k, tile, &plan, 256, 4)) return MF_ERR_UNSUPPORTED;
+    if (stats) {
+        stats[0] = plan.smem_elems;
+        stats[1] = (int)plan.phase_begin.size() - 1;
+        stats[2] = (int)plan.tasks.size();
+        stats[3] = (int)plan.work.size();
+        stats[4] = (int)std::min<long long>(plan.merge_outputs, 2147483647ll);
+        stats[5] = (int)std::min<long long>(plan.sort_elems, 2147483647ll);
+        stats[6] = plan.max_sort;
+    }
+    if (footprint && medians) mf::d1_run_plan_host(plan, footprint, medians);
+    return MF_OK;
 }

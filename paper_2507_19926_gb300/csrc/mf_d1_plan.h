@@ -37,6 +37,8 @@ struct D1Plan {
     int B = 1;                       // root tiles per strip (side by side horizontally)
     int FW = 0;                      // footprint width B*T + k - 1 (footprint at offset 0, row-major)
     int FH = 0;                      // footprint height TH + kh - 1
+    int FD = 1;                      // volumes: footprint depth TD + k - 1 (2D: 1)
+    int TD = 1;                      // volumes: root tile depth (2D: 1)
     int nt = 256;                    // threads per block the chunking targets
     int smem_elems = 0;              // shared-memory list elements needed (footprint included)
     std::vector<D1Task> tasks;       // host form; the device gets them packed (D1Packed)
@@ -57,6 +59,18 @@ struct D1Plan {
 // false outside that range.
 bool d1_build_plan(int k, int T, D1Plan *plan, int B = 1, int nt = 256, int key_bytes = 4, int kh = 0,
                    int TH = 0);
+
+// Largest window side of the volumetric filter: list lengths and ranks of
+// the packed task form stay below 2^13 (k^3 = 6859 at k = 19).
+constexpr int D3_MAX_K = 19;
+
+// Builds the plan of a k x k x k window over a T x T x T root tile of a
+// volume (paper Sec. 7.2: hierarchical tiling extended to 3D; T a power of
+// two, 1 <= T <= min(k, 16)).  Footprint F = T + k - 1 per side at offset 0,
+// element (fx, fy, fz) at (fy * F + fx) * F + fz; medians in (z, y, x) order
+// of the root tile.  Returns false outside that range or beyond the packed
+// form's limits.
+bool d3_build_plan(int k, int T, D1Plan *plan, int nt = 256, int key_bytes = 4);
 
 struct D1Packed;
 // The 16-byte device form of every task (layout in mf_d1_ops.cuh).

@@ -38,6 +38,7 @@ int d1_default_tile(int k, int dtype, bool arg, int kh = 0);
 int d1_supported_tile(int k, int dtype, bool arg, int tile, int kh = 0);
 int d1_describe(int k, int dtype, bool arg, int tile, char *buf, size_t n);
 void d1_release_all();
+void d3_release_all();  // volumetric plans (mf_volume.cu)
 // Persistent data-aware launch over a device work list for (k, dtype); the
 // block geometry is the plan d1_geometry reports.
 int d1_geometry(int k, int dtype, bool arg, int *tile, int *strip, int *threads);

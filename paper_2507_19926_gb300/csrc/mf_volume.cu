@@ -1,0 +1,348 @@
+// Volumetric k x k x k median by hierarchical tiling: the extension to 3D
+// that the paper names as future work (Sec. 7.2), built on its data-aware
+// variant (Sec. 5).
+//
+// The tree of a T x T x T root tile of voxels -- which z pillars and x lines
+// of the footprint are sorted, which sorted planes are merged into which
+// core, which ranks each merge keeps -- depends only on (k, T) and is
+// planned on the host (d3_build_plan in mf_d1_plan.cu).  One thread block
+// owns one root tile: it stages the (T + k - 1)^3 footprint as order keys in
+// shared memory (clamped to the volume on every axis), runs the planned
+// phases with a barrier between them (register sorting networks for the
+// lines, merge-path chunks for the merges, the same code as the 2D
+// data-aware kernel), and writes the T^3 medians.  Nothing but the volume
+// and the medians touches HBM.
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "../../include/medianfilter_volume.h"
+#include "d1_sortnets.cuh"
+#include "mf_d1_ops.cuh"
+#include "mf_registry.h"
+
+namespace mf {
+
+constexpr size_t D3_SMEM_BUDGET = 200 * 1024;
+constexpr size_t D3_SMEM_SMALL = 56 * 1024;  // 256 threads, several blocks a SM
+
+struct D3Dev {
+    const D1Packed *tasks;
+    const uint32_t *work;
+    const int32_t *phase_begin;
+    const int32_t *out_off;
+    int nphases;
+    int k, T, F;
+};
+
+struct VolArgs {
+    const char *src;
+    char *dst;
+    int D, H, W;
+    size_t pitch;   // bytes per row
+    size_t slice;   // bytes per slice = H * pitch
+    size_t volume;  // bytes per volume = D * slice
+    int tiles_x, tiles_y;
+};
+
+template <class KT, int N>
+__device__ __forceinline__ void d3_sort_task(KT *sm, const D1Task &t) {
+    KT v[N];
+    const KT S = d1_sentinel<KT>();
+#pragma unroll
+    for (int i = 0; i < N; i++) v[i] = i < t.a_len ? sm[t.a_off + i * t.a_stride] : S;
+    SortNet<N>::run(v);
+#pragma unroll
+    for (int i = 0; i < N; i++)
+        if (i < t.a_len) sm[t.out_off + i] = v[i];
+}
+
+template <class KT, int NMAX>
+__device__ __forceinline__ void d3_sort_any(KT *sm, const D1Task &t) {
+    const int n = t.a_len;
+    if (n <= 2) d3_sort_task<KT, 2>(sm, t);
+    else if (n <= 4) d3_sort_task<KT, 4>(sm, t);
+    else if (NMAX <= 8 || n <= 8) d3_sort_task<KT, (NMAX < 8 ? NMAX : 8)>(sm, t);
+    else if (NMAX <= 16 || n <= 16) d3_sort_task<KT, (NMAX < 16 ? NMAX : 16)>(sm, t);
+    else d3_sort_task<KT, (NMAX < 32 ? NMAX : 32)>(sm, t);
+}
+
+// blockIdx.x: root tile (x fastest, then y, then z); blockIdx.y: volume.
+template <class KT, int DT, int NMAX>
+__global__ void __launch_bounds__(1024) d3_kernel(VolArgs a, D3Dev p) {
+    extern __shared__ __align__(16) unsigned char d3_smem[];
+    KT *sm = reinterpret_cast<KT *>(d3_smem);
+    typedef typename Dt<DT>::E E;
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int T = p.T, F = p.F, R = (p.k - 1) / 2;
+    int b = blockIdx.x;
+    const int bx = b % a.tiles_x;
+    b /= a.tiles_x;
+    const int by = b % a.tiles_y, bz = b / a.tiles_y;
+    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    const char *src = a.src + (size_t)blockIdx.y * a.volume;
+
+    // footprint (fx, fy, fz) -> (fy * F + fx) * F + fz; consecutive threads
+    // read consecutive x of one row of the volume
+    const int n = F * F * F;
+    for (int i = tid; i < n; i += NT) {
+        const int fx = i % F, r = i / F;
+        const int fy = r % F, fz = r / F;
+        const int x = clampi(x0 - R + fx, 0, a.W - 1);
+        const int y = clampi(y0 - R + fy, 0, a.H - 1);
+        const int z = clampi(z0 - R + fz, 0, a.D - 1);
+        const E v = __ldg(reinterpret_cast<const E *>(src + (size_t)z * a.slice + (size_t)y * a.pitch) + x);
+        sm[(fy * F + fx) * F + fz] = (KT)Dt<DT>::key(v);
+    }
+    __syncthreads();
+
+    for (int ph = 0; ph < p.nphases; ph++) {
+        const int wb = p.phase_begin[ph], we = p.phase_begin[ph + 1];
+        for (int w = wb + tid; w < we; w += NT) {
+            const uint32_t item = p.work[w];
+            const D1Task t = d1_unpack(p.tasks[item >> 12], F);
+            if (t.type == D1_SORT) d3_sort_any<KT, NMAX>(sm, t);
+            else d1_merge_chunk<KT>(sm, t, (int)(item & 4095u));
+        }
+        __syncthreads();
+    }
+
+    char *dst = a.dst + (size_t)blockIdx.y * a.volume;
+    for (int i = tid; i < T * T * T; i += NT) {
+        const int ox = i % T, r = i / T;
+        const int oy = r % T, oz = r / T;
+        const int x = x0 + ox, y = y0 + oy, z = z0 + oz;
+        if (x >= a.W || y >= a.H || z >= a.D) continue;
+        reinterpret_cast<E *>(dst + (size_t)z * a.slice + (size_t)y * a.pitch)[x] =
+            Dt<DT>::val((uint32_t)sm[p.out_off[i]]);
+    }
+}
+
+// ------------------------------------------------------------ host side
+struct D3Cached {
+    D1Plan plan;
+    D3Dev dev;
+    int nt = 256;
+    void *mem = nullptr;
+};
+
+static std::mutex g_d3_mu;
+// (k, key bytes, device) -> uploaded plan (nullptr: none fits)
+static std::map<std::tuple<int, int, int>, D3Cached *> *g_d3 = new std::map<std::tuple<int, int, int>, D3Cached *>();
+
+static int d3_key_bytes(int dtype) { return dtype == MF_U32 || dtype == MF_F32 ? 4 : 2; }
+
+// Root tile and block size: the largest T (at most 4: the T = 8 trees need
+// more than 200 KB from k = 9 on) whose state fits shared memory; 256
+// threads when the state is small enough for several blocks a SM, else 512
+// when two blocks fit, else 1024.
+static bool d3_choose(int k, int kb, D1Plan *out, int *nt_out) {
+    for (int T = 4; T >= 1; T /= 2) {
+        if (T > k) continue;
+        for (int nt : {256, 512, 1024}) {
+            D1Plan pl;
+            if (!d3_build_plan(k, T, &pl, nt, kb)) break;
+            const size_t bytes = (size_t)pl.smem_elems * kb;
+            const bool fits = nt == 256 ? bytes <= D3_SMEM_SMALL
+                                        : (nt == 512 ? 2 * (bytes + 1024) <= 227 * 1024 : bytes <= D3_SMEM_BUDGET);
+            if (fits) {
+                *out = pl;
+                *nt_out = nt;
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+static D3Cached *d3_get(int k, int dtype, int *err) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        *err = MF_ERR_CUDA;
+        return nullptr;
+    }
+    const int kb = d3_key_bytes(dtype);
+    std::lock_guard<std::mutex> lk(g_d3_mu);
+    const auto key = std::make_tuple(k, kb, dev);
+    auto it = g_d3->find(key);
+    if (it != g_d3->end()) {
+        if (!it->second) *err = MF_ERR_UNSUPPORTED;
+        return it->second;
+    }
+    D3Cached *c = new D3Cached();
+    if (!d3_choose(k, kb, &c->plan, &c->nt)) {
+        delete c;
+        (*g_d3)[key] = nullptr;
+        *err = MF_ERR_UNSUPPORTED;
+        return nullptr;
+    }
+    const D1Plan &pl = c->plan;
+    std::vector<D1Packed> packed;
+    d1_pack_tasks(pl, &packed);
+    const size_t bt = packed.size() * sizeof(D1Packed), bw = pl.work.size() * 4, bp = pl.phase_begin.size() * 4,
+                 bo = pl.out_off.size() * 4;
+    if (dev_alloc(&c->mem, bt + bw + bp + bo + 64) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        *err = MF_ERR_ALLOC;
+        return nullptr;
+    }
+    char *m = (char *)c->mem;
+    if (cudaMemcpy(m, packed.data(), bt, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m + bt, pl.work.data(), bw, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m + bt + bw, pl.phase_begin.data(), bp, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m + bt + bw + bp, pl.out_off.data(), bo, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->mem);
+        delete c;
+        *err = MF_ERR_CUDA;
+        return nullptr;
+    }
+    c->dev.tasks = (const D1Packed *)m;
+    c->dev.work = (const uint32_t *)(m + bt);
+    c->dev.phase_begin = (const int32_t *)(m + bt + bw);
+    c->dev.out_off = (const int32_t *)(m + bt + bw + bp);
+    c->dev.nphases = (int)pl.phase_begin.size() - 1;
+    c->dev.k = k;
+    c->dev.T = pl.T;
+    c->dev.F = pl.FW;
+    (*g_d3)[key] = c;
+    return c;
+}
+
+template <class KT, int DT, int NMAX>
+static int d3_launch_n(const VolArgs &a, int volumes, const D3Cached *c, cudaStream_t s) {
+    auto kern = d3_kernel<KT, DT, NMAX>;
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D3_SMEM_BUDGET) !=
+            cudaSuccess)
+            return MF_ERR_CUDA;
+        configured = true;
+    }
+    const int T = c->plan.T;
+    const long long tiles = (long long)a.tiles_x * a.tiles_y * ((a.D + T - 1) / T);
+    dim3 grid((unsigned)tiles, (unsigned)volumes, 1);
+    kern<<<grid, c->nt, (size_t)c->plan.smem_elems * sizeof(KT), s>>>(a, c->dev);
+    count_launch();
+    return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;
+}
+
+template <class KT, int DT>
+static int d3_launch_t(const VolArgs &a, int volumes, const D3Cached *c, cudaStream_t s) {
+    const int ms = c->plan.max_sort;
+    if (ms <= 8) return d3_launch_n<KT, DT, 8>(a, volumes, c, s);
+    if (ms <= 16) return d3_launch_n<KT, DT, 16>(a, volumes, c, s);
+    return d3_launch_n<KT, DT, 32>(a, volumes, c, s);
+}
+
+void d3_release_all() {
+    std::lock_guard<std::mutex> lk(g_d3_mu);
+    for (auto &kv : *g_d3)
+        if (kv.second) {
+            cudaFree(kv.second->mem);
+            delete kv.second;
+        }
+    g_d3->clear();
+}
+
+static int elem_bytes(int dtype) { return dtype == MF_U8 ? 1 : (dtype == MF_U16 ? 2 : 4); }
+
+static int d3_check(const void *src, const void *dst, int D, int H, int W, size_t pitch, int volumes, int dtype,
+                    int k) {
+    if (dtype < MF_U8 || dtype > MF_F32) {
+        set_error("bad dtype %d", dtype);
+        return MF_ERR_DTYPE;
+    }
+    if (!src || !dst || D < 1 || H < 1 || W < 1 || volumes < 1 || volumes > 65535 || k < 1 || k > D3_MAX_K ||
+        (k & 1) == 0) {
+        set_error("bad volume arguments (D=%d H=%d W=%d volumes=%d k=%d; k odd 1..%d)", D, H, W, volumes, k,
+                  D3_MAX_K);
+        return MF_ERR_ARG;
+    }
+    const int es = elem_bytes(dtype);
+    if (pitch < (size_t)W * es || pitch % es) {
+        set_error("bad pitch %zu for W=%d", pitch, W);
+        return MF_ERR_PITCH;
+    }
+    const size_t bytes = (size_t)volumes * D * H * pitch;
+    const char *s0 = (const char *)src, *d0 = (const char *)dst;
+    if (s0 < d0 + bytes && d0 < s0 + bytes) {
+        set_error("src and dst overlap");
+        return MF_ERR_ALIAS;
+    }
+    return MF_OK;
+}
+
+}  // namespace mf
+
+using namespace mf;
+
+extern "C" int mf_median_filter_3d(const void *src, void *dst, int D, int H, int W, size_t pitch, int volumes,
+                                   mf_dtype dtype, int k, mf_stream_t stream) {
+    int rc = d3_check(src, dst, D, H, W, pitch, volumes, (int)dtype, k);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (k == 1) {
+        if (cudaMemcpy2DAsync(dst, pitch, src, pitch, (size_t)W * elem_bytes(dtype), (size_t)volumes * D * H,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            set_error("copy: %s", cudaGetErrorString(cudaGetLastError()));
+            return MF_ERR_CUDA;
+        }
+        return MF_OK;
+    }
+    int err = MF_OK;
+    const D3Cached *c = d3_get(k, (int)dtype, &err);
+    if (!c) {
+        if (err == MF_ERR_UNSUPPORTED) set_error("no volumetric plan fits shared memory for k=%d", k);
+        else set_error("cannot allocate or upload the volumetric plan for k=%d", k);
+        return err;
+    }
+    const int T = c->plan.T;
+    VolArgs a;
+    a.src = (const char *)src;
+    a.dst = (char *)dst;
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.pitch = pitch;
+    a.slice = (size_t)H * pitch;
+    a.volume = (size_t)D * a.slice;
+    a.tiles_x = (W + T - 1) / T;
+    a.tiles_y = (H + T - 1) / T;
+    if ((long long)a.tiles_x * a.tiles_y * ((D + T - 1) / T) > 2147483647ll) {
+        set_error("volume too large for one launch");
+        return MF_ERR_ARG;
+    }
+    switch (dtype) {
+        case MF_U8: rc = d3_launch_t<uint16_t, MF_U8>(a, volumes, c, s); break;
+        case MF_U16: rc = d3_launch_t<uint16_t, MF_U16>(a, volumes, c, s); break;
+        case MF_U32: rc = d3_launch_t<uint32_t, MF_U32>(a, volumes, c, s); break;
+        default: rc = d3_launch_t<uint32_t, MF_F32>(a, volumes, c, s); break;
+    }
+    if (rc == MF_ERR_CUDA) set_error("volumetric kernel: %s", cudaGetErrorString(cudaGetLastError()));
+    return rc;
+}
+
+extern "C" int mf_median_filter_3d_describe(int k, mf_dtype dtype, char *buf, size_t n) {
+    if (!buf || n == 0) return MF_ERR_ARG;
+    if ((int)dtype < MF_U8 || (int)dtype > MF_F32) return MF_ERR_DTYPE;
+    if (k < 3 || k > D3_MAX_K || (k & 1) == 0) {
+        snprintf(buf, n, "volumetric k=%d (no plan)", k);
+        return MF_OK;
+    }
+    D1Plan pl;
+    int nt = 0;
+    const int kb = d3_key_bytes((int)dtype);
+    if (!d3_choose(k, kb, &pl, &nt)) {
+        snprintf(buf, n, "volumetric k=%d (no plan fits)", k);
+        return MF_OK;
+    }
+    const double vox = (double)pl.T * pl.T * pl.T;
+    snprintf(buf, n, "volumetric data-aware k=%d tile=%dx%dx%d block=%d smem=%zuB phases=%d tasks=%zu merged/vox=%.1f sorted/vox=%.1f",
+             k, pl.T, pl.T, pl.T, nt, (size_t)pl.smem_elems * kb, (int)pl.phase_begin.size() - 1, pl.tasks.size(),
+             pl.merge_outputs / vox, pl.sort_elems / vox);
+    return MF_OK;
+}

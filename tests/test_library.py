@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI (no GPU): the library builds, loads and
-exports every function include/medianfilter.h declares, and argument errors
+exports every function include/*.h declares, and argument errors
 come back as status codes before anything touches a device."""
 import ctypes
 import os
@@ -20,7 +20,8 @@ def lib():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "medianfilter.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, n)).read() for n in sorted(os.listdir(inc)) if n.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(mf_[a-z0-9_]+)\s*\(", src)))
 
@@ -83,3 +84,18 @@ def test_batch_rejects_bad_descriptors(lib):
     d = mf.ImageDesc(0x1000, 0x900000, 8, 8, 4, 1, mf.MF_U8, 3)  # pitch < W
     with pytest.raises(mf.MedianFilterError):
         mf.mf_batch_plan_create([d])
+
+
+def test_volume_rejects_bad_arguments(lib):
+    a, b = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x900000)
+    f = lib.mf_median_filter_3d
+    assert f(a, b, 4, 8, 8, 8, 1, 0, 4, None) == -1      # even k
+    assert f(a, b, 4, 8, 8, 8, 1, 0, 21, None) == -1     # k beyond 19
+    assert f(a, b, 0, 8, 8, 8, 1, 0, 3, None) == -1      # D
+    assert f(a, b, 4, 8, 8, 8, 0, 0, 3, None) == -1      # volumes
+    assert f(a, b, 4, 8, 8, 7, 1, 0, 3, None) == -3      # pitch < W
+    assert f(a, b, 4, 8, 8, 18, 1, 2, 3, None) == -3     # u32 pitch not a multiple of 4
+    assert f(a, a, 4, 8, 8, 8, 1, 0, 3, None) == -4      # alias
+    assert f(a, b, 4, 8, 8, 8, 1, 9, 3, None) == -2      # dtype
+    assert f(None, b, 4, 8, 8, 8, 1, 0, 3, None) == -1   # null
+    assert "volumetric" in mf.mf_median_filter_3d_describe(5, mf.MF_U8)
