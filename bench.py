@@ -432,9 +432,12 @@ def bench_volume(dev, stream, flush, reps=3, cases=(("u8", 3), ("u8", 5), ("u8",
     import paper_2507_19926_gb300 as mf
     from paper_2507_19926_gb300 import synth
     codes = {"u8": mf.MF_U8, "u16": mf.MF_U16, "u32": mf.MF_U32, "f32": mf.MF_F32}
+    import re
     res = []
     sptr = stream.cuda_stream
     n = 256
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    smem_peak = sms * 128 * read_peaks().get("sm_max_mhz", 2070.0) * 1e6 / 1e9  # GB/s
     for dt, k in cases:
         x = to_device(synth.uniform((n, n, n), dt, synth.SEED_BASE + 5), dev)
         y = torch.empty_like(x)
@@ -442,8 +445,16 @@ def bench_volume(dev, stream, flush, reps=3, cases=(("u8", 3), ("u8", 5), ("u8",
         f = lambda: mf.mf_median_filter_3d(x.data_ptr(), y.data_ptr(), n, n, n, pitch, 1, codes[dt], k, sptr)
         f()
         ms = _time_ms(f, stream, reps, flush)
-        res.append({"dtype": dt, "k": k, "ms": round(ms, 4), "mvox_s": round(n ** 3 / ms / 1e3, 1),
-                    "plan": mf.mf_median_filter_3d_describe(k, codes[dt])})
+        plan = mf.mf_median_filter_3d_describe(k, codes[dt])
+        r = {"dtype": dt, "k": k, "ms": round(ms, 4), "mvox_s": round(n ** 3 / ms / 1e3, 1), "plan": plan}
+        # shared-memory roofline, as for the 2D data-aware kernel: every
+        # merged or sorted element read once and written once at the least
+        m = re.search(r"merged/vox=([\d.]+) sorted/vox=([\d.]+)", plan)
+        if m:
+            kb = 2 if dt in ("u8", "u16") else 4
+            gbs = (float(m.group(1)) + float(m.group(2))) * 2 * kb * n ** 3 / (ms * 1e-3) / 1e9
+            r["smem_roofline_frac"] = round(gbs / smem_peak, 4)
+        res.append(r)
     return res
 
 

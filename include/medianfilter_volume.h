@@ -45,13 +45,15 @@ int mf_median_filter_3d(const void *src, void *dst, int D, int H, int W, size_t 
 int mf_median_filter_3d_describe(int k, mf_dtype dtype, char *buf, size_t n);
 
 /* Host-side check of the volumetric schedule: builds the plan for a
- * k x k x k window and a tile^3 root tile and, if footprint and medians are
- * non-NULL, runs it on the CPU for one footprint of F = tile + k - 1 voxels
- * a side (64-bit order keys, element (fx, fy, fz) at (fy*F + fx)*F + fz,
- * clamped by the caller), writing the tile^3 medians in (z, y, x) order.
- * stats: NULL or 7 ints as for mf_d1_plan_check.  No GPU is used.
- * MF_ERR_UNSUPPORTED when no plan exists. */
-int mf_d3_plan_check(int k, int tile, const uint64_t *footprint, uint64_t *medians, int *stats);
+ * k x k x k window and a strip of `strip` root tiles of tile^3 voxels side
+ * by side along x and, if footprint and medians are non-NULL, runs it on
+ * the CPU for one footprint of F = tile + k - 1 voxels in y and z and
+ * FX = strip*tile + k - 1 in x (64-bit order keys, element (fx, fy, fz) at
+ * (fy*FX + fx)*F + fz, clamped by the caller), writing the strip's
+ * strip*tile x tile x tile medians in (z, y, x) order.  stats: NULL or 7
+ * ints as for mf_d1_plan_check.  No GPU is used.  MF_ERR_UNSUPPORTED when
+ * no plan exists. */
+int mf_d3_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians, int *stats);
 
 #ifdef __cplusplus
 }

@@ -85,7 +85,7 @@ def load_library(path=LIB_PATH):
         lib.mf_d1_plan_check.argtypes = [i, i, i, vp, vp, vp]
         lib.mf_median_filter_3d.argtypes = [vp, vp, i, i, i, sz, i, i, i, vp]
         lib.mf_median_filter_3d_describe.argtypes = [i, i, ctypes.c_char_p, sz]
-        lib.mf_d3_plan_check.argtypes = [i, i, vp, vp, vp]
+        lib.mf_d3_plan_check.argtypes = [i, i, i, vp, vp, vp]
         lib.mf_status_string.argtypes = [i]
         lib.mf_status_string.restype = ctypes.c_char_p
         lib.mf_last_error.restype = ctypes.c_char_p
@@ -228,18 +228,19 @@ def mf_median_filter_3d_describe(k, dtype):
     return buf.value.decode()
 
 
-def mf_d3_plan_check(k, tile, footprint=None):
-    """Builds the volumetric schedule for (k, tile); with a uint64 footprint
-    of keys (F = tile + k - 1 a side, element (fx, fy, fz) at
-    (fy*F + fx)*F + fz) also runs it on the CPU.  Returns (stats dict,
-    tile^3 medians in (z, y, x) order or None)."""
+def mf_d3_plan_check(k, tile, footprint=None, strip=1):
+    """Builds the volumetric schedule for (k, tile, strip); with a uint64
+    footprint of keys (F = tile + k - 1 in y and z, FX = strip*tile + k - 1
+    in x, element (fx, fy, fz) at (fy*FX + fx)*F + fz) also runs it on the
+    CPU.  Returns (stats dict, strip*tile^3 medians in (z, y, x) order or
+    None)."""
     import numpy as np
     st = np.zeros(7, np.int32)
     med = fp = None
     if footprint is not None:
         fp = np.ascontiguousarray(footprint, dtype=np.uint64)
-        med = np.zeros(tile ** 3, np.uint64)
-    _check(load_library().mf_d3_plan_check(k, tile, fp.ctypes.data if fp is not None else None,
+        med = np.zeros(strip * tile ** 3, np.uint64)
+    _check(load_library().mf_d3_plan_check(k, tile, strip, fp.ctypes.data if fp is not None else None,
                                            med.ctypes.data if med is not None else None, st.ctypes.data))
     names = ["smem_elems", "phases", "tasks", "work_items", "merged", "sorted", "max_sort"]
     return dict(zip(names, [int(v) for v in st])), med

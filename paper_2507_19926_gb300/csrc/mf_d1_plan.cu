@@ -486,10 +486,13 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
 // an earlier level sorted, the way sorted extra rows and columns are
 // extended by their corners in 2D.
 //
-// Footprint layout: F = T + k - 1 per side, element (fx, fy, fz) at
-// (fy * F + fx) * F + fz (z innermost), so z pillars are contiguous and x
-// lines have stride F (the plan's FW).  Output (ox, oy, oz) of the root
-// tile is entry (oz * T + oy) * T + ox of out_off.
+// A block may own a strip of NB root tiles side by side along x, which
+// share the memoised lines and planes of their overlapping footprints
+// (Sec. 3.3: adjacent tiles share their column sorts).  Footprint layout:
+// F = T + k - 1 in y and z, FX = NB * T + k - 1 in x, element (fx, fy, fz)
+// at (fy * FX + fx) * F + fz (z innermost), so z pillars are contiguous and
+// x lines have stride F (the plan's FW).  Output (ox, oy, oz) of the strip
+// is entry (oz * T + oy) * NB * T + ox of out_off.
 namespace {
 struct Box {
     int x0, x1, y0, y1, z0, z1;  // inclusive ranges in footprint coordinates
@@ -501,15 +504,16 @@ struct Box {
 };
 }  // namespace
 
-bool d3_build_plan(int k, int T, D1Plan *plan, int nt, int key_bytes) {
-    if (k < 3 || k > D3_MAX_K || (k & 1) == 0 || T < 1 || (T & (T - 1)) || T > k || T > 16) return false;
-    const int F = T + k - 1;
+bool d3_build_plan(int k, int T, D1Plan *plan, int nt, int key_bytes, int NB) {
+    if (k < 3 || k > D3_MAX_K || (k & 1) == 0 || T < 1 || (T & (T - 1)) || T > k || T > 16 || NB < 1 || NB > 16)
+        return false;
+    const int F = T + k - 1, FX = NB * T + k - 1;
     const long long n_win = (long long)k * k * k;
     Builder B;
     B.k = k;
     B.T = T;
     B.FW = F;
-    auto off = [&](int fx, int fy, int fz) { return (fy * F + fx) * F + fz; };
+    auto off = [&](int fx, int fy, int fz) { return (fy * FX + fx) * F + fz; };
     std::map<std::tuple<int, int, int, int, int, int>, std::pair<Box, Ref>> memo;
 
     // sorted list of every window position in box b (full, never pruned)
@@ -561,74 +565,75 @@ bool d3_build_plan(int k, int T, D1Plan *plan, int nt, int key_bytes) {
         return r;
     };
 
-    // ---------------------------------------------------------- initialisation
     struct Node {
-        int o[3];  // output origin (x, y, z) in the root tile
+        int o[3];  // output origin (x, y, z): x in the strip, y and z in the root tile
         Ref core;
     };
-    int t[3] = {T, T, T};
-    const Box root_core{T - 1, k - 1, T - 1, k - 1, T - 1, k - 1};
-    long long c = root_core.vol();
-    int lo, hi;
-    keep_range((int)n_win, (int)c, 0, (int)c, &lo, &hi);
-    int d = lo;
-    std::vector<Node> nodes;
-    {
-        std::vector<Ref> pillars;
-        for (int y = T - 1; y <= k - 1; y++)
-            for (int x = T - 1; x <= k - 1; x++) pillars.push_back(get(Box{x, x, y, y, T - 1, k - 1}));
-        nodes.push_back(Node{{0, 0, 0}, B.multiway(pillars, lo, hi)});
-    }
-
-    // ---------------------------------------------------------- recursion
-    while (t[0] * t[1] * t[2] > 1) {
-        const int ax = (t[0] >= t[1] && t[0] >= t[2]) ? 0 : (t[1] >= t[2] ? 1 : 2);
-        const int h = t[ax] / 2;
-        long long other = 1;
-        for (int a = 0; a < 3; a++)
-            if (a != ax) other *= k - t[a] + 1;
-        const int held = nodes[0].core.len;
-        c += (long long)h * other;
-        keep_range((int)n_win, (int)c, d, held + (int)(h * other), &lo, &hi);
-        std::vector<Node> next;
-        for (const Node &nd : nodes) {
-            int cr[3][2];  // the parent core's ranges
-            for (int a = 0; a < 3; a++) {
-                cr[a][0] = nd.o[a] + t[a] - 1;
-                cr[a][1] = nd.o[a] + k - 1;
-            }
-            for (int s = 0; s < 2; s++) {
-                const int u0 = s == 0 ? nd.o[ax] + h - 1 : nd.o[ax] + k;  // first new plane
-                std::vector<Ref> planes;
-                for (int u = u0; u < u0 + h; u++) {
-                    int rg[3][2] = {{cr[0][0], cr[0][1]}, {cr[1][0], cr[1][1]}, {cr[2][0], cr[2][1]}};
-                    rg[ax][0] = rg[ax][1] = u;
-                    planes.push_back(get(Box{rg[0][0], rg[0][1], rg[1][0], rg[1][1], rg[2][0], rg[2][1]}));
-                }
-                const Ref slab = B.multiway(planes, 0, 1 << 30);
-                Node ch = nd;
-                ch.o[ax] = nd.o[ax] + s * h;
-                ch.core = B.merge_range(nd.core, slab, lo, hi);
-                next.push_back(ch);
-            }
+    const int SW = NB * T;
+    std::vector<Ref> outs(SW * T * T);
+    for (int tb = 0; tb < NB; tb++) {  // root tiles of the strip share the memoised lines and planes
+        const int bx = tb * T;
+        // ------------------------------------------------------ initialisation
+        int t[3] = {T, T, T};
+        long long c = (long long)(k - T + 1) * (k - T + 1) * (k - T + 1);
+        int lo, hi;
+        keep_range((int)n_win, (int)c, 0, (int)c, &lo, &hi);
+        int d = lo;
+        std::vector<Node> nodes;
+        {
+            std::vector<Ref> pillars;
+            for (int y = T - 1; y <= k - 1; y++)
+                for (int x = bx + T - 1; x <= bx + k - 1; x++) pillars.push_back(get(Box{x, x, y, y, T - 1, k - 1}));
+            nodes.push_back(Node{{bx, 0, 0}, B.multiway(pillars, lo, hi)});
         }
-        nodes.swap(next);
-        t[ax] = h;
-        d += lo;
+        // ------------------------------------------------------ recursion
+        while (t[0] * t[1] * t[2] > 1) {
+            const int ax = (t[0] >= t[1] && t[0] >= t[2]) ? 0 : (t[1] >= t[2] ? 1 : 2);
+            const int h = t[ax] / 2;
+            long long other = 1;
+            for (int a = 0; a < 3; a++)
+                if (a != ax) other *= k - t[a] + 1;
+            const int held = nodes[0].core.len;
+            c += (long long)h * other;
+            keep_range((int)n_win, (int)c, d, held + (int)(h * other), &lo, &hi);
+            std::vector<Node> next;
+            for (const Node &nd : nodes) {
+                int cr[3][2];  // the parent core's ranges
+                for (int a = 0; a < 3; a++) {
+                    cr[a][0] = nd.o[a] + t[a] - 1;
+                    cr[a][1] = nd.o[a] + k - 1;
+                }
+                for (int s = 0; s < 2; s++) {
+                    const int u0 = s == 0 ? nd.o[ax] + h - 1 : nd.o[ax] + k;  // first new plane
+                    std::vector<Ref> planes;
+                    for (int u = u0; u < u0 + h; u++) {
+                        int rg[3][2] = {{cr[0][0], cr[0][1]}, {cr[1][0], cr[1][1]}, {cr[2][0], cr[2][1]}};
+                        rg[ax][0] = rg[ax][1] = u;
+                        planes.push_back(get(Box{rg[0][0], rg[0][1], rg[1][0], rg[1][1], rg[2][0], rg[2][1]}));
+                    }
+                    const Ref slab = B.multiway(planes, 0, 1 << 30);
+                    Node ch = nd;
+                    ch.o[ax] = nd.o[ax] + s * h;
+                    ch.core = B.merge_range(nd.core, slab, lo, hi);
+                    next.push_back(ch);
+                }
+            }
+            nodes.swap(next);
+            t[ax] = h;
+            d += lo;
+        }
+        for (const Node &nd : nodes) outs[(nd.o[2] * T + nd.o[1]) * SW + nd.o[0]] = nd.core;
     }
-
-    std::vector<Ref> outs(T * T * T);
-    for (const Node &nd : nodes) outs[(nd.o[2] * T + nd.o[1]) * T + nd.o[0]] = nd.core;
     plan->k = k;
     plan->kh = k;
     plan->T = T;
     plan->TH = T;
     plan->TD = T;
-    plan->B = 1;
-    plan->FW = F;
+    plan->B = NB;
+    plan->FW = F;   // x lines are F elements apart
     plan->FH = F;
-    plan->FD = F;
-    return finish_plan(B, outs, F * F * F, nt, key_bytes, plan);
+    plan->FD = FX;  // FW * FH * FD: the footprint's element count
+    return finish_plan(B, outs, F * F * FX, nt, key_bytes, plan);
 }
 
 void d1_pack_tasks(const D1Plan &plan, std::vector<D1Packed> *out) {
@@ -693,9 +698,10 @@ extern "C" int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *foot
 }
 
 // Host check of the volumetric schedule (declared in medianfilter.h).
-extern "C" int mf_d3_plan_check(int k, int tile, const uint64_t *footprint, uint64_t *medians, int *stats) {
+extern "C" int mf_d3_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,
+                                int *stats) {
     mf::D1Plan plan;
-    if (!mf::d3_build_plan(k, tile, &plan, 256, 4)) return MF_ERR_UNSUPPORTED;
+    if (!mf::d3_build_plan(k, tile, &plan, 256, 4, strip)) return MF_ERR_UNSUPPORTED;
     if (stats) {
         stats[0] = plan.smem_elems;
         stats[1] = (int)plan.phase_begin.size() - 1;

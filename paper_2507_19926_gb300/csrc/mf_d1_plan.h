@@ -64,13 +64,15 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int B = 1, int nt = 256, int key_
 // the packed task form stay below 2^13 (k^3 = 6859 at k = 19).
 constexpr int D3_MAX_K = 19;
 
-// Builds the plan of a k x k x k window over a T x T x T root tile of a
-// volume (paper Sec. 7.2: hierarchical tiling extended to 3D; T a power of
-// two, 1 <= T <= min(k, 16)).  Footprint F = T + k - 1 per side at offset 0,
-// element (fx, fy, fz) at (fy * F + fx) * F + fz; medians in (z, y, x) order
-// of the root tile.  Returns false outside that range or beyond the packed
+// Builds the plan of a k x k x k window over a strip of NB root tiles of
+// T x T x T voxels side by side along x (paper Sec. 7.2: hierarchical tiling
+// extended to 3D; T a power of two, 1 <= T <= min(k, 16); 1 <= NB <= 16).
+// Footprint at offset 0: F = T + k - 1 in y and z, FX = NB*T + k - 1 in x,
+// element (fx, fy, fz) at (fy * FX + fx) * F + fz; the plan records FW = F
+// (the x-line stride), FH = F, FD = FX.  Medians in (z, y, x) order of the
+// strip (NB*T wide).  Returns false outside that range or beyond the packed
 // form's limits.
-bool d3_build_plan(int k, int T, D1Plan *plan, int nt = 256, int key_bytes = 4);
+bool d3_build_plan(int k, int T, D1Plan *plan, int nt = 256, int key_bytes = 4, int NB = 1);
 
 struct D1Packed;
 // The 16-byte device form of every task (layout in mf_d1_ops.cuh).

@@ -33,7 +33,8 @@ struct D3Dev {
     const int32_t *phase_begin;
     const int32_t *out_off;
     int nphases;
-    int k, T, F;
+    int k, T, F;  // window, root tile side, footprint side in y and z
+    int B, FX;    // root tiles per strip (along x), footprint width B*T + k - 1
 };
 
 struct VolArgs {
@@ -43,7 +44,7 @@ struct VolArgs {
     size_t pitch;   // bytes per row
     size_t slice;   // bytes per slice = H * pitch
     size_t volume;  // bytes per volume = D * slice
-    int tiles_x, tiles_y;
+    int tiles_x, tiles_y;  // strips along x, root tiles along y
 };
 
 template <class KT, int N>
@@ -68,32 +69,33 @@ __device__ __forceinline__ void d3_sort_any(KT *sm, const D1Task &t) {
     else d3_sort_task<KT, (NMAX < 32 ? NMAX : 32)>(sm, t);
 }
 
-// blockIdx.x: root tile (x fastest, then y, then z); blockIdx.y: volume.
+// blockIdx.x: strip of B root tiles (x fastest, then y, then z);
+// blockIdx.y: volume.
 template <class KT, int DT, int NMAX>
 __global__ void __launch_bounds__(1024) d3_kernel(VolArgs a, D3Dev p) {
     extern __shared__ __align__(16) unsigned char d3_smem[];
     KT *sm = reinterpret_cast<KT *>(d3_smem);
     typedef typename Dt<DT>::E E;
     const int tid = threadIdx.x, NT = blockDim.x;
-    const int T = p.T, F = p.F, R = (p.k - 1) / 2;
+    const int T = p.T, F = p.F, FX = p.FX, SW = p.B * p.T, R = (p.k - 1) / 2;
     int b = blockIdx.x;
     const int bx = b % a.tiles_x;
     b /= a.tiles_x;
     const int by = b % a.tiles_y, bz = b / a.tiles_y;
-    const int x0 = bx * T, y0 = by * T, z0 = bz * T;
+    const int x0 = bx * SW, y0 = by * T, z0 = bz * T;
     const char *src = a.src + (size_t)blockIdx.y * a.volume;
 
-    // footprint (fx, fy, fz) -> (fy * F + fx) * F + fz; consecutive threads
+    // footprint (fx, fy, fz) -> (fy * FX + fx) * F + fz; consecutive threads
     // read consecutive x of one row of the volume
-    const int n = F * F * F;
+    const int n = FX * F * F;
     for (int i = tid; i < n; i += NT) {
-        const int fx = i % F, r = i / F;
+        const int fx = i % FX, r = i / FX;
         const int fy = r % F, fz = r / F;
         const int x = clampi(x0 - R + fx, 0, a.W - 1);
         const int y = clampi(y0 - R + fy, 0, a.H - 1);
         const int z = clampi(z0 - R + fz, 0, a.D - 1);
         const E v = __ldg(reinterpret_cast<const E *>(src + (size_t)z * a.slice + (size_t)y * a.pitch) + x);
-        sm[(fy * F + fx) * F + fz] = (KT)Dt<DT>::key(v);
+        sm[(fy * FX + fx) * F + fz] = (KT)Dt<DT>::key(v);
     }
     __syncthreads();
 
@@ -109,8 +111,8 @@ __global__ void __launch_bounds__(1024) d3_kernel(VolArgs a, D3Dev p) {
     }
 
     char *dst = a.dst + (size_t)blockIdx.y * a.volume;
-    for (int i = tid; i < T * T * T; i += NT) {
-        const int ox = i % T, r = i / T;
+    for (int i = tid; i < SW * T * T; i += NT) {
+        const int ox = i % SW, r = i / SW;
         const int oy = r % T, oz = r / T;
         const int x = x0 + ox, y = y0 + oy, z = z0 + oz;
         if (x >= a.W || y >= a.H || z >= a.D) continue;
@@ -133,20 +135,28 @@ static std::map<std::tuple<int, int, int>, D3Cached *> *g_d3 = new std::map<std:
 
 static int d3_key_bytes(int dtype) { return dtype == MF_U32 || dtype == MF_F32 ? 4 : 2; }
 
-// Root tile and block size: the largest T (at most 4: the T = 8 trees need
-// more than 200 KB from k = 9 on) whose state fits shared memory; 256
-// threads when the state is small enough for several blocks a SM, else 512
-// when two blocks fit, else 1024.
+// Root tile, strip and block size: the largest T (at most 4: the T = 8 trees
+// need more than 200 KB from k = 9 on) whose state fits shared memory; with
+// 256 threads the widest strip of 8, 4, 2 or 1 tiles whose state is small
+// enough for several blocks a SM (the tiles share lines and planes, and the
+// block has enough merges to spread over its threads), else one tile with
+// 512 threads when two blocks fit, else 1024.
 static bool d3_choose(int k, int kb, D1Plan *out, int *nt_out) {
     for (int T = 4; T >= 1; T /= 2) {
         if (T > k) continue;
-        for (int nt : {256, 512, 1024}) {
+        for (int nb = 8; nb >= 1; nb /= 2) {
             D1Plan pl;
-            if (!d3_build_plan(k, T, &pl, nt, kb)) break;
+            if (d3_build_plan(k, T, &pl, 256, kb, nb) && (size_t)pl.smem_elems * kb <= D3_SMEM_SMALL) {
+                *out = pl;
+                *nt_out = 256;
+                return true;
+            }
+        }
+        for (int nt : {512, 1024}) {
+            D1Plan pl;
+            if (!d3_build_plan(k, T, &pl, nt, kb, 1)) break;
             const size_t bytes = (size_t)pl.smem_elems * kb;
-            const bool fits = nt == 256 ? bytes <= D3_SMEM_SMALL
-                                        : (nt == 512 ? 2 * (bytes + 1024) <= 227 * 1024 : bytes <= D3_SMEM_BUDGET);
-            if (fits) {
+            if (nt == 512 ? 2 * (bytes + 1024) <= 227 * 1024 : bytes <= D3_SMEM_BUDGET) {
                 *out = pl;
                 *nt_out = nt;
                 return true;
@@ -208,6 +218,8 @@ static D3Cached *d3_get(int k, int dtype, int *err) {
     c->dev.k = k;
     c->dev.T = pl.T;
     c->dev.F = pl.FW;
+    c->dev.B = pl.B;
+    c->dev.FX = pl.FD;
     (*g_d3)[key] = c;
     return c;
 }
@@ -310,7 +322,7 @@ extern "C" int mf_median_filter_3d(const void *src, void *dst, int D, int H, int
     a.pitch = pitch;
     a.slice = (size_t)H * pitch;
     a.volume = (size_t)D * a.slice;
-    a.tiles_x = (W + T - 1) / T;
+    a.tiles_x = (W + c->plan.B * T - 1) / (c->plan.B * T);
     a.tiles_y = (H + T - 1) / T;
     if ((long long)a.tiles_x * a.tiles_y * ((D + T - 1) / T) > 2147483647ll) {
         set_error("volume too large for one launch");
@@ -340,9 +352,9 @@ extern "C" int mf_median_filter_3d_describe(int k, mf_dtype dtype, char *buf, si
         snprintf(buf, n, "volumetric k=%d (no plan fits)", k);
         return MF_OK;
     }
-    const double vox = (double)pl.T * pl.T * pl.T;
-    snprintf(buf, n, "volumetric data-aware k=%d tile=%dx%dx%d block=%d smem=%zuB phases=%d tasks=%zu merged/vox=%.1f sorted/vox=%.1f",
-             k, pl.T, pl.T, pl.T, nt, (size_t)pl.smem_elems * kb, (int)pl.phase_begin.size() - 1, pl.tasks.size(),
-             pl.merge_outputs / vox, pl.sort_elems / vox);
+    const double vox = (double)pl.B * pl.T * pl.T * pl.T;
+    snprintf(buf, n, "volumetric data-aware k=%d tile=%dx%dx%d strip=%d block=%d smem=%zuB phases=%d tasks=%zu merged/vox=%.1f sorted/vox=%.1f",
+             k, pl.T, pl.T, pl.T, pl.B, nt, (size_t)pl.smem_elems * kb, (int)pl.phase_begin.size() - 1,
+             pl.tasks.size(), pl.merge_outputs / vox, pl.sort_elems / vox);
     return MF_OK;
 }

@@ -34,6 +34,19 @@ def test_plan_matches_oracle(k, T):
     assert st["max_sort"] <= 32 and st["phases"] >= 3
 
 
+@pytest.mark.parametrize("k,T,B", [(3, 2, 8), (5, 4, 2), (7, 2, 4), (9, 4, 2)])
+def test_strip_plan_matches_oracle(k, T, B):
+    """A strip of B root tiles along x sharing their lines and planes."""
+    F, FX = T + k - 1, B * T + k - 1
+    r = k // 2
+    vol = synth.levels16((F, F, FX), "u16", 41 * k + B)
+    st, med = mf.mf_d3_plan_check(k, T, _footprint(vol), strip=B)
+    want = oracle.median_filter_3d(vol, k)[r:r + T, r:r + T, r:r + B * T].ravel()
+    assert np.array_equal(med.astype(np.uint16), want), (k, T, B)
+    one, _ = mf.mf_d3_plan_check(k, T)
+    assert st["sorted"] < B * one["sorted"]  # shared line sorts
+
+
 def test_plan_work_grows_slower_than_the_window():
     """Sharing the sorted core among the T^3 voxels of a root tile: merged
     elements per voxel stay below the k^3 elements of one window, and their
