@@ -428,8 +428,10 @@ def bench_sweep(dev, stream, flush, reps=3, ks=(3, 5, 9, 15, 21, 31, 45, 75), dt
     return res
 
 
-def bench_volume(dev, stream, flush, reps=3, cases=(("u8", 3), ("u8", 5), ("u8", 7), ("u8", 9), ("u8", 15),
-                                                      ("u8", 19), ("u16", 7), ("f32", 3), ("f32", 7), ("f32", 19))):
+def bench_volume(dev, stream, flush, reps=3, cases=(("u8", 3, "auto"), ("u8", 3, "data_aware"), ("u8", 5, "auto"),
+                                                      ("u8", 7, "auto"), ("u8", 9, "auto"), ("u8", 15, "auto"),
+                                                      ("u8", 19, "auto"), ("u16", 7, "auto"), ("f32", 3, "auto"),
+                                                      ("f32", 7, "auto"), ("f32", 19, "auto"))):
     """256^3 single volumes, uniform values: the k x k x k median by
     hierarchical tiling in 3D (mf_median_filter_3d)."""
     import torch
@@ -442,15 +444,21 @@ def bench_volume(dev, stream, flush, reps=3, cases=(("u8", 3), ("u8", 5), ("u8",
     n = 256
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     smem_peak = sms * 128 * read_peaks().get("sm_max_mhz", 2070.0) * 1e6 / 1e9  # GB/s
-    for dt, k in cases:
+    for dt, k, variant in cases:
         x = to_device(synth.uniform((n, n, n), dt, synth.SEED_BASE + 5), dev)
         y = torch.empty_like(x)
         pitch = n * x.element_size()
-        f = lambda: mf.mf_median_filter_3d(x.data_ptr(), y.data_ptr(), n, n, n, pitch, 1, codes[dt], k, sptr)
+        f = lambda: mf.mf_median_filter_3d_ex(x.data_ptr(), y.data_ptr(), n, n, n, pitch, 1, codes[dt], k,
+                                              mf.VARIANTS[variant], sptr)
         f()
         ms = _time_ms(f, stream, reps, flush)
-        plan = mf.mf_median_filter_3d_describe(k, codes[dt])
-        r = {"dtype": dt, "k": k, "ms": round(ms, 4), "mvox_s": round(n ** 3 / ms / 1e3, 1), "plan": plan}
+        plan = mf.mf_median_filter_3d_describe(k, codes[dt]) if variant == "auto" else variant
+        r = {"dtype": dt, "k": k, "variant": variant, "ms": round(ms, 4), "mvox_s": round(n ** 3 / ms / 1e3, 1),
+             "plan": plan}
+        m = re.search(r"min/max per voxel=([\d.]+)", plan)
+        if m:  # ALU roofline: 32-bit min/max at 64 per clock per SM
+            peak = sms * 64 * read_peaks().get("sm_max_mhz", 2070.0) * 1e6
+            r["alu_roofline_frac"] = round(float(m.group(1)) * n ** 3 / (ms * 1e-3) / peak, 4)
         # shared-memory roofline, as for the 2D data-aware kernel: every
         # merged or sorted element read once and written once at the least
         m = re.search(r"merged/vox=([\d.]+) sorted/vox=([\d.]+)", plan)

@@ -24,9 +24,10 @@ extern "C" {
  * src(clamp(z+dz), clamp(y+dy), clamp(x+dx)), dz, dy, dx in [-(k-1)/2,
  * (k-1)/2], clamped to the edge on every axis, ordered as in
  * mf_median_filter (f32 by the sign-flip key); the winner is copied bit for
- * bit.  Data-aware variant (Sec. 5) on T x T x T root tiles of voxels: one
- * thread block keeps a tile's footprint and its whole tree of sorted lists
- * in shared memory.
+ * bit.  MF_AUTO of mf_median_filter_3d_ex: the data-oblivious network
+ * where one is built (k = 3), else the data-aware variant (Sec. 5) on
+ * T x T x T root tiles of voxels: one thread block keeps a strip of tiles'
+ * footprint and its whole tree of sorted lists in shared memory.
  *   src, dst: device, caller-owned, not aliasing; `volumes` volumes of D
  *             slices of H rows of W elements; row r of slice z of volume v
  *             at base + ((v*D + z)*H + r)*pitch.
@@ -38,6 +39,15 @@ extern "C" {
  * an error. */
 int mf_median_filter_3d(const void *src, void *dst, int D, int H, int W, size_t pitch, int volumes,
                         mf_dtype dtype, int k, mf_stream_t stream);
+
+/* As mf_median_filter_3d with a choice of variant: MF_DATA_AWARE runs the
+ * data-aware plan above (every k); MF_OBLIVIOUS a generated min/max network
+ * of the same tree held in registers, one thread per 2 x 2 x 2 tile (the
+ * data-oblivious variant of Sec. 4 in 3D; built for k = 3, else
+ * MF_ERR_UNSUPPORTED); MF_AUTO the network where one is built and the grid
+ * fits, else the data-aware plan.  Bad variant: MF_ERR_ARG. */
+int mf_median_filter_3d_ex(const void *src, void *dst, int D, int H, int W, size_t pitch, int volumes,
+                           mf_dtype dtype, int k, mf_variant variant, mf_stream_t stream);
 
 /* One line describing the plan mf_median_filter_3d runs for (k, dtype):
  * root tile, threads per block, shared memory, phases, tasks, merged and

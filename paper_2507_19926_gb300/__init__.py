@@ -35,7 +35,7 @@ EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_tile", "
            "mf_status_string", "mf_last_error", "mf_version", "mf_shutdown", "mf_probe_minmax",
            "mf_d1_plan_check",
            # include/medianfilter_volume.h
-           "mf_median_filter_3d", "mf_median_filter_3d_describe", "mf_d3_plan_check"]
+           "mf_median_filter_3d", "mf_median_filter_3d_ex", "mf_median_filter_3d_describe", "mf_d3_plan_check"]
 
 
 class MedianFilterError(RuntimeError):
@@ -84,6 +84,7 @@ def load_library(path=LIB_PATH):
         lib.mf_probe_minmax.argtypes = [i, i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         lib.mf_d1_plan_check.argtypes = [i, i, i, vp, vp, vp]
         lib.mf_median_filter_3d.argtypes = [vp, vp, i, i, i, sz, i, i, i, vp]
+        lib.mf_median_filter_3d_ex.argtypes = [vp, vp, i, i, i, sz, i, i, i, i, vp]
         lib.mf_median_filter_3d_describe.argtypes = [i, i, ctypes.c_char_p, sz]
         lib.mf_d3_plan_check.argtypes = [i, i, i, vp, vp, vp]
         lib.mf_status_string.argtypes = [i]
@@ -222,6 +223,11 @@ def mf_median_filter_3d(src, dst, D, H, W, pitch, volumes, dtype, k, stream=None
     return _check(load_library().mf_median_filter_3d(src, dst, D, H, W, pitch, volumes, dtype, k, stream))
 
 
+def mf_median_filter_3d_ex(src, dst, D, H, W, pitch, volumes, dtype, k, variant, stream=None):
+    return _check(load_library().mf_median_filter_3d_ex(src, dst, D, H, W, pitch, volumes, dtype, k, variant,
+                                                        stream))
+
+
 def mf_median_filter_3d_describe(k, dtype):
     buf = ctypes.create_string_buffer(512)
     _check(load_library().mf_median_filter_3d_describe(k, dtype, buf, 512))
@@ -324,9 +330,9 @@ def median_filter(x, k, variant="auto", return_idx=False, out=None, kh=None):
     return (out, idx) if return_idx else out
 
 
-def median_filter_3d(x, k, out=None):
+def median_filter_3d(x, k, out=None, variant="auto"):
     """k x k x k clamp-to-edge median of every (D, H, W) volume of a CUDA
-    tensor (..., D, H, W) of u8, u16, u32 or f32 (mf_median_filter_3d)."""
+    tensor (..., D, H, W) of u8, u16, u32 or f32 (mf_median_filter_3d_ex)."""
     torch = _torch()
     if x.dim() < 3:
         raise MedianFilterError("need (..., D, H, W)")
@@ -337,8 +343,8 @@ def median_filter_3d(x, k, out=None):
     if _planes(out) != (slices, H, W, pitch):
         raise MedianFilterError("out must have the layout of x")
     with torch.cuda.device(x.device):
-        mf_median_filter_3d(x.data_ptr(), out.data_ptr(), D, H, W, pitch, slices // D, dtype_code(x.dtype), int(k),
-                            _stream_ptr(x))
+        mf_median_filter_3d_ex(x.data_ptr(), out.data_ptr(), D, H, W, pitch, slices // D, dtype_code(x.dtype),
+                               int(k), VARIANTS[variant], _stream_ptr(x))
     return out
 
 

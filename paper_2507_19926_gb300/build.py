@@ -145,6 +145,7 @@ def generate():
         if name.startswith("o1_k") and name.endswith(".cu"):
             os.remove(os.path.join(GEN, name))
     codegen.write_if_changed(os.path.join(GEN, "d1_sortnets.cuh"), codegen.emit_d1_sortnets())
+    codegen.write_if_changed(os.path.join(GEN, "d3_nets.cuh"), codegen.emit_d3_networks())
     insts = _o1_instances()
     by_k = {}
     for inst in insts:  # one translation unit per instantiation (parallel build)

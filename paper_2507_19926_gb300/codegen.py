@@ -159,3 +159,42 @@ def emit_d1_sortnets(sizes=(2, 4, 8, 16, 32, 64)):
         out.append("};")
     out.append("}  // namespace mf")
     return "\n".join(out) + "\n"
+
+
+# Volumetric data-oblivious networks: (k, t) with a t^3 tile of voxels per
+# thread.  k = 3 with 2^3 tiles: 108 min/max per voxel on 64 footprint
+# registers.
+D3_NETS = ((3, 2),)
+
+
+def emit_d3_networks(cases=D3_NETS):
+    """Straight-line register code of netgen.build3d networks, as
+    D3Net<k>::run<KO>(f, out): f holds the F^3 footprint keys (F = t + k - 1,
+    element (fx, fy, fz) at (fz*F + fy)*F + fx), out receives the t^3
+    medians in (z, y, x) order."""
+    out = ["// generated by codegen.emit_d3_networks -- do not edit", "#pragma once", "namespace mf {",
+           "template <int K> struct D3Net;"]
+    for k, t in cases:
+        net = netgen.build3d(k, t)
+        F = t + k - 1
+        n_in = len(net.inputs)
+        out.append("template <> struct D3Net<%d> {" % k)
+        out.append("  static constexpr int k = %d, T = %d, F = %d, n_ops = %d;" % (k, t, F, len(net.ops)))
+        out.append("  template <class KO> static __device__ __forceinline__ void run(const typename KO::T *f,"
+                   " typename KO::T *out) {")
+        out.append("    typedef typename KO::T T;")
+
+        def ref(v):
+            if v < n_in:
+                _, fx, fy, fz = net.inputs[v]
+                return "f[%d]" % ((fz * F + fy) * F + fx)
+            return "v%d" % v
+
+        for kind, a, b, v in net.ops:
+            out.append("    const T v%d = KO::%s(%s, %s);" % (v, "mn" if kind == "min" else "mx", ref(a), ref(b)))
+        for i, v in enumerate(net.outputs):
+            out.append("    out[%d] = %s;" % (i, ref(v)))
+        out.append("  }")
+        out.append("};")
+    out.append("}  // namespace mf")
+    return "\n".join(out) + "\n"

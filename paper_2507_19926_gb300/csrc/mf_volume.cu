@@ -19,6 +19,7 @@
 
 #include "../../include/medianfilter_volume.h"
 #include "d1_sortnets.cuh"
+#include "d3_nets.cuh"
 #include "mf_d1_ops.cuh"
 #include "mf_registry.h"
 
@@ -120,6 +121,75 @@ __global__ void __launch_bounds__(1024) d3_kernel(VolArgs a, D3Dev p) {
             Dt<DT>::val((uint32_t)sm[p.out_off[i]]);
     }
 }
+
+// Data-oblivious form (Sec. 4 in 3D): one thread owns one T x T x T tile,
+// loads its (T + k - 1)^3 footprint into registers (clamped on every axis;
+// neighbouring threads share the loads through L1) and runs the generated
+// min/max network of the same tree (netgen.build3d) straight through: no
+// shared memory, no barriers.  Blocks of 32 x 4 threads along x and y;
+// blockIdx.z = tile slice + volume * tiles_z.
+template <class NET, int DT>
+__global__ void __launch_bounds__(128) d3o_kernel(VolArgs a, int tiles_z) {
+    typedef typename Dt<DT>::E E;
+    constexpr int T = NET::T, F = NET::F, R = (NET::k - 1) / 2;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * T;
+    const int y0 = (blockIdx.y * blockDim.y + threadIdx.y) * T;
+    const int z0 = (blockIdx.z % tiles_z) * T;
+    const int v = blockIdx.z / tiles_z;
+    if (x0 >= a.W || y0 >= a.H) return;
+    const char *src = a.src + (size_t)v * a.volume;
+    int xs[F];
+#pragma unroll
+    for (int fx = 0; fx < F; fx++) xs[fx] = clampi(x0 - R + fx, 0, a.W - 1);
+    uint32_t f[F * F * F];
+#pragma unroll
+    for (int fz = 0; fz < F; fz++) {
+        const int z = clampi(z0 - R + fz, 0, a.D - 1);
+#pragma unroll
+        for (int fy = 0; fy < F; fy++) {
+            const int y = clampi(y0 - R + fy, 0, a.H - 1);
+            const E *row = reinterpret_cast<const E *>(src + (size_t)z * a.slice + (size_t)y * a.pitch);
+#pragma unroll
+            for (int fx = 0; fx < F; fx++) f[(fz * F + fy) * F + fx] = Dt<DT>::key(__ldg(row + xs[fx]));
+        }
+    }
+    uint32_t o[T * T * T];
+    NET::template run<KoU32>(f, o);
+    char *dst = a.dst + (size_t)v * a.volume;
+#pragma unroll
+    for (int oz = 0; oz < T; oz++)
+#pragma unroll
+        for (int oy = 0; oy < T; oy++)
+#pragma unroll
+            for (int ox = 0; ox < T; ox++) {
+                const int x = x0 + ox, y = y0 + oy, z = z0 + oz;
+                if (x < a.W && y < a.H && z < a.D)
+                    reinterpret_cast<E *>(dst + (size_t)z * a.slice + (size_t)y * a.pitch)[x] =
+                        Dt<DT>::val(o[(oz * T + oy) * T + ox]);
+            }
+}
+
+// Launches the data-oblivious form if a network is built for k and the
+// grid fits; returns MF_ERR_UNSUPPORTED (nothing launched) otherwise.
+template <class NET>
+static int d3o_launch(const VolArgs &a0, int volumes, int dtype, cudaStream_t s) {
+    constexpr int T = NET::T;
+    VolArgs a = a0;
+    const long long tx = (a.W + T - 1) / T, ty = (a.H + T - 1) / T, tz = (a.D + T - 1) / T;
+    const long long gx = (tx + 31) / 32, gy = (ty + 3) / 4, gz = tz * volumes;
+    if (gx > 2147483647ll || gy > 65535 || gz > 65535) return MF_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)gz), block(32, 4, 1);
+    switch (dtype) {
+        case MF_U8: d3o_kernel<NET, MF_U8><<<grid, block, 0, s>>>(a, (int)tz); break;
+        case MF_U16: d3o_kernel<NET, MF_U16><<<grid, block, 0, s>>>(a, (int)tz); break;
+        case MF_U32: d3o_kernel<NET, MF_U32><<<grid, block, 0, s>>>(a, (int)tz); break;
+        default: d3o_kernel<NET, MF_F32><<<grid, block, 0, s>>>(a, (int)tz); break;
+    }
+    count_launch();
+    return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;
+}
+
+static bool d3o_built(int k) { return k == 3; }
 
 // ------------------------------------------------------------ host side
 struct D3Cached {
@@ -292,10 +362,18 @@ static int d3_check(const void *src, const void *dst, int D, int H, int W, size_
 
 using namespace mf;
 
-extern "C" int mf_median_filter_3d(const void *src, void *dst, int D, int H, int W, size_t pitch, int volumes,
-                                   mf_dtype dtype, int k, mf_stream_t stream) {
+extern "C" int mf_median_filter_3d_ex(const void *src, void *dst, int D, int H, int W, size_t pitch, int volumes,
+                                      mf_dtype dtype, int k, mf_variant variant, mf_stream_t stream) {
     int rc = d3_check(src, dst, D, H, W, pitch, volumes, (int)dtype, k);
     if (rc) return rc;
+    if (variant != MF_AUTO && variant != MF_OBLIVIOUS && variant != MF_DATA_AWARE) {
+        set_error("bad variant %d", (int)variant);
+        return MF_ERR_ARG;
+    }
+    if (variant == MF_OBLIVIOUS && k != 1 && !d3o_built(k)) {
+        set_error("no volumetric data-oblivious network built for k=%d", k);
+        return MF_ERR_UNSUPPORTED;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     if (k == 1) {
         if (cudaMemcpy2DAsync(dst, pitch, src, pitch, (size_t)W * elem_bytes(dtype), (size_t)volumes * D * H,
@@ -304,6 +382,28 @@ extern "C" int mf_median_filter_3d(const void *src, void *dst, int D, int H, int
             return MF_ERR_CUDA;
         }
         return MF_OK;
+    }
+    if (variant != MF_DATA_AWARE && d3o_built(k)) {
+        VolArgs a;
+        a.src = (const char *)src;
+        a.dst = (char *)dst;
+        a.D = D;
+        a.H = H;
+        a.W = W;
+        a.pitch = pitch;
+        a.slice = (size_t)H * pitch;
+        a.volume = (size_t)D * a.slice;
+        a.tiles_x = a.tiles_y = 0;
+        rc = d3o_launch<D3Net<3>>(a, volumes, (int)dtype, s);
+        if (rc == MF_OK) return MF_OK;
+        if (rc == MF_ERR_CUDA) {
+            set_error("volumetric network kernel: %s", cudaGetErrorString(cudaGetLastError()));
+            return rc;
+        }
+        if (variant == MF_OBLIVIOUS) {
+            set_error("volume too large for the data-oblivious grid");
+            return MF_ERR_UNSUPPORTED;
+        }
     }
     int err = MF_OK;
     const D3Cached *c = d3_get(k, (int)dtype, &err);
@@ -338,9 +438,20 @@ extern "C" int mf_median_filter_3d(const void *src, void *dst, int D, int H, int
     return rc;
 }
 
+extern "C" int mf_median_filter_3d(const void *src, void *dst, int D, int H, int W, size_t pitch, int volumes,
+                                   mf_dtype dtype, int k, mf_stream_t stream) {
+    return mf_median_filter_3d_ex(src, dst, D, H, W, pitch, volumes, dtype, k, MF_AUTO, stream);
+}
+
 extern "C" int mf_median_filter_3d_describe(int k, mf_dtype dtype, char *buf, size_t n) {
     if (!buf || n == 0) return MF_ERR_ARG;
     if ((int)dtype < MF_U8 || (int)dtype > MF_F32) return MF_ERR_DTYPE;
+    if (d3o_built(k)) {
+        snprintf(buf, n, "volumetric oblivious k=%d tile=%dx%dx%d block=32x4 net_ops=%d min/max per voxel=%.1f", k,
+                 D3Net<3>::T, D3Net<3>::T, D3Net<3>::T, D3Net<3>::n_ops,
+                 (double)D3Net<3>::n_ops / (D3Net<3>::T * D3Net<3>::T * D3Net<3>::T));
+        return MF_OK;
+    }
     if (k < 3 || k > D3_MAX_K || (k & 1) == 0) {
         snprintf(buf, n, "volumetric k=%d (no plan)", k);
         return MF_OK;

@@ -575,3 +575,132 @@ def count(net):
 def default_tile(k):
     """Root tile heuristic t(k) = 2^(floor(log2 k) - 1) (paper Sec. 4.2)."""
     return max(1, 1 << (k.bit_length() - 2)) if k >= 2 else 1
+
+
+def build3d(k, t):
+    """Data-oblivious network of the k x k x k median over a t x t x t tile
+    of voxels: hierarchical tiling extended to 3D (the paper's future work,
+    Sec. 7.2), with the tree of the volumetric data-aware plan.  Inputs
+    ("v", fx, fy, fz) are footprint voxels (F = t + k - 1 a side); outputs
+    are the t^3 medians in (z, y, x) order.
+
+    A node of tx x ty x tz outputs holds its core -- the box of window
+    positions all its outputs share -- sorted and pruned by forgetfulness
+    over n = k^3 (Sec. 2.2).  A split halves the longest side (x, y, z on
+    ties); a child merges into the parent's core the planes of window
+    positions on its side over the parent core's other two ranges.  Every
+    node keeps its extra planes sorted over its own core ranges, so a
+    child's plane is its parent's plane merged with the strip its split
+    added (the 2D extra rows and columns of Sec. 3.3-3.4, one dimension up).
+    Sorted boxes are memoised; a box is the largest sorted box inside it
+    merged with the sorted remainder, or a merge of sorted z pillars / x
+    lines."""
+    net = Network(k, t, t)
+    n = k ** 3
+    m = (n - 1) // 2
+    memo = {}
+
+    def inside(a, b):
+        return a[0] >= b[0] and a[1] <= b[1] and a[2] >= b[2] and a[3] <= b[3] and a[4] >= b[4] and a[5] <= b[5]
+
+    def vol(b):
+        return (b[1] - b[0] + 1) * (b[3] - b[2] + 1) * (b[5] - b[4] + 1)
+
+    def get(b):
+        if b in memo:
+            return memo[b]
+        x0, x1, y0, y1, z0, z1 = b
+        if (x0 == x1 and y0 == y1) or (y0 == y1 and z0 == z1):  # one line
+            r = net.sort([net.inp(("v", x, y, z)) for z in range(z0, z1 + 1)
+                          for y in range(y0, y1 + 1) for x in range(x0, x1 + 1)])
+        else:
+            line = max(z1 - z0 + 1, x1 - x0 + 1)
+            best = None
+            for c in memo:
+                if inside(c, b) and vol(c) > line and (best is None or vol(c) > vol(best)):
+                    best = c
+            if best is not None:
+                c = best
+                rest = []
+                if x0 < c[0]: rest.append((x0, c[0] - 1, y0, y1, z0, z1))
+                if c[1] < x1: rest.append((c[1] + 1, x1, y0, y1, z0, z1))
+                if y0 < c[2]: rest.append((c[0], c[1], y0, c[2] - 1, z0, z1))
+                if c[3] < y1: rest.append((c[0], c[1], c[3] + 1, y1, z0, z1))
+                if z0 < c[4]: rest.append((c[0], c[1], c[2], c[3], z0, c[4] - 1))
+                if c[5] < z1: rest.append((c[0], c[1], c[2], c[3], c[5] + 1, z1))
+                small = net.multiway_range([get(q) for q in rest], 0, 1 << 30)
+                r = net.merge(memo[c], small)
+            elif z1 - z0 >= x1 - x0:
+                r = net.multiway_range([get((x, x, y, y, z0, z1)) for y in range(y0, y1 + 1)
+                                        for x in range(x0, x1 + 1)], 0, 1 << 30)
+            else:
+                r = net.multiway_range([get((x0, x1, y, y, z, z)) for z in range(z0, z1 + 1)
+                                        for y in range(y0, y1 + 1)], 0, 1 << 30)
+        memo[b] = r
+        return r
+
+    def keep(c, d, held):
+        return max(0, m - d - (n - c)), min(held - 1, m - d)
+
+    ts = [t, t, t]
+    c = (k - t + 1) ** 3
+    lo, hi = keep(c, 0, c)
+    d = lo
+    pillars = [get((x, x, y, y, t - 1, k - 1)) for y in range(t - 1, k) for x in range(t - 1, k)]
+    nodes = [((0, 0, 0), net.multiway_range(pillars, lo, hi))]
+    while ts[0] * ts[1] * ts[2] > 1:
+        for o, _ in nodes:  # extra planes of every node, over its own core ranges
+            cr = [(o[a] + ts[a] - 1, o[a] + k - 1) for a in range(3)]
+            for a in range(3):
+                if ts[a] == 1:
+                    continue
+                for u in range(o[a], o[a] + k + ts[a] - 1):
+                    if cr[a][0] <= u <= cr[a][1]:
+                        continue
+                    rg = list(cr)
+                    rg[a] = (u, u)
+                    get((rg[0][0], rg[0][1], rg[1][0], rg[1][1], rg[2][0], rg[2][1]))
+        ax = 0 if ts[0] >= ts[1] and ts[0] >= ts[2] else (1 if ts[1] >= ts[2] else 2)
+        h = ts[ax] // 2
+        other = 1
+        for a in range(3):
+            if a != ax:
+                other *= k - ts[a] + 1
+        held = len(nodes[0][1])
+        c += h * other
+        lo, hi = keep(c, d, held + h * other)
+        nxt = []
+        for o, core in nodes:
+            cr = [(o[a] + ts[a] - 1, o[a] + k - 1) for a in range(3)]
+            for s in range(2):
+                u0 = o[ax] + h - 1 if s == 0 else o[ax] + k
+                planes = []
+                for u in range(u0, u0 + h):
+                    rg = list(cr)
+                    rg[ax] = (u, u)
+                    planes.append(get((rg[0][0], rg[0][1], rg[1][0], rg[1][1], rg[2][0], rg[2][1])))
+                slab = net.multiway_range(planes, 0, 1 << 30)
+                co = list(o)
+                co[ax] = o[ax] + s * h
+                nxt.append((tuple(co), net.merge_range(core, slab, lo, hi)))
+        nodes = nxt
+        ts[ax] = h
+        d += lo
+    out = [None] * t ** 3
+    for o, core in nodes:
+        assert len(core) == 1
+        out[(o[2] * t + o[1]) * t + o[0]] = core[0]
+    net.outputs = out
+    return prune(net)
+
+
+def evaluate3d(net, vox_fn):
+    """Run a build3d network on the host; vox_fn(fx, fy, fz) returns a numpy
+    array (one entry per tile instance).  Returns the outputs."""
+    import numpy as np
+    vals = [None] * (len(net.inputs) + len(net.ops))
+    for i, desc in enumerate(net.inputs):
+        vals[i] = vox_fn(desc[1], desc[2], desc[3])
+    for kind, a, b, v in net.ops:
+        vals[v] = (np.minimum if kind == "min" else np.maximum)(vals[a], vals[b])
+    return [vals[v] for v in net.outputs]

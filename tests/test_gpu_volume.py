@@ -12,12 +12,12 @@ pytestmark = pytest.mark.gpu
 DTYPES = ["u8", "u16", "u32", "f32"]
 
 
-def gpu_filter_3d(x, k):
+def gpu_filter_3d(x, k, variant="auto"):
     import torch
     import paper_2507_19926_gb300 as mf
     ensure_lib()
     xd = to_dev(x)
-    y = mf.median_filter_3d(xd, k)
+    y = mf.median_filter_3d(xd, k, variant=variant)
     torch.cuda.synchronize()
     return to_host(y, None)
 
@@ -70,3 +70,22 @@ def test_volume_256_cube_sampled_slices():
         lo, hi = max(0, z - 3), min(256, z + 4)
         want = oracle.median_filter_3d(x[lo:hi], 7)[z - lo]
         assert np.array_equal(got[z], want), z
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("variant", ["oblivious", "data_aware"])
+def test_volume_k3_both_variants(dt, variant):
+    """k = 3: the register network (data-oblivious) and the shared-memory
+    plan (data-aware) on volumes with ragged tails on every axis."""
+    for j, gen in enumerate((synth.uniform, synth.levels16)):
+        x = gen((3, 11, 37, 70), dt, 7000 + j)
+        assert same_bits(gpu_filter_3d(x, 3, variant), oracle.median_filter_3d(x, 3)), (dt, variant, j)
+    xs = f32_specials((7, 9, 40), 71) if dt == "f32" else synth.uniform((1, 1, 5), dt, 72)
+    assert same_bits(gpu_filter_3d(xs, 3, variant), oracle.median_filter_3d(xs, 3))
+
+
+def test_volume_oblivious_unbuilt_k_is_refused():
+    import paper_2507_19926_gb300 as mf
+    with pytest.raises(mf.MedianFilterError) as e:
+        gpu_filter_3d(synth.uniform((4, 5, 6), "u8", 1), 5, "oblivious")
+    assert e.value.status == mf.MF_ERR_UNSUPPORTED

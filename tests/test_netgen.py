@@ -196,3 +196,20 @@ def test_pressure_order_is_a_permutation_with_lower_peak(k, tw, th):
             live -= sum(1 for u in {x, y} if u >= n_in and last[u] == i)
         return best
     assert peak(b) <= peak(a)
+
+
+
+@pytest.mark.parametrize("k,t", [(3, 1), (3, 2), (5, 1), (5, 2)])
+def test_volume_network_matches_oracle(k, t):
+    """The 3D data-oblivious network (hierarchical tiling over a t^3 tile of
+    voxels, Sec. 7.2) evaluated on the host against the volumetric oracle,
+    on many footprints with heavy ties."""
+    net = netgen.build3d(k, t)
+    F = t + k - 1
+    vols = synth.levels16((40, F, F, F), "u16", 900 + 10 * k + t).astype(np.uint32)
+    outs = netgen.evaluate3d(net, lambda fx, fy, fz: vols[:, fz, fy, fx])
+    r = k // 2
+    for i in range(vols.shape[0]):
+        want = oracle.median_filter_3d(vols[i], k)[r:r + t, r:r + t, r:r + t].ravel()
+        assert np.array_equal(np.array([o[i] for o in outs]), want), (k, t, i)
+    assert all(kind in ("min", "max") for kind, _, _, _ in net.ops)
