@@ -429,6 +429,7 @@ def bench_sweep(dev, stream, flush, reps=3, ks=(3, 5, 9, 15, 21, 31, 45, 75), dt
 
 
 def bench_volume(dev, stream, flush, reps=3, cases=(("u8", 3, "auto"), ("u8", 3, "data_aware"), ("u8", 5, "auto"),
+                                                      ("u8", 5, "data_aware"), ("f32", 5, "auto"),
                                                       ("u8", 7, "auto"), ("u8", 9, "auto"), ("u8", 15, "auto"),
                                                       ("u8", 19, "auto"), ("u16", 7, "auto"), ("f32", 3, "auto"),
                                                       ("f32", 7, "auto"), ("f32", 19, "auto"))):

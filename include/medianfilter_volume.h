@@ -25,7 +25,7 @@ extern "C" {
  * (k-1)/2], clamped to the edge on every axis, ordered as in
  * mf_median_filter (f32 by the sign-flip key); the winner is copied bit for
  * bit.  MF_AUTO of mf_median_filter_3d_ex: the data-oblivious network
- * where one is built (k = 3), else the data-aware variant (Sec. 5) on
+ * where one is built (k = 3, 5), else the data-aware variant (Sec. 5) on
  * T x T x T root tiles of voxels: one thread block keeps a strip of tiles'
  * footprint and its whole tree of sorted lists in shared memory.
  *   src, dst: device, caller-owned, not aliasing; `volumes` volumes of D
@@ -43,7 +43,7 @@ int mf_median_filter_3d(const void *src, void *dst, int D, int H, int W, size_t 
 /* As mf_median_filter_3d with a choice of variant: MF_DATA_AWARE runs the
  * data-aware plan above (every k); MF_OBLIVIOUS a generated min/max network
  * of the same tree held in registers, one thread per 2 x 2 x 2 tile (the
- * data-oblivious variant of Sec. 4 in 3D; built for k = 3, else
+ * data-oblivious variant of Sec. 4 in 3D; built for k = 3 and 5, else
  * MF_ERR_UNSUPPORTED); MF_AUTO the network where one is built and the grid
  * fits, else the data-aware plan.  Bad variant: MF_ERR_ARG. */
 int mf_median_filter_3d_ex(const void *src, void *dst, int D, int H, int W, size_t pitch, int volumes,

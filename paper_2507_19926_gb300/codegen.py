@@ -163,8 +163,9 @@ def emit_d1_sortnets(sizes=(2, 4, 8, 16, 32, 64)):
 
 # Volumetric data-oblivious networks: (k, t) with a t^3 tile of voxels per
 # thread.  k = 3 with 2^3 tiles: 108 min/max per voxel on 64 footprint
-# registers.
-D3_NETS = ((3, 2),)
+# registers; k = 5 with 2^3 tiles: 643.5 per voxel on 216 footprint
+# registers (255 registers, some spills; a 1^3 tile would need 2378).
+D3_NETS = ((3, 2), (5, 2))
 
 
 def emit_d3_networks(cases=D3_NETS):

@@ -189,7 +189,7 @@ static int d3o_launch(const VolArgs &a0, int volumes, int dtype, cudaStream_t s)
     return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;
 }
 
-static bool d3o_built(int k) { return k == 3; }
+static bool d3o_built(int k) { return k == 3 || k == 5; }
 
 // ------------------------------------------------------------ host side
 struct D3Cached {
@@ -394,7 +394,7 @@ extern "C" int mf_median_filter_3d_ex(const void *src, void *dst, int D, int H, 
         a.slice = (size_t)H * pitch;
         a.volume = (size_t)D * a.slice;
         a.tiles_x = a.tiles_y = 0;
-        rc = d3o_launch<D3Net<3>>(a, volumes, (int)dtype, s);
+        rc = k == 3 ? d3o_launch<D3Net<3>>(a, volumes, (int)dtype, s) : d3o_launch<D3Net<5>>(a, volumes, (int)dtype, s);
         if (rc == MF_OK) return MF_OK;
         if (rc == MF_ERR_CUDA) {
             set_error("volumetric network kernel: %s", cudaGetErrorString(cudaGetLastError()));
@@ -447,9 +447,9 @@ extern "C" int mf_median_filter_3d_describe(int k, mf_dtype dtype, char *buf, si
     if (!buf || n == 0) return MF_ERR_ARG;
     if ((int)dtype < MF_U8 || (int)dtype > MF_F32) return MF_ERR_DTYPE;
     if (d3o_built(k)) {
-        snprintf(buf, n, "volumetric oblivious k=%d tile=%dx%dx%d block=32x4 net_ops=%d min/max per voxel=%.1f", k,
-                 D3Net<3>::T, D3Net<3>::T, D3Net<3>::T, D3Net<3>::n_ops,
-                 (double)D3Net<3>::n_ops / (D3Net<3>::T * D3Net<3>::T * D3Net<3>::T));
+        const int T = k == 3 ? D3Net<3>::T : D3Net<5>::T, ops = k == 3 ? D3Net<3>::n_ops : D3Net<5>::n_ops;
+        snprintf(buf, n, "volumetric oblivious k=%d tile=%dx%dx%d block=32x4 net_ops=%d min/max per voxel=%.1f", k, T,
+                 T, T, ops, (double)ops / (T * T * T));
         return MF_OK;
     }
     if (k < 3 || k > D3_MAX_K || (k & 1) == 0) {

@@ -74,18 +74,19 @@ def test_volume_256_cube_sampled_slices():
 
 @pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("variant", ["oblivious", "data_aware"])
-def test_volume_k3_both_variants(dt, variant):
-    """k = 3: the register network (data-oblivious) and the shared-memory
+@pytest.mark.parametrize("k", [3, 5])
+def test_volume_both_variants(k, dt, variant):
+    """k = 3, 5: the register network (data-oblivious) and the shared-memory
     plan (data-aware) on volumes with ragged tails on every axis."""
     for j, gen in enumerate((synth.uniform, synth.levels16)):
-        x = gen((3, 11, 37, 70), dt, 7000 + j)
-        assert same_bits(gpu_filter_3d(x, 3, variant), oracle.median_filter_3d(x, 3)), (dt, variant, j)
+        x = gen((3, 11, 37, 70), dt, 7000 + 10 * k + j)
+        assert same_bits(gpu_filter_3d(x, k, variant), oracle.median_filter_3d(x, k)), (dt, variant, j)
     xs = f32_specials((7, 9, 40), 71) if dt == "f32" else synth.uniform((1, 1, 5), dt, 72)
-    assert same_bits(gpu_filter_3d(xs, 3, variant), oracle.median_filter_3d(xs, 3))
+    assert same_bits(gpu_filter_3d(xs, k, variant), oracle.median_filter_3d(xs, k))
 
 
 def test_volume_oblivious_unbuilt_k_is_refused():
     import paper_2507_19926_gb300 as mf
     with pytest.raises(mf.MedianFilterError) as e:
-        gpu_filter_3d(synth.uniform((4, 5, 6), "u8", 1), 5, "oblivious")
+        gpu_filter_3d(synth.uniform((4, 5, 6), "u8", 1), 7, "oblivious")
     assert e.value.status == mf.MF_ERR_UNSUPPORTED

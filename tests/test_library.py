@@ -100,6 +100,6 @@ def test_volume_rejects_bad_arguments(lib):
     assert f(None, b, 4, 8, 8, 8, 1, 0, 3, None) == -1   # null
     g = lib.mf_median_filter_3d_ex
     assert g(a, b, 4, 8, 8, 8, 1, 0, 3, 7, None) == -1   # variant
-    assert g(a, b, 4, 8, 8, 8, 1, 0, 5, 1, None) == -9   # no network built for k = 5
-    assert "volumetric" in mf.mf_median_filter_3d_describe(5, mf.MF_U8)
+    assert g(a, b, 4, 8, 8, 8, 1, 0, 7, 1, None) == -9   # no network built for k = 7
+    assert "volumetric" in mf.mf_median_filter_3d_describe(7, mf.MF_U8)
     assert "oblivious" in mf.mf_median_filter_3d_describe(3, mf.MF_U8)
