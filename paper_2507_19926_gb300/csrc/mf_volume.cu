@@ -1,17 +1,20 @@
 // Volumetric k x k x k median by hierarchical tiling: the extension to 3D
-// that the paper names as future work (Sec. 7.2), built on its data-aware
-// variant (Sec. 5).
+// that the paper names as future work (Sec. 7.2), in both of its variants.
 //
-// The tree of a T x T x T root tile of voxels -- which z pillars and x lines
-// of the footprint are sorted, which sorted planes are merged into which
-// core, which ranks each merge keeps -- depends only on (k, T) and is
-// planned on the host (d3_build_plan in mf_d1_plan.cu).  One thread block
-// owns one root tile: it stages the (T + k - 1)^3 footprint as order keys in
-// shared memory (clamped to the volume on every axis), runs the planned
-// phases with a barrier between them (register sorting networks for the
-// lines, merge-path chunks for the merges, the same code as the 2D
-// data-aware kernel), and writes the T^3 medians.  Nothing but the volume
-// and the medians touches HBM.
+// Data-aware form (Sec. 5): the tree of a strip of T x T x T root tiles of
+// voxels -- which z pillars and x lines of the footprint are sorted, which
+// sorted planes are merged into which core, which ranks each merge keeps --
+// depends only on (k, T) and is planned on the host (d3_build_plan in
+// mf_d1_plan.cu).  One thread block owns one strip: it stages the footprint
+// as order keys in shared memory (clamped to the volume on every axis), runs
+// the planned phases with a barrier between them (register sorting networks
+// for the lines, merge-path chunks for the merges, the same code as the 2D
+// data-aware kernel), and writes the medians.  Nothing but the volume and
+// the medians touches HBM.
+//
+// Data-oblivious form (Sec. 4): the same tree as a generated straight-line
+// min/max network (netgen.build3d) over one thread's 2 x 2 x 2 tile, with
+// the footprint in registers, for k = 3 and 5.
 #include <cstdio>
 #include <map>
 #include <mutex>
