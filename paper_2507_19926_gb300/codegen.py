@@ -170,29 +170,39 @@ D3_NETS = ((3, 2), (5, 2))
 
 def emit_d3_networks(cases=D3_NETS):
     """Straight-line register code of netgen.build3d networks, as
-    D3Net<k>::run<KO>(f, out): f holds the F^3 footprint keys (F = t + k - 1,
-    element (fx, fy, fz) at (fz*F + fy)*F + fx), out receives the t^3
-    medians in (z, y, x) order."""
+    D3Net<k>::run<KO>(ld, out): ld(fx, fy, fz) returns the key of footprint
+    voxel (fx, fy, fz) (F = t + k - 1 a side), out receives the t^3 medians
+    in (z, y, x) order.  Ops run in the register-pressure-aware order of
+    netgen.schedule_pressure, and each footprint voxel is loaded just before
+    its first use, so the F^3 inputs are never all live at once (k = 5:
+    spills of 348-760 bytes a thread with the whole footprint loaded first,
+    0-56 bytes this way)."""
     out = ["// generated by codegen.emit_d3_networks -- do not edit", "#pragma once", "namespace mf {",
            "template <int K> struct D3Net;"]
     for k, t in cases:
         net = netgen.build3d(k, t)
+        net = netgen.schedule_pressure(net, list(range(len(net.outputs))))
         F = t + k - 1
         n_in = len(net.inputs)
         out.append("template <> struct D3Net<%d> {" % k)
         out.append("  static constexpr int k = %d, T = %d, F = %d, n_ops = %d;" % (k, t, F, len(net.ops)))
-        out.append("  template <class KO> static __device__ __forceinline__ void run(const typename KO::T *f,"
+        out.append("  template <class KO, class LD> static __device__ __forceinline__ void run(const LD &ld,"
                    " typename KO::T *out) {")
         out.append("    typedef typename KO::T T;")
+        loaded = set()
 
         def ref(v):
             if v < n_in:
-                _, fx, fy, fz = net.inputs[v]
-                return "f[%d]" % ((fz * F + fy) * F + fx)
+                if v not in loaded:
+                    loaded.add(v)
+                    _, fx, fy, fz = net.inputs[v]
+                    out.append("    const T i%d = ld(%d, %d, %d);" % (v, fx, fy, fz))
+                return "i%d" % v
             return "v%d" % v
 
         for kind, a, b, v in net.ops:
-            out.append("    const T v%d = KO::%s(%s, %s);" % (v, "mn" if kind == "min" else "mx", ref(a), ref(b)))
+            ra, rb = ref(a), ref(b)
+            out.append("    const T v%d = KO::%s(%s, %s);" % (v, "mn" if kind == "min" else "mx", ra, rb))
         for i, v in enumerate(net.outputs):
             out.append("    out[%d] = %s;" % (i, ref(v)))
         out.append("  }")

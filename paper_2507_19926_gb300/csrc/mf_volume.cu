@@ -125,11 +125,11 @@ __global__ void __launch_bounds__(1024) d3_kernel(VolArgs a, D3Dev p) {
     }
 }
 
-// Data-oblivious form (Sec. 4 in 3D): one thread owns one T x T x T tile,
-// loads its (T + k - 1)^3 footprint into registers (clamped on every axis;
-// neighbouring threads share the loads through L1) and runs the generated
-// min/max network of the same tree (netgen.build3d) straight through: no
-// shared memory, no barriers.  Blocks of 32 x 4 threads along x and y;
+// Data-oblivious form (Sec. 4 in 3D): one thread owns one T x T x T tile and
+// runs the generated min/max network of the same tree (netgen.build3d)
+// straight through, loading each voxel of its (T + k - 1)^3 footprint into a
+// register at its first use (clamped on every axis; neighbouring threads
+// share the loads through L1): no shared memory, no barriers.  Blocks of 32 x 4 threads along x and y;
 // blockIdx.z = tile slice + volume * tiles_z.
 template <class NET, int DT>
 __global__ void __launch_bounds__(128) d3o_kernel(VolArgs a, int tiles_z) {
@@ -141,23 +141,16 @@ __global__ void __launch_bounds__(128) d3o_kernel(VolArgs a, int tiles_z) {
     const int v = blockIdx.z / tiles_z;
     if (x0 >= a.W || y0 >= a.H) return;
     const char *src = a.src + (size_t)v * a.volume;
-    int xs[F];
-#pragma unroll
-    for (int fx = 0; fx < F; fx++) xs[fx] = clampi(x0 - R + fx, 0, a.W - 1);
-    uint32_t f[F * F * F];
-#pragma unroll
-    for (int fz = 0; fz < F; fz++) {
+    // footprint voxel (fx, fy, fz), clamped on every axis; the network loads
+    // each one just before its first use
+    auto ld = [&](int fx, int fy, int fz) -> uint32_t {
+        const int x = clampi(x0 - R + fx, 0, a.W - 1);
+        const int y = clampi(y0 - R + fy, 0, a.H - 1);
         const int z = clampi(z0 - R + fz, 0, a.D - 1);
-#pragma unroll
-        for (int fy = 0; fy < F; fy++) {
-            const int y = clampi(y0 - R + fy, 0, a.H - 1);
-            const E *row = reinterpret_cast<const E *>(src + (size_t)z * a.slice + (size_t)y * a.pitch);
-#pragma unroll
-            for (int fx = 0; fx < F; fx++) f[(fz * F + fy) * F + fx] = Dt<DT>::key(__ldg(row + xs[fx]));
-        }
-    }
+        return Dt<DT>::key(__ldg(reinterpret_cast<const E *>(src + (size_t)z * a.slice + (size_t)y * a.pitch) + x));
+    };
     uint32_t o[T * T * T];
-    NET::template run<KoU32>(f, o);
+    NET::template run<KoU32>(ld, o);
     char *dst = a.dst + (size_t)v * a.volume;
 #pragma unroll
     for (int oz = 0; oz < T; oz++)

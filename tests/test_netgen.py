@@ -213,3 +213,8 @@ def test_volume_network_matches_oracle(k, t):
         want = oracle.median_filter_3d(vols[i], k)[r:r + t, r:r + t, r:r + t].ravel()
         assert np.array_equal(np.array([o[i] for o in outs]), want), (k, t, i)
     assert all(kind in ("min", "max") for kind, _, _, _ in net.ops)
+    # the emitted (pressure-aware) order computes the same
+    sched = netgen.schedule_pressure(net, list(range(len(net.outputs))))
+    assert sorted(op[3] for op in sched.ops) == sorted(op[3] for op in net.ops)
+    souts = netgen.evaluate3d(sched, lambda fx, fy, fz: vols[:, fz, fy, fx])
+    assert all(np.array_equal(a, b) for a, b in zip(outs, souts))
