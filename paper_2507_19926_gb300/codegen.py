@@ -162,9 +162,10 @@ def emit_d1_sortnets(sizes=(2, 4, 8, 16, 32, 64)):
 
 
 # Volumetric data-oblivious networks: (k, t) with a t^3 tile of voxels per
-# thread.  k = 3 with 2^3 tiles: 108 min/max per voxel on 64 footprint
-# registers; k = 5 with 2^3 tiles: 643.5 per voxel on 216 footprint
-# registers (255 registers, some spills; a 1^3 tile would need 2378).
+# thread.  k = 3 with 2^3 tiles: 108 min/max per voxel over a 64-voxel
+# footprint; k = 5 with 2^3 tiles: 643.5 per voxel over 216 voxels (a 1^3
+# tile would need 2378), which fits 255 registers only with the footprint
+# loaded at first use.
 D3_NETS = ((3, 2), (5, 2))
 
 
