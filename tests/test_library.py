@@ -103,3 +103,15 @@ def test_volume_rejects_bad_arguments(lib):
     assert g(a, b, 4, 8, 8, 8, 1, 0, 7, 1, None) == -9   # no network built for k = 7
     assert "volumetric" in mf.mf_median_filter_3d_describe(7, mf.MF_U8)
     assert "oblivious" in mf.mf_median_filter_3d_describe(3, mf.MF_U8)
+
+
+def test_volume_describe_carries_the_work_counts(lib):
+    """bench.py reads the per-voxel work of a volume plan from these lines
+    (roofline fractions): the network form gives its min/max per voxel, the
+    data-aware form its merged and sorted elements per voxel."""
+    import re
+    net = mf.mf_median_filter_3d_describe(5, mf.MF_U8)
+    assert re.search(r"min/max per voxel=([\d.]+)", net) and "oblivious" in net
+    plan = mf.mf_median_filter_3d_describe(9, mf.MF_F32)
+    m = re.search(r"merged/vox=([\d.]+) sorted/vox=([\d.]+)", plan)
+    assert m and float(m.group(1)) > 0 and "data-aware" in plan
