@@ -256,6 +256,12 @@ def test_volume_matches_scipy_nearest(dt, k):
                                   scipy_nd.median_filter(xl, size=k, mode="nearest"))
 
 
+def test_volume_hand_worked_2x2x2():
+    g = _load("hand_2x2x2_k3_volume.json")
+    x = np.array(g["input"], synth.NP[g["dtype"]])
+    np.testing.assert_array_equal(oracle.median_filter_3d(x, g["k"]), np.array(g["output"], x.dtype))
+
+
 def test_volume_brute_force_edge_padded():
     """Rank (k^3-1)/2 of the window gathered from an edge-padded volume."""
     for k, shape, seed in ((3, (4, 5, 6), 1), (5, (3, 7, 4), 2), (3, (1, 1, 9), 3)):
