@@ -17,8 +17,8 @@ scipy.ndimage's median filter, the counting characterisation of a rank,
 k=1, constant images and monotone remaps; the argmedian tie rule by
 hand-worked fixtures with ties; the backward by a hand-worked case and
 central finite differences.  The volumetric k x k x k filter
-(``median_filter_3d``) is pinned by scipy.ndimage's 3D median, a numpy brute
-force over an edge-padded volume, the one-slice reduction to the 2D filter,
+(``median_filter_3d``) is pinned by a hand-worked 2x2x2 volume, scipy.ndimage's
+3D median, a numpy brute force over an edge-padded volume, the one-slice reduction to the 2D filter,
 axis permutations, constants and k = 1.
 """
 import ctypes
