@@ -34,7 +34,7 @@ def test_plan_matches_oracle(k, T):
     assert st["max_sort"] <= 32 and st["phases"] >= 3
 
 
-@pytest.mark.parametrize("k,T,B", [(3, 2, 8), (5, 4, 2), (7, 2, 4), (9, 4, 2)])
+@pytest.mark.parametrize("k,T,B", [(3, 2, 8), (5, 4, 2), (5, 4, 4), (7, 2, 4), (7, 4, 2), (9, 4, 2)])
 def test_strip_plan_matches_oracle(k, T, B):
     """A strip of B root tiles along x sharing their lines and planes."""
     F, FX = T + k - 1, B * T + k - 1
