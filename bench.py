@@ -16,6 +16,7 @@ sample of the same workload (the reference arm of this tier).
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -144,6 +145,84 @@ def algorithmic_ops_per_px(k):
             best = v if best is None else min(best, v)
         t *= 2
     return best
+
+
+_O1_NAME = re.compile(r"o1_launch_k(\d+)_(\d+)x(\d+)_b(\d+)x(\d+)_u(m1|\d+)((?:_[a-z]{2})*)_MF_\w+?_Ko(U16x2|U32)")
+
+
+def o1_executed_per_px(plan):
+    """Min/max instructions the data-oblivious kernel named in `plan` issues
+    per output pixel: its generated network with three-input fusion (one
+    instruction per fused op) plus the column sorts, divided by the pixels
+    one instruction serves (two tiles a register for packed 16-bit keys).
+    None when the plan names no such kernel."""
+    from paper_2507_19926_gb300 import netgen
+    m = _O1_NAME.search(plan)
+    if not m:
+        return None
+    k, tw, th, bx, by = (int(v) for v in m.groups()[:5])
+    form = m.group(7)
+    lanes = 2 if m.group(8) == "U16x2" else 1
+    net = netgen.build(k, tw, th, rows_smem="_rs" in form, lazy="_lz" in form, pressure="_pr" in form)
+    ops = len(netgen.fuse3(net).ops)
+    cs = len(netgen.column_sort_network(k - th + 1).ops)
+    if "_dr" in form:  # direct form: every thread sorts its own footprint columns
+        per_thread = ops + (tw + k - 1) * cs
+    else:  # block-wide column sort over the block footprint, shared by its threads
+        per_thread = ops + by * (bx * tw + k - 1) * cs / (bx * by)
+    return per_thread / (tw * th * lanes)
+
+
+_PROBE = {}
+
+
+def probe_ipc(sms, mhz, lanes):
+    """Measured min/max instructions per clock per SM (mf_probe_minmax, u32
+    or packed u16x2), at the SM clock `mhz` sampled while the bench ran."""
+    import paper_2507_19926_gb300 as mf
+    if lanes not in _PROBE:
+        rate, _ = mf.mf_probe_minmax(1 if lanes == 2 else 0)
+        _PROBE[lanes] = rate / (sms * mhz * 1e6)
+    return _PROBE[lanes]
+
+
+def roofline_entry(plan, dt, k, px, ms, sms, peaks, probe_mhz=None, with_idx=False):
+    """Roofline of one filter call: the floor is the slower of its HBM bytes
+    (in + out) and its work at the unit that bounds the variant -- min/max
+    issue for the data-oblivious networks (the cheapest hierarchy the
+    generator emits), shared-memory bytes for the data-aware merges (every
+    merged or sorted element read once and written once).  `frac` =
+    floor / measured time for the bound that is larger."""
+    import re
+    max_mhz = peaks.get("sm_max_mhz", 2070.0)
+    es = {"u8": 1, "u16": 2, "u32": 4, "f32": 4}[dt]
+    hbm_gbs = peaks.get("hbm_gbs") or 6800.0
+    t_hbm = px * (2 * es + (4 if with_idx else 0)) / (hbm_gbs * 1e9)
+    out = {"hbm_frac": round(t_hbm / (ms * 1e-3), 4)}
+    t_work, bound = None, None
+    if "oblivious" in plan:
+        lanes = 2 if dt in ("u8", "u16") else 1
+        ipc = probe_ipc(sms, probe_mhz or max_mhz, lanes)
+        ipc_nominal = 64.0 if ipc < 96 else 128.0
+        peak = sms * ipc_nominal * max_mhz * 1e6 * lanes  # element-ops/s
+        ops = algorithmic_ops_per_px(k)
+        t_work, bound = ops * px / peak, "alu"
+        out["alu_frac"] = round(t_work / (ms * 1e-3), 4)
+        ex = o1_executed_per_px(plan)
+        if ex is not None:  # instructions actually issued, against the instruction rate
+            out["executed_instr_frac"] = round(ex * px / (sms * ipc_nominal * max_mhz * 1e6) / (ms * 1e-3), 4)
+    elif "data-aware" in plan:
+        m = re.search(r"merged/px=([\d.]+) sorted/px=([\d.]+)", plan)
+        if m:
+            kb = (4 if with_idx else 2) if dt in ("u8", "u16") else (8 if with_idx else 4)
+            elems = float(m.group(1)) + float(m.group(2))
+            t_work, bound = elems * 2 * kb * px / (sms * 128 * max_mhz * 1e6), "smem"
+            out["smem_frac"] = round(t_work / (ms * 1e-3), 4)
+    if t_work is None or t_hbm >= t_work:
+        out["bound"], out["frac"] = "hbm", out["hbm_frac"]
+    else:
+        out["bound"], out["frac"] = bound, round(t_work / (ms * 1e-3), 4)
+    return out
 
 
 def measured_traffic(plan):
@@ -406,26 +485,57 @@ def bench_rect(dev, stream, flush, reps=3, cases=(("u8", 31, 7), ("u8", 7, 31), 
     return res
 
 
-def bench_sweep(dev, stream, flush, reps=3, ks=(3, 5, 9, 15, 21, 31, 45, 75), dts=("u8", "u16", "u32", "f32")):
-    """4096 x 4096 single-plane images, uniform values, auto variant."""
+SWEEP_KS = (3, 5, 7, 9, 11, 15, 21, 31, 45, 61, 75)
+
+
+def bench_sweep(dev, stream, flush, peaks, probe_mhz, reps=3, ks=SWEEP_KS, dts=("u8", "u16", "u32", "f32")):
+    """4096 x 4096 single-plane images in every dtype, k over the sweep's
+    set, two value distributions (uniform over the full range, and 16
+    levels: heavy ties), auto variant; each cell with its roofline."""
     import torch
     import paper_2507_19926_gb300 as mf
     from paper_2507_19926_gb300 import synth
     codes = {"u8": mf.MF_U8, "u16": mf.MF_U16, "u32": mf.MF_U32, "f32": mf.MF_F32}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     res = []
     sptr = stream.cuda_stream
+    px = 4096 * 4096
     for dt in dts:
-        x = to_device(synth.uniform((1, 4096, 4096), dt, synth.SEED_BASE + 2), dev)
-        y = torch.empty_like(x)
-        pitch = 4096 * x.element_size()
-        for k in ks:
-            f = lambda: mf.mf_median_filter(x.data_ptr(), y.data_ptr(), 4096, 4096, pitch, 1, codes[dt], k,
-                                            mf.MF_BORDER_CLAMP, sptr)
-            f()
-            ms = _time_ms(f, stream, reps, flush)
-            res.append({"dtype": dt, "k": k, "ms": round(ms, 4), "mpix_s": round(4096 * 4096 / ms / 1e3, 1),
-                        "plan": mf.mf_describe(4096, 4096, 1, codes[dt], k).split(" kernel=")[0]})
+        for dist, gen in (("uniform", synth.uniform), ("levels16", synth.levels16)):
+            x = to_device(gen((1, 4096, 4096), dt, synth.SEED_BASE + 2), dev)
+            y = torch.empty_like(x)
+            pitch = 4096 * x.element_size()
+            for k in ks:
+                f = lambda: mf.mf_median_filter(x.data_ptr(), y.data_ptr(), 4096, 4096, pitch, 1, codes[dt], k,
+                                                mf.MF_BORDER_CLAMP, sptr)
+                f()
+                ms = _time_ms(f, stream, reps, flush)
+                plan = mf.mf_describe(4096, 4096, 1, codes[dt], k)
+                res.append({"dtype": dt, "dist": dist, "k": k, "ms": round(ms, 4),
+                            "mpix_s": round(px / ms / 1e3, 1),
+                            "roofline": roofline_entry(plan, dt, k, px, ms, sms, peaks, probe_mhz),
+                            "plan": plan.split(" kernel=")[0]})
+            del x, y
     return res
+
+
+def bench_photo_data_aware(dev, stream, flush, peaks, probe_mhz, x, reps=5):
+    """The 30 MP RGB u8 photo, k = 17, through the data-aware variant (the
+    headline runs the auto choice, the data-oblivious network)."""
+    import torch
+    import paper_2507_19926_gb300 as mf
+    C, H, W = x.shape
+    y = torch.empty_like(x)
+    sptr = stream.cuda_stream
+    f = lambda: mf.mf_median_filter_ex(x.data_ptr(), y.data_ptr(), H, W, W, C, mf.MF_U8, 17, mf.MF_BORDER_CLAMP,
+                                       mf.MF_DATA_AWARE, None, 0, sptr)
+    f()
+    ms = _time_ms(f, stream, reps, flush)
+    plan = mf.mf_describe(H, W, C, mf.MF_U8, 17, mf.MF_DATA_AWARE)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return {"workload": "photo_rgb_30mp_u8_k17", "variant": "data_aware", "ms": round(ms, 4),
+            "mpix_s": round(C * H * W / ms / 1e3, 1),
+            "roofline": roofline_entry(plan, "u8", 17, C * H * W, ms, sms, peaks, probe_mhz), "plan": plan}
 
 
 def bench_volume(dev, stream, flush, reps=3, cases=(("u8", 3, "auto"), ("u8", 3, "data_aware"), ("u8", 5, "auto"),
@@ -550,26 +660,30 @@ def run_ours(args):
     plan = mf.mf_describe(H, W, C, code, k, variant)
     peaks = read_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = peaks.get("sm_max_mhz", 2070.0)
+    # the probe's instructions per clock are taken at the clock sampled under load
+    probe_mhz = clocks["sm_mhz"] if clocks else max_mhz
     roof = None
     extra = {}
     if "oblivious" in plan:
         lanes = 2 if dt in ("u8", "u16") else 1
         ops_px = algorithmic_ops_per_px(k)
-        kind = 1 if lanes == 2 else 0
-        rate, _ = mf.mf_probe_minmax(kind)
-        max_mhz = peaks.get("sm_max_mhz", 2070.0)
-        # min/max instructions per clock per SM from the probe, at the clock it ran
-        probe_mhz = clocks["sm_mhz"] if clocks else max_mhz
-        ipc = rate / (sms * probe_mhz * 1e6)
+        ipc = probe_ipc(sms, probe_mhz, lanes)
         ipc_nominal = 64.0 if ipc < 96 else 128.0
         peak = sms * ipc_nominal * max_mhz * 1e6 * lanes / 1e9  # G element-ops/s
         achieved = ops_px * px_per_step / (ms_per_step * 1e-3) / 1e9
+        ex = o1_executed_per_px(plan)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gminmax/s",
                 "frac": achieved / peak, "traffic": measured_traffic(plan),
                 "basis": "%.1f min/max element-ops per pixel (cheapest generated hierarchy) x %d px; "
                          "peak = %d SMs x %d min/max instr/clk/SM x %.0f MHz x %d lanes "
                          "(probe: %.1f instr/clk/SM at %.0f MHz)" % (
                              ops_px, px_per_step, sms, ipc_nominal, max_mhz, lanes, ipc, probe_mhz)}
+        if ex is not None:
+            # what the kernel issues: its own network (lazy tree, fused
+            # three-input ops) plus column sorts, one instruction each
+            roof["executed_instr_per_px"] = round(ex, 2)
+            roof["executed_instr_frac"] = ex * px_per_step / (sms * ipc_nominal * max_mhz * 1e6) / (ms_per_step * 1e-3)
     elif "data-aware" in plan:
         # shared-memory merging: every merged or sorted element is read once
         # and written once at the least; peak = 128 B/clk/SM of shared memory
@@ -601,7 +715,9 @@ def run_ours(args):
         extra["small_frame"] = bench_small(dev, stream)
         extra["batched_vs_plain"] = bench_batched(dev, stream, flush)
         extra["fwd_bwd_vs_fwd"] = bench_fwd_bwd(dev, stream, flush)
-        extra["sweep_4096"] = bench_sweep(dev, stream, flush)
+        if args.workload == "photo_rgb_30mp_u8_k17":
+            extra["photo_data_aware"] = bench_photo_data_aware(dev, stream, flush, peaks, probe_mhz, x)
+        extra["sweep_4096"] = bench_sweep(dev, stream, flush, peaks, probe_mhz)
         extra["rect_4096"] = bench_rect(dev, stream, flush)
         extra["volume_256"] = bench_volume(dev, stream, flush)
     out = {

@@ -184,7 +184,7 @@ int mf_batch_describe(const mf_batch_plan *plan, int *kernels, long long *items)
  * 2 MiB that the library's module holds on every device where it is used,
  * until the library is unloaded.  Limits: at most 256 images, k = 1 or a
  * k the data-oblivious kernels are built for (odd 3 to 27), and at most
- * 126,976 work items (one item is one
+ * 129,392 work items (one item is one
  * thread block's pixels -- lanes x block width x tile width by block height
  * x tile height, as mf_describe reports them: from 64 x 8 (k = 3, 32-bit
  * data) to 256 x 16 (k = 7, 8/16-bit data)); beyond them it returns
@@ -194,11 +194,18 @@ int mf_batch_describe(const mf_batch_plan *plan, int *kernels, long long *items)
  * call): the image table and work records are copied from the stack, the
  * queue counters are cleared on every call.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
- * share the array and it keeps the last call's contents, so calls whose
- * work overlaps on the GPU (different streams, or devices sharing the
- * module) race; calls issued in order on one stream are safe.  Work is
- * enqueued on `stream`; the call returns without waiting for it. */
+ * device current; make that first call before any stream capture.  The
+ * table copies come from pageable (stack) memory, so the call may wait
+ * until earlier work on `stream` has drained before it returns; for the
+ * same reason a call on a stream that is being captured is rejected with
+ * MF_ERR_UNSUPPORTED.  Each device has its own copy of the array, which
+ * keeps the last call's contents, so calls whose work overlaps on the GPU
+ * of one device (different streams, or threads sharing a device) race;
+ * calls issued in order on one stream are safe.  Work is enqueued on
+ * `stream` and the call does not wait for it to finish.  An error returned
+ * after the argument checks (a failed launch) can leave the kernel classes
+ * enqueued before the failure in the stream: their images may be
+ * filtered, the others are not. */
 int mf_batch_run_static(const mf_image_desc *descs, int n, mf_stream_t stream);
 
 /* ---- tuning and introspection ------------------------------------------ */

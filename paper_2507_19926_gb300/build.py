@@ -79,6 +79,11 @@ O1_VALUE = {3: [(2, 2, 32, 4, -1, 8), (2, 2, 32, 4, -1, 0)],
 for _spec in filter(None, os.environ.get("MF_O1_EXTRA", "").split(",")):
     _v = [int(v) for v in _spec.split(":")]
     O1_VALUE.setdefault(_v[0], []).append(tuple((_v + [0, 0, 0])[1:8]))
+# MF_O1_ONLY="k1,k2,...": build the data-oblivious kernels for these k only
+# (a smaller, faster build; the data-aware variant still covers every k)
+if os.environ.get("MF_O1_ONLY"):
+    _only = {int(v) for v in os.environ["MF_O1_ONLY"].split(",") if v.strip()}
+    O1_VALUE = {k: v for k, v in O1_VALUE.items() if k in _only}
 # a 7th field restricts a configuration to 16-bit keys (u8/u16, two tiles a
 # thread) or 32-bit keys (u32/f32); 0 = both; 1 = u8/u16 data with 32-bit
 # keys (one tile a thread: half the values in flight of the packed form)

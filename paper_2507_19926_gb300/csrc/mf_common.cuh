@@ -7,6 +7,7 @@
 // are bit-identical values.  Min/max networks on keys therefore select the
 // exact input element (paper Sec. 4: networks compile to min/max sequences).
 #pragma once
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -125,6 +126,23 @@ struct ImgArgs {
     size_t idx_pitch;   // bytes per row of idx
     size_t idx_plane;   // bytes per plane of idx
 };
+
+// Function attributes (cudaFuncSetAttribute) belong to the context of the
+// device that is current when they are set, so every kernel instantiation is
+// configured once per device: bit d of a DevMask records device d (0..63;
+// devices beyond that are configured on every call).
+typedef std::atomic<unsigned long long> DevMask;
+inline bool dev_configured(const DevMask &m, int *dev) {
+    if (cudaGetDevice(dev) != cudaSuccess) {
+        cudaGetLastError();
+        *dev = -1;
+        return false;
+    }
+    return *dev >= 0 && *dev < 64 && ((m.load(std::memory_order_acquire) >> *dev) & 1ull);
+}
+inline void dev_mark_configured(DevMask &m, int dev) {
+    if (dev >= 0 && dev < 64) m.fetch_or(1ull << dev, std::memory_order_acq_rel);
+}
 
 // Kernel launch counter (host side, see mf_kernel_launch_count).
 void count_launch(unsigned n = 1);

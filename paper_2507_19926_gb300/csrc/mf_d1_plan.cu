@@ -21,6 +21,7 @@
 // exchanges rows and columns.  Merges whose needed output ranks are known
 // only read the input ranks that can reach them.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstdio>
 #include <functional>
@@ -39,6 +40,9 @@ namespace mf {
 // (min 16, div 2), wider keys with (min 12, div 1).  MF_D1_CHUNK="min:div"
 // overrides both (tuning sweeps).
 static const bool D1_ODD_CHUNKS = !getenv("MF_D1_EVEN_CHUNKS");
+// Phase balancing of the tasks off the critical chain (MF_D1_BALANCE=0
+// keeps every task in its earliest phase).
+static const bool D1_BALANCE = !getenv("MF_D1_BALANCE") || atoi(getenv("MF_D1_BALANCE")) != 0;
 
 static void chunk_rule(int key_bytes, int *min_chunk, int *div) {
     *min_chunk = key_bytes <= 2 ? 16 : 12;
@@ -336,16 +340,121 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
         lphase[t.out] = p;
         nph = std::max(nph, p + 1);
     }
-    // last use of every list
+    // ---------------------------------------------------------- balancing
+    // The phase count is the tree's dependency depth (the chain of core
+    // merges).  Tasks off that chain -- extending extra rows and columns,
+    // merging the new columns of a later split -- have slack: each may run
+    // in any phase between its earliest (inputs ready) and its latest (all
+    // readers still after it).  Placing each in the least-loaded phase of
+    // that window evens out the work of the phases (the threads of a block
+    // wait for the slowest one at every barrier) and produces lists closer
+    // to where they are read, which shortens their lifetimes in shared
+    // memory.
+    if (D1_BALANCE && nph > 1) {
+        std::vector<std::vector<int>> readers(B.lists.size());
+        for (size_t ti = 0; ti < B.tasks.size(); ti++) {
+            if (!keep[ti]) continue;
+            const PTask &t = B.tasks[ti];
+            if (t.a.list >= 0) readers[t.a.list].push_back((int)ti);
+            if (t.b.list >= 0 && t.b.list != t.a.list) readers[t.b.list].push_back((int)ti);
+        }
+        std::vector<bool> is_out(B.lists.size(), false);
+        for (const Ref &r : outs)
+            if (r.list >= 0) is_out[r.list] = true;
+        std::vector<int> alap(B.tasks.size(), nph - 1);
+        for (int ti = (int)B.tasks.size() - 1; ti >= 0; ti--) {
+            if (!keep[ti]) continue;
+            int a = nph - 1;
+            for (int r : readers[B.tasks[ti].out]) a = std::min(a, alap[r] - 1);
+            if (is_out[B.tasks[ti].out]) a = std::min(a, nph - 1);
+            alap[ti] = a;
+        }
+        // cost in merged-element units: a merge costs its outputs, a sort of
+        // n elements about n (log2 n)^2 / 8 (a register sorting network)
+        auto cost = [&](const PTask &t) -> double {
+            if (t.type == D1_MERGE) return t.hi - t.lo + 1;
+            const double n = t.a.len, l = std::log2(std::max(2.0, n));
+            return n * std::max(1.0, l * l / 8);
+        };
+        // windows [asap, alap]; tasks are placed least-slack first (the
+        // chain has none), each in the least-loaded phase of its current
+        // window; a placement narrows the windows of everything that
+        // depends on it, or that it depends on, so every window stays
+        // non-empty
+        std::vector<int> asap(task_phase);
+        std::vector<std::vector<int>> succ(B.tasks.size()), pred(B.tasks.size());
+        std::vector<int> producer(B.lists.size(), -1);
+        for (size_t ti = 0; ti < B.tasks.size(); ti++)
+            if (keep[ti]) producer[B.tasks[ti].out] = (int)ti;
+        for (size_t ti = 0; ti < B.tasks.size(); ti++) {
+            if (!keep[ti]) continue;
+            const PTask &t = B.tasks[ti];
+            for (int l : {t.a.list, t.b.list})
+                if (l >= 0 && producer[l] >= 0) {
+                    succ[producer[l]].push_back((int)ti);
+                    pred[ti].push_back(producer[l]);
+                }
+        }
+        std::vector<int> order;
+        for (size_t ti = 0; ti < B.tasks.size(); ti++)
+            if (keep[ti]) order.push_back((int)ti);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            const int sx = alap[x] - asap[x], sy = alap[y] - asap[y];
+            if (sx != sy) return sx < sy;
+            return cost(B.tasks[x]) > cost(B.tasks[y]);
+        });
+        std::vector<double> load(nph, 0.0);
+        std::vector<int> stack;
+        for (int ti : order) {
+            const double c = cost(B.tasks[ti]);
+            int p = asap[ti];
+            for (int q = asap[ti] + 1; q <= alap[ti]; q++)
+                if (load[q] <= load[p]) p = q;  // ties: the later phase
+            load[p] += c;
+            asap[ti] = alap[ti] = p;
+            stack.assign(1, ti);
+            while (!stack.empty()) {  // readers start after p
+                const int u = stack.back();
+                stack.pop_back();
+                for (int v : succ[u])
+                    if (asap[v] < asap[u] + 1) {
+                        asap[v] = asap[u] + 1;
+                        stack.push_back(v);
+                    }
+            }
+            stack.assign(1, ti);
+            while (!stack.empty()) {  // producers finish before p
+                const int u = stack.back();
+                stack.pop_back();
+                for (int v : pred[u])
+                    if (alap[v] > alap[u] - 1) {
+                        alap[v] = alap[u] - 1;
+                        stack.push_back(v);
+                    }
+            }
+        }
+        std::vector<int> lp(B.lists.size(), -1);
+        for (size_t ti = 0; ti < B.tasks.size(); ti++)
+            if (keep[ti]) {
+                task_phase[ti] = asap[ti];
+                lp[B.tasks[ti].out] = asap[ti];
+            }
+        lphase.swap(lp);
+    }
+    // last use of every list, and of the footprint (read by sorts only)
     std::vector<int> last(B.lists.size(), -1);
+    int foot_last = -1;
     for (size_t ti = 0; ti < B.tasks.size(); ti++) {
         if (!keep[ti]) continue;
         const PTask &t = B.tasks[ti];
         if (t.a.list >= 0) last[t.a.list] = std::max(last[t.a.list], task_phase[ti]);
         if (t.b.list >= 0) last[t.b.list] = std::max(last[t.b.list], task_phase[ti]);
+        if (t.a.list == -1 || t.b.list == -1) foot_last = std::max(foot_last, task_phase[ti]);
     }
-    for (const Ref &r : outs)
+    for (const Ref &r : outs) {
         if (r.list >= 0) last[r.list] = nph;  // read after the last phase
+        if (r.list == -1) foot_last = nph;
+    }
 
     // ---------------------------------------------------------- allocation
     // first fit over a free list, phase by phase; the footprint sits at 0
@@ -389,6 +498,8 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
         return off;
     };
     for (int p = 0; p <= nph; p++) {
+        // the footprint is free once its last reader has run
+        if (D1_BALANCE && p == foot_last + 1 && base > 0) release(0, base);
         for (int li : dies[p]) release(B.lists[li].off, B.lists[li].len);
         if (p < nph)
             for (int li : prod[p]) B.lists[li].off = alloc(B.lists[li].len);

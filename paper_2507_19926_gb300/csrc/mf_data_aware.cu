@@ -334,12 +334,13 @@ template <class KT, int DT, bool ARG, int NMAX>
 static int d1_launch_n(const ImgArgs &a, int C, const D1Cached *c, int nt, cudaStream_t s) {
     const size_t smem = (size_t)c->plan.smem_elems * sizeof(KT);
     auto kern = d1_kernel<KT, DT, ARG, NMAX>;
-    static bool configured = false;
-    if (!configured) {
+    static DevMask configured;
+    int cfg_dev = 0;
+    if (!dev_configured(configured, &cfg_dev)) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM_BUDGET) !=
             cudaSuccess)
             return MF_ERR_CUDA;
-        configured = true;
+        dev_mark_configured(configured, cfg_dev);
     }
     const int SW = c->plan.B * c->plan.T;
     dim3 grid((a.W + SW - 1) / SW, (a.H + c->plan.TH - 1) / c->plan.TH, C);
@@ -397,12 +398,13 @@ static int d1_persist_n(const ImgArgs *imgs, const int4 *items, int n_items, uns
                         const D1Cached *c, int nt, int blocks_per_sm, int sms, cudaStream_t s, int *grid_out) {
     const size_t smem = (size_t)c->plan.smem_elems * sizeof(KT);
     auto kern = d1_persistent<KT, DT, false, NMAX>;
-    static bool configured = false;
-    if (!configured) {
+    static DevMask configured;
+    int cfg_dev = 0;
+    if (!dev_configured(configured, &cfg_dev)) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM_BUDGET) !=
             cudaSuccess)
             return MF_ERR_CUDA;
-        configured = true;
+        dev_mark_configured(configured, cfg_dev);
     }
     if (n_items == 0) {  // prepare only (see persist_o1)
         int occ = 0;

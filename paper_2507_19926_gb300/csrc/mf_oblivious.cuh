@@ -413,11 +413,12 @@ int persist_o1(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *co
     typedef O1Layout<K, TW, TH, BX, BY, NET::rows_smem> L;
     constexpr size_t smem = o1_smem_bytes<K, TW, TH, BX, BY, DT, KO, ARG, NET>();
     auto kern = o1_persistent<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT, RSORT>;
-    static bool configured = false;
-    if (!configured) {
+    static DevMask configured;
+    int cfg_dev = 0;
+    if (!dev_configured(configured, &cfg_dev)) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return MF_ERR_CUDA;
-        configured = true;
+        dev_mark_configured(configured, cfg_dev);
     }
     // n_items == 0: prepare only (attributes, occupancy -> *grid_out as
     // blocks per SM); call this outside stream capture
@@ -443,8 +444,9 @@ int launch_o1(const ImgArgs &a, int channels, cudaStream_t s) {
     constexpr int P = KO::lanes;
     constexpr size_t smem = o1_smem_bytes<K, TW, TH, BX, BY, DT, KO, ARG, NET>();
     auto kern = o1_kernel<K, TW, TH, BX, BY, DT, KO, ARG, IB, NET, CSORT, RSORT>;
-    static bool configured = false;  // per instantiation; benign race: idempotent
-    if (!configured) {
+    static DevMask configured;
+    int cfg_dev = 0;
+    if (!dev_configured(configured, &cfg_dev)) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return MF_ERR_CUDA;
@@ -457,7 +459,7 @@ int launch_o1(const ImgArgs &a, int channels, cudaStream_t s) {
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
         }
         cudaGetLastError();
-        configured = true;
+        dev_mark_configured(configured, cfg_dev);
     }
     dim3 grid((a.W + P * BX * TW - 1) / (P * BX * TW), (a.H + BY * TH - 1) / (BY * TH), channels);
     kern<<<grid, BX * BY, smem, s>>>(a);

@@ -11,8 +11,14 @@
 // The array holds, in order: one queue counter per kernel class (cleared on
 // every call), the image table, the per-image work records, and the
 // expanded work items that the persistent kernels of the batched path
-// (mf_batch.cu) consume.  Every call reuses the same array, so calls whose
-// work overlaps on the GPU race; calls on one stream are ordered and safe.
+// (mf_batch.cu) consume.  A __device__ array has one instance per device;
+// every call on a device reuses that device's instance, so calls whose work
+// overlaps on the same device race; calls on one stream are ordered and safe.
+//
+// The tables are copied from the caller's stack with cudaMemcpyAsync, so a
+// call made while its stream is being captured into a CUDA graph is
+// rejected: the graph would keep the stack addresses and read dead memory on
+// every replay.
 #include <cstring>
 #include <mutex>
 
@@ -27,6 +33,9 @@ constexpr size_t kOffImgs = 256;                   // after the counters
 constexpr size_t kOffRecs = kOffImgs + (size_t)kStaticMaxImages * sizeof(ImgArgs);
 constexpr size_t kOffItems = (kOffRecs + (size_t)kStaticMaxImages * sizeof(int4) * 2 + 255) & ~(size_t)255;
 constexpr int kStaticMaxItems = (int)((kStaticScratchBytes - kOffItems) / sizeof(int4));
+// The header documents these limits by number; keep the two in step.
+static_assert(sizeof(ImgArgs) == 72, "image table layout changed: update the documented item limit");
+static_assert(kStaticMaxItems == 129392, "the documented work-item limit of mf_batch_run_static is 129,392");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -168,6 +177,18 @@ extern "C" int mf_batch_run_static(const mf_image_desc *descs, int n, mf_stream_
         a.idx_pitch = a.idx_plane = 0;
     }
 
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) {
+        set_error("static batch: cannot query the stream: %s", cudaGetErrorString(e));
+        return MF_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) {
+        set_error("static batch: the stream is being captured; this call copies its tables from the stack "
+                  "and must not be captured into a graph");
+        return MF_ERR_UNSUPPORTED;
+    }
     unsigned char *base = nullptr;
     int rc = static_scratch(&base);
     if (rc) return rc;
@@ -177,10 +198,9 @@ extern "C" int mf_batch_run_static(const mf_image_desc *descs, int n, mf_stream_
         set_error("device attribute: %s", cudaGetErrorString(cudaGetLastError()));
         return MF_ERR_CUDA;
     }
-    cudaStream_t s = (cudaStream_t)stream;
     // tables from the stack (pageable: the copies have consumed them when
     // the calls return), counters cleared on every call
-    cudaError_t e = cudaMemcpyAsync(base + kOffImgs, args, n * sizeof(ImgArgs), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(base + kOffImgs, args, n * sizeof(ImgArgs), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && n_recs)
         e = cudaMemcpyAsync(base + kOffRecs, recs, 2 * n_recs * sizeof(int4), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, kOffImgs, s);

@@ -293,12 +293,13 @@ static D3Cached *d3_get(int k, int dtype, int *err) {
 template <class KT, int DT, int NMAX>
 static int d3_launch_n(const VolArgs &a, int volumes, const D3Cached *c, cudaStream_t s) {
     auto kern = d3_kernel<KT, DT, NMAX>;
-    static bool configured = false;
-    if (!configured) {
+    static DevMask configured;
+    int cfg_dev = 0;
+    if (!dev_configured(configured, &cfg_dev)) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D3_SMEM_BUDGET) !=
             cudaSuccess)
             return MF_ERR_CUDA;
-        configured = true;
+        dev_mark_configured(configured, cfg_dev);
     }
     const int T = c->plan.T;
     const long long tiles = (long long)a.tiles_x * a.tiles_y * ((a.D + T - 1) / T);

@@ -16,7 +16,11 @@ def lib():
 
 
 CASES = [(3, 2), (5, 2), (5, 4), (7, 4), (9, 2), (9, 8), (11, 4), (13, 8), (17, 8), (17, 16),
-         (21, 8), (25, 16), (31, 16), (45, 16), (61, 16), (75, 16), (75, 8), (33, 16)]
+         (21, 8), (25, 16), (31, 16), (45, 16), (61, 16), (75, 16), (75, 8), (33, 16),
+         # the default 16 x 16 root tile at every odd k from 35 to 71 not listed above
+         (35, 16), (37, 16), (39, 16), (41, 16), (43, 16), (47, 16), (49, 16), (51, 16), (53, 16),
+         (55, 16), (57, 16), (59, 16), (63, 16), (65, 16), (67, 16), (69, 16), (71, 16), (73, 16),
+         (39, 8), (55, 8), (71, 8)]
 
 
 @pytest.mark.parametrize("k,T", CASES)

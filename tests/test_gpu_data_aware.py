@@ -10,7 +10,7 @@ from gpu_util import ensure_lib, gpu_filter, same_bits, f32_specials, to_dev, to
 pytestmark = pytest.mark.gpu
 
 DTYPES = ["u8", "u16", "u32", "f32"]
-KS = [3, 5, 7, 9, 11, 13, 15, 17, 19, 21, 23, 25, 27, 29, 31, 33, 37, 41, 45, 49, 53, 57, 61, 65, 69, 73, 75]
+KS = list(range(3, 76, 2))  # every odd k the library accepts above 1
 
 
 @pytest.mark.parametrize("dt", DTYPES)
@@ -23,7 +23,7 @@ def test_value_parity(dt, k):
 
 
 @pytest.mark.parametrize("dt", DTYPES)
-@pytest.mark.parametrize("k", [3, 9, 17, 25, 45, 75])
+@pytest.mark.parametrize("k", [3, 9, 17, 25, 35, 45, 51, 59, 67, 75])
 def test_argmedian_parity(dt, k):
     for j, gen in enumerate((synth.levels16, synth.uniform)):
         x = gen((1, 53, 97), dt, 4000 + 10 * k + j)
@@ -41,7 +41,7 @@ def test_small_and_thin_shapes(dt, shape):
         assert same_bits(gpu_filter(x, k, "data_aware"), oracle.median_filter(x, k)), (dt, shape, k)
 
 
-@pytest.mark.parametrize("k", [5, 21, 63])
+@pytest.mark.parametrize("k", [5, 21, 35, 47, 63, 71])
 def test_f32_special_values(k):
     x = f32_specials((60, 90), 55 + k)
     assert same_bits(gpu_filter(x, k, "data_aware"), oracle.median_filter(x, k))

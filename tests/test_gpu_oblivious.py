@@ -33,7 +33,7 @@ def test_small_and_thin_shapes(dt, shape):
         assert same_bits(gpu_filter(x, k, "oblivious"), oracle.median_filter(x, k)), (dt, shape, k)
 
 
-@pytest.mark.parametrize("k", [3, 7, 11, 17])
+@pytest.mark.parametrize("k", KS)
 def test_f32_special_values(k):
     x = f32_specials((64, 150), 99 + k)
     assert same_bits(gpu_filter(x, k, "oblivious"), oracle.median_filter(x, k))
