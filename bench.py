@@ -147,7 +147,7 @@ def algorithmic_ops_per_px(k):
     return best
 
 
-_O1_NAME = re.compile(r"o1_launch_k(\d+)_(\d+)x(\d+)_b(\d+)x(\d+)_u(m1|\d+)((?:_[a-z]{2})*)_MF_\w+?_Ko(U16x2|U32)")
+_O1_NAME = re.compile(r"o1_launch_k(\d+)_(\d+)x(\d+)_b(\d+)x(\d+)_u(m1|\d+)((?:_[a-z][a-z0-9])*)_MF_\w+?_Ko(U16x2|U32)")
 
 
 def o1_executed_per_px(plan):
@@ -166,11 +166,12 @@ def o1_executed_per_px(plan):
     net = netgen.build(k, tw, th, rows_smem="_rs" in form, lazy="_lz" in form, pressure="_pr" in form)
     ops = len(netgen.fuse3(net).ops)
     cs = len(netgen.column_sort_network(k - th + 1).ops)
-    if "_dr" in form:  # direct form: every thread sorts its own footprint columns
-        per_thread = ops + (tw + k - 1) * cs
+    run = 4 if "_w4" in form else (2 if "_w2" in form else 1)
+    if "_dr" in form:  # direct forms: every thread sorts its own footprint columns
+        per_thread = run * ops + (run * tw + k - 1) * cs
     else:  # block-wide column sort over the block footprint, shared by its threads
         per_thread = ops + by * (bx * tw + k - 1) * cs / (bx * by)
-    return per_thread / (tw * th * lanes)
+    return per_thread / (run * tw * th * lanes)
 
 
 _PROBE = {}

@@ -185,9 +185,8 @@ int mf_batch_describe(const mf_batch_plan *plan, int *kernels, long long *items)
  * until the library is unloaded.  Limits: at most 256 images, k = 1 or a
  * k the data-oblivious kernels are built for (odd 3 to 27), and at most
  * 129,392 work items (one item is one
- * thread block's pixels -- lanes x block width x tile width by block height
- * x tile height, as mf_describe reports them: from 64 x 8 (k = 3, 32-bit
- * data) to 256 x 16 (k = 7, 8/16-bit data)); beyond them it returns
+ * thread block's pixels -- lanes x block width x tile width x run by block
+ * height x tile height, as mf_describe reports them); beyond them it returns
  * MF_ERR_ARG
  * or MF_ERR_UNSUPPORTED with a message, before touching the device.
  * Nothing is allocated (no cudaMalloc, cudaFree or allocating library
@@ -226,7 +225,10 @@ int mf_describe(int H, int W, int channels, mf_dtype dtype, int k, mf_variant va
  * kernels' ALU roofline; no counterpart in the paper).  kind: 0 = u32,
  * 1 = packed u16x2, 2 = f32, 3 = packed f16x2, 4 = u16x2 min interleaved
  * with f16x2 max, 5 = u32 min interleaved with f32 max, 6 = three-input
- * u16x2 min/max, 7 = three-input u32 min/max.  Runs `iters`
+ * u16x2 min/max, 7 = three-input u32 min/max, 8 = four-lane u8 min/max
+ * (__vminu4/__vmaxu4), 9 = warp shuffles, 10 = byte permutes (the last two
+ * are the exchange and packing steps the kernels could use instead of
+ * shared memory).  Runs `iters`
  * iterations of 16 min/max per thread on 4 blocks of 256 threads per SM of
  * the current device (the library allocates and frees its own 8 KB-scale
  * buffers) and writes instructions per second (one per thread-instruction)

@@ -55,12 +55,20 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-r
 # staging dominates: k = 3 (u8 35.6 -> 25.0 us, u32 56.7 -> 35.4 us at
 # 4096^2) and 32-bit keys up to k = 9 (u32 k = 7 180 -> 121 us, k = 9 280 ->
 # 229 us); with packed 8/16-bit keys it ties at k = 5, 7 and spills at 9.
+# The wide direct form (form bits 16/32: 4 or 2 tiles a lane side by side,
+# vector row loads, one byte permute per packed word, vector stores) wins at
+# k = 3 and 5 (4096^2, L2 flushed): u8 k = 3 27.3 -> 21.2 us, f32 k = 3
+# 49.8 -> 41.6 us, u8 k = 5 58.0 -> 41.6 us, u32 k = 5 80.5 -> 68.2 us (two
+# tiles a lane); u32 k = 3 ties the direct form (35.5 us).
 # k = 27: 3.64 ms against 7.62 ms for the best data-aware tile (u32 4096^2),
 # u8 4.03 vs 5.02 ms (one tile a thread on 32-bit keys); at k = 29 the
 # data-aware kernel wins for u8 and the spilling network gains too little
 # for 32-bit keys to pay its compile time.
-O1_VALUE = {3: [(2, 2, 32, 4, -1, 8), (2, 2, 32, 4, -1, 0)],
-            5: [(2, 2, 32, 4, -1, 0, 16), (2, 2, 32, 4, -1, 8, 32), (2, 2, 32, 4, -1, 0, 32)],
+O1_VALUE = {3: [(2, 2, 16, 8, -1, 24), (2, 2, 32, 4, -1, 8), (2, 2, 32, 4, -1, 0), (2, 2, 32, 4, -1, 24),
+                (2, 2, 16, 8, -1, 40)],
+            5: [(2, 2, 16, 8, -1, 24, 16), (2, 2, 16, 8, -1, 40, 32), (2, 2, 32, 4, -1, 0, 16),
+                (2, 2, 32, 4, -1, 8, 32), (2, 2, 32, 4, -1, 0, 32), (2, 2, 16, 8, -1, 40, 16),
+                (2, 2, 16, 8, -1, 24, 32)],
             7: [(4, 4, 32, 4, -1, 0, 16), (4, 4, 32, 4, -1, 8, 32), (4, 4, 32, 4, -1, 0, 32)],
             9: [(4, 4, 16, 8, -1, 6, 16), (4, 4, 32, 4, -1, 8, 32), (4, 4, 32, 4, -1, 0, 32)],
             11: [(4, 4, 16, 8, -1)], 13: [(4, 4, 16, 8, -1)], 15: [(4, 4, 16, 8, -1)],
@@ -135,7 +143,7 @@ def _o1_instances():
                 for dt in (0, 1):
                     out.append((k, tw, th, bx, by, (u, rs), dt, "KoU32", False, 0, ci))
     for k, (tw, th, bx, by, u, rs, keys) in sorted(O1_ARG32.items()):
-        rs &= ~8  # argmedian records run in the shared-memory kernel
+        rs &= ~(8 | 16 | 32)  # argmedian records run in the shared-memory kernel
         out.append((k, tw, th, bx, by, (u, rs), 0, "KoU32", True, 24, 0))
         out.append((k, tw, th, bx, by, (u, rs), 1, "KoU32", True, 16, 0))
     for k, (tw, th, bx, by, u, rs, keys) in sorted(O1_ARG64.items()):
@@ -170,6 +178,7 @@ def generate():
         n_ops = {}
         for tw, th in nets:
             assert not (rsm & 8 and rsm & 1), "the direct kernel takes no shared-memory rows"
+            assert not (rsm & 48) or rsm & 8, "the wide form is a direct form"
             net = netgen.build(k, tw, th, rows_smem=bool(rsm & 1), lazy=bool(rsm & 2), pressure=bool(rsm & 4))
             n_ops[(tw, th)] = netgen.n_minmax(net)
             if O1_FUSE3:
@@ -177,7 +186,8 @@ def generate():
             sync = O1_SYNC_EVERY if O1_SYNC_EVERY and len(net.ops) > 4 * O1_SYNC_EVERY else 0
             u_eff = unroll if O1_ROLLED else -1
             src, _ = codegen.emit_network_auto(net, codegen.net_name(k, tw, th, u_eff, rsm), sync, u_eff,
-                                               direct=bool(rsm & 8), mad_select=O1_MAD_SELECT)
+                                               direct=bool(rsm & 8), mad_select=O1_MAD_SELECT,
+                                               wide=codegen.wide_tiles(rsm))
             parts.append(src)
         for n in sorts:
             parts.append(codegen.emit_colsort(n))
@@ -200,9 +210,9 @@ def generate():
                 decls.append("int %s(const ImgArgs *i, const int4 *w, int n, unsigned *q, int b, int sms, "
                              "cudaStream_t s, int *g);" % pfn)
             decls.append("int %s(const ImgArgs &a, int c, cudaStream_t s);" % fn)
-            entries.append("  {%d, %s, %d, %d, %d, %d, %d, %d, %d, %s, %s, \"%s\"}," %
+            entries.append("  {%d, %s, %d, %d, %d, %d, %d, %d, %d, %d, %s, %s, \"%s\"}," %
                            (k, DT_NAMES[dt], 1 if arg else 0, tw, th, bx, by, 2 if ko == "KoU16x2" else 1,
-                            n_ops[(tw, th)], fn, pfn, fn))
+                            codegen.wide_tiles(rsm), n_ops[(tw, th)], fn, pfn, fn))
         parts.append("}  // namespace mf")
         path = os.path.join(GEN, "o1_k%d_%dx%d_b%dx%d_u%s%s_%s%s_%s.cu" % (
             key[:5] + ("m1" if key[5][0] < 0 else key[5][0], codegen.form_suffix(key[5][1]), key[6],

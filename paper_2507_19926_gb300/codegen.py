@@ -21,7 +21,13 @@ def form_suffix(form):
     bit 1: lazy extra rows/columns, bit 2: pressure-aware order, bit 3: the
     direct kernel -- footprint in registers, no shared memory)."""
     return (("_rs" if form & 1 else "") + ("_lz" if form & 2 else "") + ("_pr" if form & 4 else "") +
-            ("_dr" if form & 8 else ""))
+            ("_dr" if form & 8 else "") + ("_w4" if form & 16 else "") + ("_w2" if form & 32 else ""))
+
+
+def wide_tiles(form):
+    """Root tiles a lane of one thread runs side by side in the wide direct
+    form (form bit 16: 4, bit 32: 2), else 1."""
+    return 4 if form & 16 else (2 if form & 32 else 1)
 
 
 def net_name(k, tw, th, unroll=None, form=0):
@@ -37,7 +43,7 @@ def sort_name(n):
     return "ColSort_%d" % n
 
 
-def emit_network(net, name, sync_every=0, direct=False):
+def emit_network(net, name, sync_every=0, direct=False, wide=1):
     """sync_every > 0 inserts a block barrier after every that many ops: all
     threads of a block run this same branch-free code, so the barrier only
     keeps the block's warps within one window of the (very long) program,
@@ -48,6 +54,8 @@ def emit_network(net, name, sync_every=0, direct=False):
     w("  static constexpr int n_ops = %d;" % netgen.n_minmax(net))
     w("  static constexpr bool rows_smem = %s;" % ("true" if any(d[0] == "row" for d in net.inputs) else "false"))
     w("  static constexpr bool direct = %s;" % ("true" if direct else "false"))
+    if wide > 1:
+        w("  static constexpr int wide = %d;" % wide)
     w("  template <class KO, class L, class OUT>")
     w("  static __device__ __forceinline__ void run(const typename KO::T *__restrict__ cs,")
     w("                                            const typename KO::T *__restrict__ rw,")
@@ -85,7 +93,7 @@ def emit_network(net, name, sync_every=0, direct=False):
     return "\n".join(lines) + "\n"
 
 
-def emit_network_auto(net, name, sync_every=0, unroll_levels=0, direct=False, mad_select=False):
+def emit_network_auto(net, name, sync_every=0, unroll_levels=0, direct=False, mad_select=False, wide=1):
     """The loop-rolled form (rolled.py) when the tree's children pair up,
     else the straight-line form.  unroll_levels < 0 forces straight-line.
     direct: the network runs in the register-footprint kernel, which needs
@@ -98,7 +106,7 @@ def emit_network_auto(net, name, sync_every=0, unroll_levels=0, direct=False, ma
             return rolled.emit(net, ir, name, unroll_levels=unroll_levels, mad_select=mad_select), True
         except rolled.RollError:
             pass
-    return emit_network(net, name, sync_every, direct), False
+    return emit_network(net, name, sync_every, direct, wide), False
 
 
 def emit_colsort(n):

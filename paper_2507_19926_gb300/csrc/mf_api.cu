@@ -461,8 +461,8 @@ int mf_describe(int H, int W, int channels, mf_dtype dtype, int k, mf_variant va
     int rc = resolve(k, dtype, false, variant, &p);
     if (rc) return rc;
     if (p.variant == MF_OBLIVIOUS)
-        snprintf(buf, buflen, "oblivious k=%d tile=%dx%d block=%dx%d net_ops=%d kernel=%s", k, p.o1->tw,
-                 p.o1->th, p.o1->bx, p.o1->by, p.o1->net_ops, p.o1->name);
+        snprintf(buf, buflen, "oblivious k=%d tile=%dx%d block=%dx%d run=%d net_ops=%d kernel=%s", k, p.o1->tw,
+                 p.o1->th, p.o1->bx, p.o1->by, p.o1->run, p.o1->net_ops, p.o1->name);
     else
         d1_describe(k, dtype, false, p.tile, buf, buflen);
     return MF_OK;

@@ -112,7 +112,7 @@ extern "C" int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_
             c.dtype = d.dtype;
             if (var == MF_OBLIVIOUS) {
                 const int lanes = o1->lanes;
-                c.rw = lanes * o1->bx * o1->tw;
+                c.rw = lanes * o1->bx * o1->tw * o1->run;
                 c.rh = o1->by * o1->th;
             } else {
                 int T, B, nt;

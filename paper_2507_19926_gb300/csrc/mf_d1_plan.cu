@@ -43,6 +43,9 @@ static const bool D1_ODD_CHUNKS = !getenv("MF_D1_EVEN_CHUNKS");
 // Phase balancing of the tasks off the critical chain (MF_D1_BALANCE=0
 // keeps every task in its earliest phase).
 static const bool D1_BALANCE = !getenv("MF_D1_BALANCE") || atoi(getenv("MF_D1_BALANCE")) != 0;
+// Split cores grow by shared sorted slabs plus per-node corner blocks
+// (MF_D1_SLABS=0: extra rows and columns extended level by level).
+static const bool D1_SLABS = !getenv("MF_D1_SLABS") || atoi(getenv("MF_D1_SLABS")) != 0;
 
 static void chunk_rule(int key_bytes, int *min_chunk, int *div) {
     *min_chunk = key_bytes <= 2 ? 16 : 12;
@@ -224,6 +227,75 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
     int d = lo;
     // per level state
     std::vector<std::vector<Ref>> core(1, std::vector<Ref>(1, B.multiway(cc, lo, hi)));  // [j][i]
+    if (D1_SLABS) {
+        // A child's core is its parent's core plus the h new columns (rows)
+        // over the parent's core rows (columns).  Those split into the part
+        // over the root core's rows (columns) -- the same for every node of
+        // a node column (row), sorted once from the sorted column segments
+        // (root extra rows) and shared -- and a small block over the node's
+        // own extra rows (columns).  Sorted rectangles are memoised, so no
+        // extra row or column is ever carried and re-merged level by level.
+        std::map<std::tuple<int, int, int, int>, Ref> memo;
+        auto rect = [&](int y0r, int y1r, int x0r, int x1r) -> Ref {
+            if (y1r < y0r || x1r < x0r) return Ref{-2, 0, 0};
+            const auto key = std::make_tuple(y0r, y1r, x0r, x1r);
+            auto it = memo.find(key);
+            if (it != memo.end()) return it->second;
+            std::vector<Ref> parts;
+            if (y0r == TH - 1 && y1r == kh - 1) {
+                for (int fx = x0r; fx <= x1r; fx++) parts.push_back(col0.at(fx));
+            } else if (x0r == TW - 1 && x1r == kw - 1) {
+                for (int fy = y0r; fy <= y1r; fy++) parts.push_back(row0.at(fy));
+            } else if (x1r - x0r >= y1r - y0r) {
+                for (int fy = y0r; fy <= y1r; fy++) parts.push_back(B.sort_gather(F(fy, x0r), 1, x1r - x0r + 1));
+            } else {
+                for (int fx = x0r; fx <= x1r; fx++) parts.push_back(B.sort_gather(F(y0r, fx), FW, y1r - y0r + 1));
+            }
+            const Ref r = B.multiway(parts, 0, 1 << 30);
+            memo[key] = r;
+            return r;
+        };
+        while (tw * th > 1) {
+            const int NX = TW / tw, NY = TH / th;
+            const bool horiz = tw >= th;
+            const int h = (horiz ? tw : th) / 2;
+            const int cw = kw - (horiz ? h : tw) + 1, ch = kh - (horiz ? th : h) + 1;
+            c = cw * ch;
+            const int K = core[0][0].len;
+            const int n_held = K + h * (horiz ? kh - th + 1 : kw - tw + 1);
+            keep_range(n_win, c, d, n_held, &lo, &hi);
+            std::vector<std::vector<Ref>> ncore(horiz ? NY : 2 * NY, std::vector<Ref>(horiz ? 2 * NX : NX));
+            for (int j = 0; j < NY; j++)
+                for (int i = 0; i < NX; i++) {
+                    const int x0n = i * tw, y0n = j * th;
+                    for (int s2 = 0; s2 < 2; s2++) {
+                        std::vector<Ref> parts;
+                        if (horiz) {
+                            const int q0 = s2 == 0 ? x0n + h - 1 : x0n + kw, q1 = q0 + h - 1;
+                            parts.push_back(rect(TH - 1, kh - 1, q0, q1));
+                            parts.push_back(rect(y0n + th - 1, TH - 2, q0, q1));
+                            parts.push_back(rect(kh, y0n + kh - 1, q0, q1));
+                        } else {
+                            const int r0 = s2 == 0 ? y0n + h - 1 : y0n + kh, r1 = r0 + h - 1;
+                            parts.push_back(rect(r0, r1, TW - 1, kw - 1));
+                            parts.push_back(rect(r0, r1, x0n + tw - 1, TW - 2));
+                            parts.push_back(rect(r0, r1, kw, x0n + kw - 1));
+                        }
+                        const Ref extra = B.multiway(parts, 0, 1 << 30);
+                        const Ref nc = B.merge_range(core[j][i], extra, lo, hi);
+                        if (horiz) ncore[j][2 * i + s2] = nc;
+                        else ncore[2 * j + s2][i] = nc;
+                    }
+                }
+            core.swap(ncore);
+            if (horiz) tw = h;
+            else th = h;
+            d += lo;
+        }
+        for (int j = 0; j < TH; j++)
+            for (int i = 0; i < TW; i++) outs[j * NB * TW + bx + i] = core[j][i];
+        continue;
+    }
     std::vector<std::map<int, Ref>> rows(1, row0);  // [i][fy]
     std::vector<std::map<int, Ref>> cols(1);        // [j][fx]
     for (auto &kv : col0)

@@ -29,6 +29,8 @@
 // footprint column tx*TW + fx at base + tx + const, so a warp's 32 lanes
 // hit 32 consecutive words (no bank conflicts) for every network input.
 #pragma once
+#include <type_traits>
+
 #include "mf_common.cuh"
 
 namespace mf {
@@ -258,13 +260,230 @@ __device__ __forceinline__ void o1_block_direct(const ImgArgs &a, int bxi, int b
     }
 }
 
+// ------------------------------------------------------- wide direct form
+// Tiles of a lane per thread (NTX) for networks emitted in the wide form
+// (NET::wide), 1 otherwise.
+template <class N, class = void>
+struct NetWide {
+    static constexpr int v = 1;
+};
+template <class N>
+struct NetWide<N, std::void_t<decltype(N::wide)>> {
+    static constexpr int v = N::wide;
+};
+
+// Footprint of a lane's run of tiles in registers: FWL columns, the sorted
+// column segments CH0 long.
+template <int FWL, int CH0>
+struct O1RunLayout {
+    static __host__ __device__ constexpr int px(int fy, int fx) { return fy * FWL + fx; }
+    static __host__ __device__ constexpr int col(int fx, int i) { return fx * CH0 + i; }
+    static __host__ __device__ constexpr int row(int, int) { return 0; }
+};
+
+// Row buffer of the wide form: HB + RUN*P + HB elements of one footprint
+// row, starting HB elements left of the run, as 32-bit words.
+template <class E, int NE>
+struct O1RowBuf {
+    static constexpr int WORDS = NE * (int)sizeof(E) / 4;
+    uint32_t w[WORDS];
+    // element i (compile-time i) as a raw value
+    __device__ __forceinline__ uint32_t elem(int i) const {
+        if (sizeof(E) == 1) return (w[i >> 2] >> (8 * (i & 3))) & 0xffu;
+        if (sizeof(E) == 2) return (w[i >> 1] >> (16 * (i & 1))) & 0xffffu;
+        return w[i];
+    }
+};
+
+// Comparison word of the two lanes' elements i0 and i1 of a row buffer.
+// 8-bit data: each 16-bit lane holds v * 257 (the byte in both halves of
+// the lane: one byte permute builds both lanes, and v -> 257 v keeps the
+// order and is one to one).  16-bit data: the two elements' halves.
+// 32-bit data (one lane): the order key.
+template <int DT, class KO, class BUF>
+__device__ __forceinline__ typename KO::T o1_pack(const BUF &b, int i0, int i1) {
+    typedef typename Dt<DT>::E E;
+    if constexpr (KO::lanes == 2 && sizeof(E) == 1) {
+        const int a = i0 & 3, c = i1 & 3;
+        return __byte_perm(b.w[i0 >> 2], b.w[i1 >> 2], (unsigned)(a | a << 4 | (4 + c) << 8 | (4 + c) << 12));
+    } else if constexpr (KO::lanes == 2) {
+        const int a = 2 * (i0 & 1), c = 4 + 2 * (i1 & 1);
+        return __byte_perm(b.w[i0 >> 1], b.w[i1 >> 1], (unsigned)(a | (a + 1) << 4 | c << 8 | (c + 1) << 12));
+    } else {
+        return (typename KO::T)Dt<DT>::key((typename Dt<DT>::E)b.elem(i0));
+    }
+}
+
+// Wide direct form for small k: each thread owns NTX horizontally adjacent
+// root tiles per lane, the lanes side by side (lane 1's tiles start RUN =
+// NTX*TW columns after lane 0's), i.e. one contiguous run of P*RUN columns
+// by TH rows.  Where the run and its halo lie inside the image, every
+// footprint row is read with vector loads of up to 16 bytes;
+// the two lanes' elements are packed with one byte permute per word; the
+// NTX tiles of a lane share their sorted footprint columns (Sec. 3.3); the
+// medians go out as vector stores.  Near the borders the same row buffers
+// are filled by clamped element loads and the medians stored one by one.
+template <int K, int TW, int TH, int BX, int BY, int DT, class KO, class NET, class CSORT, int NTX>
+__device__ __forceinline__ void o1_block_wide(const ImgArgs &a, int bxi, int byi, int z) {
+    typedef typename KO::T T;
+    typedef typename Dt<DT>::E E;
+    constexpr int P = KO::lanes, R = (K - 1) / 2;
+    constexpr int RUN = NTX * TW, TOT = P * RUN;
+    constexpr int HB = 16 / (int)sizeof(E) < 4 ? 16 / (int)sizeof(E) : 4;  // halo elements each side (>= R)
+    constexpr int NE = TOT + 2 * HB;
+    constexpr int FWL = RUN + K - 1, FH = TH + K - 1, CH0 = K - TH + 1;
+    static_assert(R <= HB, "halo wider than the row buffer");
+    static_assert(P == 1 || RUN % (sizeof(E) == 1 ? 4 : 2) == 0, "lane runs of whole output words");
+    static_assert((TOT * (int)sizeof(E)) % 4 == 0 && (HB * (int)sizeof(E)) % 4 == 0, "vector geometry");
+    typedef O1RunLayout<FWL, CH0> RL;
+    const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
+    const int x0 = bxi * (BX * TOT) + tx * TOT;
+    const int y0 = byi * (BY * TH) + ty * TH;
+    if (x0 >= a.W || y0 >= a.H) return;
+    const char *src = a.src + (size_t)z * a.plane;
+    // vector loads need the run and its halo inside the row and 16-byte
+    // aligned rows (x0 * sizeof(E) is a multiple of 16 by construction)
+    const bool vec = x0 - HB >= 0 && x0 + TOT + HB <= a.W && ((a.pitch | (size_t)src) & 15) == 0;
+    T f[FH * FWL];
+#pragma unroll
+    for (int fy = 0; fy < FH; fy++) {
+        const int y = clampi(y0 - R + fy, a.y_lo, a.y_hi);
+        const E *row = reinterpret_cast<const E *>(src + (ptrdiff_t)y * (ptrdiff_t)a.pitch);
+        O1RowBuf<E, NE> b;
+        constexpr int HW = HB * (int)sizeof(E) / 4;   // halo words each side
+        constexpr int MW = TOT * (int)sizeof(E) / 4;  // run words
+        if (vec) {
+            const uint32_t *wr = reinterpret_cast<const uint32_t *>(row + x0);
+            if constexpr (HW == 1) {
+                b.w[0] = __ldg(wr - 1);
+                b.w[HW + MW] = __ldg(wr + MW);
+            } else if constexpr (HW == 2) {
+                const uint2 l = __ldg(reinterpret_cast<const uint2 *>(wr) - 1);
+                const uint2 r = __ldg(reinterpret_cast<const uint2 *>(wr + MW));
+                b.w[0] = l.x; b.w[1] = l.y; b.w[HW + MW] = r.x; b.w[HW + MW + 1] = r.y;
+            } else {
+                const uint4 l = __ldg(reinterpret_cast<const uint4 *>(wr) - 1);
+                const uint4 r = __ldg(reinterpret_cast<const uint4 *>(wr + MW));
+                b.w[0] = l.x; b.w[1] = l.y; b.w[2] = l.z; b.w[3] = l.w;
+                b.w[HW + MW] = r.x; b.w[HW + MW + 1] = r.y; b.w[HW + MW + 2] = r.z; b.w[HW + MW + 3] = r.w;
+            }
+            if constexpr (MW % 4 == 0) {
+#pragma unroll
+                for (int m = 0; m < MW / 4; m++) {
+                    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(wr) + m);
+                    b.w[HW + 4 * m] = v.x; b.w[HW + 4 * m + 1] = v.y; b.w[HW + 4 * m + 2] = v.z; b.w[HW + 4 * m + 3] = v.w;
+                }
+            } else if constexpr (MW % 2 == 0) {
+#pragma unroll
+                for (int m = 0; m < MW / 2; m++) {
+                    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(wr) + m);
+                    b.w[HW + 2 * m] = v.x; b.w[HW + 2 * m + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < MW; m++) b.w[HW + m] = __ldg(wr + m);
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < b.WORDS; m++) b.w[m] = 0;
+#pragma unroll
+            for (int i = 0; i < NE; i++) {
+                if (i < HB - R || i >= HB + TOT + R) continue;  // never read
+                const uint32_t v = (uint32_t)__ldg(row + clampi(x0 - HB + i, 0, a.W - 1));
+                b.w[i * (int)sizeof(E) / 4] |= v << (8 * ((i * (int)sizeof(E)) & 3));
+            }
+        }
+#pragma unroll
+        for (int fx = 0; fx < FWL; fx++) f[RL::px(fy, fx)] = o1_pack<DT, KO>(b, HB - R + fx, HB - R + fx + RUN);
+    }
+    // the lane's footprint columns over the root core rows, shared by its NTX tiles
+    T cs[FWL * CH0];
+#pragma unroll
+    for (int fx = 0; fx < FWL; fx++) {
+        T v[CH0];
+#pragma unroll
+        for (int i = 0; i < CH0; i++) v[i] = f[RL::px(TH - 1 + i, fx)];
+        CSORT::template run<KO>(v);
+#pragma unroll
+        for (int i = 0; i < CH0; i++) cs[RL::col(fx, i)] = v[i];
+    }
+    T res[NTX * TW * TH];
+#pragma unroll
+    for (int q = 0; q < NTX; q++) {
+        O1Collect<T, TW * TH> out{res + q * TW * TH};
+        NET::template run<KO, RL>(cs + q * TW * CH0, f + q * TW, f + q * TW, out);
+    }
+    // medians out: output column c of row py is lane c / RUN, tile (c % RUN) / TW
+    char *dst = a.dst + (size_t)z * a.plane;
+    const bool vst = x0 + TOT <= a.W && ((a.pitch | (size_t)dst) & 15) == 0;
+#pragma unroll
+    for (int py = 0; py < TH; py++) {
+        const int y = y0 + py;
+        if (y >= a.H) break;
+        E *orow = reinterpret_cast<E *>(dst + (size_t)y * a.pitch) + x0;
+        auto med = [&](int c) -> uint32_t {  // median key of output column c (compile-time c)
+            const int l = c / RUN, cc = c % RUN;
+            const T w = res[(cc / TW) * TW * TH + py * TW + cc % TW];
+            return P == 2 ? (uint32_t)((w >> (16 * l)) & 0xffffu) : (uint32_t)w;
+        };
+        if (vst) {
+            constexpr int OW = TOT * (int)sizeof(E) / 4;  // output words
+            uint32_t o[OW];
+            // the packed median of lane-0 column cc (both lanes in one word)
+            auto rw = [&](int cc) -> uint32_t { return (uint32_t)res[(cc / TW) * TW * TH + py * TW + cc % TW]; };
+            if constexpr (sizeof(E) == 1) {
+                // lanes hold 257 v, so bytes 0 and 2 of a packed word are the
+                // two lanes' values: two permutes gather four columns of
+                // both lanes, two more make the lane-0 and lane-1 words
+#pragma unroll
+                for (int m = 0; m < RUN / 4; m++) {
+                    const uint32_t t01 = __byte_perm(rw(4 * m), rw(4 * m + 1), 0x6240);
+                    const uint32_t t23 = __byte_perm(rw(4 * m + 2), rw(4 * m + 3), 0x6240);
+                    o[m] = __byte_perm(t01, t23, 0x5410);
+                    o[RUN / 4 + m] = __byte_perm(t01, t23, 0x7632);
+                }
+            } else if constexpr (sizeof(E) == 2) {
+#pragma unroll
+                for (int m = 0; m < RUN / 2; m++) {
+                    o[m] = __byte_perm(rw(2 * m), rw(2 * m + 1), 0x5410);
+                    o[RUN / 2 + m] = __byte_perm(rw(2 * m), rw(2 * m + 1), 0x7632);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < OW; m++) o[m] = Dt<DT>::val(med(m));
+            }
+            if constexpr (OW % 4 == 0) {
+#pragma unroll
+                for (int m = 0; m < OW / 4; m++)
+                    reinterpret_cast<uint4 *>(orow)[m] = make_uint4(o[4 * m], o[4 * m + 1], o[4 * m + 2], o[4 * m + 3]);
+            } else if constexpr (OW % 2 == 0) {
+#pragma unroll
+                for (int m = 0; m < OW / 2; m++) reinterpret_cast<uint2 *>(orow)[m] = make_uint2(o[2 * m], o[2 * m + 1]);
+            } else {
+#pragma unroll
+                for (int m = 0; m < OW; m++) reinterpret_cast<uint32_t *>(orow)[m] = o[m];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < TOT; c++) {
+                if (x0 + c >= a.W) break;
+                const uint32_t kv = med(c);
+                orow[c] = sizeof(E) == 1 ? (E)(kv & 0xffu) : Dt<DT>::val(kv);
+            }
+        }
+    }
+}
+
 // One block's work: the block of tiles at (bxi, byi) of plane z.
 template <int K, int TW, int TH, int BX, int BY, int DT, class KO, bool ARG, int IB, class NET,
           class CSORT, class RSORT>
 __device__ __forceinline__ void o1_block(const ImgArgs &a, int bxi, int byi, int z) {
     if constexpr (NET::direct) {
         static_assert(!ARG, "the direct form computes values only");
-        o1_block_direct<K, TW, TH, BX, BY, DT, KO, NET, CSORT>(a, bxi, byi, z);
+        if constexpr (NetWide<NET>::v > 1)
+            o1_block_wide<K, TW, TH, BX, BY, DT, KO, NET, CSORT, NetWide<NET>::v>(a, bxi, byi, z);
+        else
+            o1_block_direct<K, TW, TH, BX, BY, DT, KO, NET, CSORT>(a, bxi, byi, z);
         return;
     }
     typedef O1Layout<K, TW, TH, BX, BY, NET::rows_smem> L;
@@ -461,7 +680,8 @@ int launch_o1(const ImgArgs &a, int channels, cudaStream_t s) {
         cudaGetLastError();
         dev_mark_configured(configured, cfg_dev);
     }
-    dim3 grid((a.W + P * BX * TW - 1) / (P * BX * TW), (a.H + BY * TH - 1) / (BY * TH), channels);
+    constexpr int RW = P * BX * TW * NetWide<NET>::v;  // columns of a block's region
+    dim3 grid((a.W + RW - 1) / RW, (a.H + BY * TH - 1) / (BY * TH), channels);
     kern<<<grid, BX * BY, smem, s>>>(a);
     count_launch();
     return cudaPeekAtLastError() == cudaSuccess ? MF_OK : MF_ERR_CUDA;

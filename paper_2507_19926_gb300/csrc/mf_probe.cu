@@ -17,6 +17,9 @@ __device__ __forceinline__ uint32_t pmin(uint32_t a, uint32_t b) {
     if (KIND == 3) asm("min.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     if (KIND == 4) asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     if (KIND == 5) asm("min.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    if (KIND == 8) d = __vminu4(a, b);                        // four 8-bit lanes
+    if (KIND == 9) d = __shfl_sync(0xffffffffu, a, b & 31u);  // register exchange across lanes
+    if (KIND == 10) d = __byte_perm(a, b, 0x5140);            // byte permute (lane packing)
     return d;
 }
 template <int KIND>
@@ -28,6 +31,9 @@ __device__ __forceinline__ uint32_t pmax(uint32_t a, uint32_t b) {
     if (KIND == 3) asm("max.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     if (KIND == 4) asm("max.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     if (KIND == 5) d = __float_as_uint(fmaxf(__uint_as_float(a), __uint_as_float(b)));
+    if (KIND == 8) d = __vmaxu4(a, b);
+    if (KIND == 9) d = __shfl_xor_sync(0xffffffffu, a ^ b, 1);
+    if (KIND == 10) d = __byte_perm(a, b, 0x7362);
     return d;
 }
 
@@ -93,11 +99,14 @@ using namespace mf;
 
 // kind: 0 u32 min/max, 1 u16x2 min/max, 2 f32 min/max, 3 f16x2 min/max,
 // 4 u16x2 min interleaved with f16x2 max, 5 u32 min interleaved with f32 max,
-// 6 three-input u16x2 min/max, 7 three-input u32 min/max.
-// Writes min/max instructions per second (per warp-lane instruction) and
-// the elapsed milliseconds; buffers are allocated and freed here.
+// 6 three-input u16x2 min/max, 7 three-input u32 min/max, 8 four-lane u8
+// min/max (__vminu4/__vmaxu4), 9 warp shuffles (an index and an xor
+// shuffle a pair; the xor one carries one extra logic op), 10 byte
+// permutes.  Writes operations per second (per warp-lane operation: one
+// call of the min/max, shuffle or permute) and the elapsed milliseconds;
+// buffers are allocated and freed here.
 extern "C" int mf_probe_minmax(int kind, int iters, double *instr_per_s, double *ms_out) {
-    if (kind < 0 || kind > 7 || iters < 1 || !instr_per_s) { set_error("bad probe arguments"); return MF_ERR_ARG; }
+    if (kind < 0 || kind > 10 || iters < 1 || !instr_per_s) { set_error("bad probe arguments"); return MF_ERR_ARG; }
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -113,7 +122,8 @@ extern "C" int mf_probe_minmax(int kind, int iters, double *instr_per_s, double 
     void (*kern)(const uint32_t *, uint32_t *, int) =
         kind == 0 ? probe_kernel<0> : kind == 1 ? probe_kernel<1> : kind == 2 ? probe_kernel<2>
         : kind == 3 ? probe_kernel<3> : kind == 4 ? probe_kernel<4> : kind == 5 ? probe_kernel<5>
-        : kind == 6 ? probe3_kernel<6> : probe3_kernel<7>;
+        : kind == 6 ? probe3_kernel<6> : kind == 7 ? probe3_kernel<7> : kind == 8 ? probe_kernel<8>
+        : kind == 9 ? probe_kernel<9> : probe_kernel<10>;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -17,6 +17,7 @@ struct O1Entry {
     int tw, th;     // root tile
     int bx, by;     // threads per block (x, y)
     int lanes;      // root tiles a thread (2: two 16-bit keys a register)
+    int run;        // root tiles of a lane side by side along x (wide direct form), else 1
     int net_ops;    // min/max ops of one root tile's network (excl. column sort)
     ImgLaunchFn launch;
     PersistFn persist;

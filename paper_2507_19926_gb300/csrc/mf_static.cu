@@ -147,7 +147,7 @@ extern "C" int mf_batch_run_static(const mf_image_desc *descs, int n, mf_stream_
             if (img_cls[i] != c) continue;
             const mf_image_desc &d = descs[i];
             const int lanes = o1->lanes;
-            const int rw = lanes * o1->bx * o1->tw, rh = o1->by * o1->th;
+            const int rw = lanes * o1->bx * o1->tw * o1->run, rh = o1->by * o1->th;
             const int gx = (d.W + rw - 1) / rw, gy = (d.H + rh - 1) / rh;
             const long long cnt = (long long)gx * gy * d.channels;
             if (n_items + cnt > kStaticMaxItems) {

@@ -78,17 +78,18 @@ def test_static_batch_rejects_what_it_cannot_hold():
 def test_static_batch_item_limit_is_exact():
     """Exactly the documented number of work items runs; one more is
     rejected before the device is touched.  One item is one thread block's
-    pixels (lanes x block width x tile width by block height x tile height,
-    read from mf_describe), so a plane of 4 x 4 blocks is 16 items."""
+    pixels (lanes x block width x tile width x tiles a lane runs, by block
+    height x tile height, read from mf_describe), so a plane of 4 x 4 blocks
+    is 16 items."""
     import re
     import torch
     ensure_lib()
     desc = mf.mf_describe(64, 64, 1, mf.MF_U8, 3)
-    m = re.search(r"oblivious k=3 tile=(\d+)x(\d+) block=(\d+)x(\d+) .*kernel=\S*_Ko(U16x2|U32)", desc)
+    m = re.search(r"oblivious k=3 tile=(\d+)x(\d+) block=(\d+)x(\d+) run=(\d+) .*kernel=\S*_Ko(U16x2|U32)", desc)
     assert m, desc
-    tw, th, bx, by = (int(v) for v in m.groups()[:4])
-    lanes = 2 if m.group(5) == "U16x2" else 1
-    rw, rh = lanes * bx * tw, by * th
+    tw, th, bx, by, run = (int(v) for v in m.groups()[:5])
+    lanes = 2 if m.group(6) == "U16x2" else 1
+    rw, rh = lanes * bx * tw * run, by * th
     W, H = 4 * rw, 4 * rh
     planes = MAX_ITEMS // 16
     assert planes * 16 == MAX_ITEMS
