@@ -40,12 +40,29 @@ namespace mf {
 // (min 16, div 2), wider keys with (min 12, div 1).  MF_D1_CHUNK="min:div"
 // overrides both (tuning sweeps).
 static const bool D1_ODD_CHUNKS = !getenv("MF_D1_EVEN_CHUNKS");
-// Phase balancing of the tasks off the critical chain (MF_D1_BALANCE=0
-// keeps every task in its earliest phase).
-static const bool D1_BALANCE = !getenv("MF_D1_BALANCE") || atoi(getenv("MF_D1_BALANCE")) != 0;
-// Split cores grow by shared sorted slabs plus per-node corner blocks
-// (MF_D1_SLABS=0: extra rows and columns extended level by level).
-static const bool D1_SLABS = !getenv("MF_D1_SLABS") || atoi(getenv("MF_D1_SLABS")) != 0;
+// Phase balancing of the tasks off the critical chain.  It shortens list
+// lifetimes (less shared memory: more blocks a SM where the state limits
+// them) at the price of phases that mix sorts and merges.  Measured on
+// 4096^2 images it pays for 4-byte keys from k = 41 (u32 k = 75 46.9 ->
+// 35.9 ms, k = 45 13.6 -> 12.8 ms) and for 2-byte keys from k = 61 (u8 k = 75
+// 20.3 -> 19.3 ms) and costs up to 12% below; volumes gain nothing.
+// MF_D1_BALANCE=0/1 forces it off/on for every plan.
+static int d1_balance_env() {
+    const char *e = getenv("MF_D1_BALANCE");
+    return e ? (atoi(e) != 0) : -1;
+}
+static bool d1_balance(int n_win, int key_bytes, bool volume) {
+    static const int forced = d1_balance_env();
+    if (forced >= 0) return forced != 0;
+    if (volume) return false;
+    return key_bytes >= 4 ? n_win >= 41 * 41 : n_win >= 61 * 61;
+}
+// Split cores grown from shared sorted slabs plus per-node corner blocks
+// instead of extra rows and columns extended level by level
+// (MF_D1_SLABS=1).  12% fewer merged elements at k = 45 but three times the
+// small sorts; measured slower (u8 k = 61 14.0 -> 17.5 ms, u32 k = 31 8.6 ->
+// 10.4 ms), so off by default.
+static const bool D1_SLABS = getenv("MF_D1_SLABS") && atoi(getenv("MF_D1_SLABS")) != 0;
 
 static void chunk_rule(int key_bytes, int *min_chunk, int *div) {
     *min_chunk = key_bytes <= 2 ? 16 : 12;
@@ -186,7 +203,8 @@ static void keep_range(int n, int c, int d, int n_held, int *lo, int *hi) {
 
 }  // namespace
 
-static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int nt, int key_bytes, D1Plan *plan);
+static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int nt, int key_bytes, D1Plan *plan,
+                        bool balance);
 
 bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, int kh, int TH) {
     // k: window width (columns), kh: window height (rows); root tile T
@@ -377,14 +395,15 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
     plan->FH = FH;
     plan->FD = 1;
     plan->TD = 1;
-    return finish_plan(B, outs, FW * FH, nt, key_bytes, plan);
+    return finish_plan(B, outs, FW * FH, nt, key_bytes, plan, d1_balance(n_win, key_bytes, false));
 }
 
 // Liveness, phases, shared-memory allocation and the emitted task list of a
 // built tree (outs: the list holding each output's median, in output order;
 // the footprint occupies the first `base` elements).  The geometry fields of
 // `plan` are set by the caller.
-static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int nt, int key_bytes, D1Plan *plan) {
+static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int nt, int key_bytes, D1Plan *plan,
+                        bool balance) {
     // ---------------------------------------------------------- liveness
     for (const Ref &r : outs) {
         if (r.len != 1) return false;
@@ -422,7 +441,7 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
     // wait for the slowest one at every barrier) and produces lists closer
     // to where they are read, which shortens their lifetimes in shared
     // memory.
-    if (D1_BALANCE && nph > 1) {
+    if (balance && nph > 1) {
         std::vector<std::vector<int>> readers(B.lists.size());
         for (size_t ti = 0; ti < B.tasks.size(); ti++) {
             if (!keep[ti]) continue;
@@ -571,7 +590,7 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
     };
     for (int p = 0; p <= nph; p++) {
         // the footprint is free once its last reader has run
-        if (D1_BALANCE && p == foot_last + 1 && base > 0) release(0, base);
+        if (balance && p == foot_last + 1 && base > 0) release(0, base);
         for (int li : dies[p]) release(B.lists[li].off, B.lists[li].len);
         if (p < nph)
             for (int li : prod[p]) B.lists[li].off = alloc(B.lists[li].len);
@@ -837,7 +856,7 @@ bool d3_build_plan(int k, int T, D1Plan *plan, int nt, int key_bytes, int NB) {
     plan->FW = F;   // x lines are F elements apart
     plan->FH = F;
     plan->FD = FX;  // FW * FH * FD: the footprint's element count
-    return finish_plan(B, outs, F * F * FX, nt, key_bytes, plan);
+    return finish_plan(B, outs, F * F * FX, nt, key_bytes, plan, d1_balance((int)n_win, key_bytes, true));
 }
 
 void d1_pack_tasks(const D1Plan &plan, std::vector<D1Packed> *out) {

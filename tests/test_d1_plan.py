@@ -116,3 +116,33 @@ def test_rect_plan_rejects_tiles_beyond_the_short_side():
         mf.mf_d1_plan_check(9, 4, kh=3)
     with pytest.raises(mf.MedianFilterError):
         mf.mf_d1_plan_check(1, 2, kh=9)
+
+
+def test_slab_form_plans_match_oracle():
+    """The slab form of the split cores (environment MF_D1_SLABS=1, read when
+    the library loads: new cores grow from shared sorted strips plus
+    per-node corner blocks) plans the same filter; checked in a fresh
+    process, with and without phase balancing."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = """
+import numpy as np, oracle, paper_2507_19926_gb300 as mf
+from paper_2507_19926_gb300 import synth
+mf.load_library()
+for k, T, B in [(5, 2, 1), (9, 4, 2), (17, 8, 1), (31, 16, 1), (45, 16, 1)]:
+    for s in range(2):
+        gen = synth.levels16 if s else synth.uniform
+        FH, FW = T + k - 1, B * T + k - 1
+        img = gen((FH, FW), "u16", 5 * k + T + s)
+        st, med = mf.mf_d1_plan_check(k, T, img.astype(np.uint64).ravel(), strip=B)
+        r = k // 2
+        want = oracle.median_filter(img, k)[r:r + T, r:r + B * T].ravel()
+        assert np.array_equal(med.astype(np.uint16), want), (k, T, B, s)
+print("ok")
+"""
+    for bal in ("0", "1"):
+        env = dict(os.environ, MF_D1_SLABS="1", MF_D1_BALANCE=bal, PYTHONPATH=root)
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=root)
+        assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
