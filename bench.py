@@ -355,27 +355,42 @@ def bench_batched(dev, stream, flush, reps=5):
         descs.append(mf.ImageDesc(x.data_ptr(), y.data_ptr(), d["H"], d["W"], d["W"] * x.element_size(), 1,
                                   codes[d["dtype"]], d["k"]))
         px += d["H"] * d["W"]
-    plan = mf.mf_batch_plan_create(descs)
     sptr = stream.cuda_stream
-    try:
-        kernels, items = mf.mf_batch_describe(plan)
-        run = lambda: mf.mf_batch_run(plan, sptr)
-        for _ in range(2):
-            run()
-        t_batch = _time_ms(run, stream, reps, flush)
 
-        def plain():
-            for x, y, d in bufs:
-                mf.mf_median_filter(x.data_ptr(), y.data_ptr(), d["H"], d["W"], d["W"] * x.element_size(), 1,
-                                    codes[d["dtype"]], d["k"], mf.MF_BORDER_CLAMP, sptr)
+    def plain():
+        for x, y, d in bufs:
+            mf.mf_median_filter(x.data_ptr(), y.data_ptr(), d["H"], d["W"], d["W"] * x.element_size(), 1,
+                                codes[d["dtype"]], d["k"], mf.MF_BORDER_CLAMP, sptr)
+
+    def measure(plan):
+        try:
+            kernels, items = mf.mf_batch_describe(plan)
+            run = lambda: mf.mf_batch_run(plan, sptr)
+            for _ in range(2):
+                run()
+            t_batch = _time_ms(run, stream, reps, flush)
+        finally:
+            mf.mf_batch_plan_destroy(plan)
         plain()
         t_plain = _time_ms(plain, stream, reps, flush)
-    finally:
-        mf.mf_batch_plan_destroy(plan)
+        return kernels, items, t_batch, t_plain
+
+    # default kernels (no tuning entries yet), then a plan that autotunes
+    # every (k, dtype, size bucket) of the batch first; plain launches
+    # after it use the same tuning table
+    kernels, items, t_batch, t_plain = measure(mf.mf_batch_plan_create(descs))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tuned = mf.mf_batch_plan_create_ex(descs, 1)
+    tune_s = time.perf_counter() - t0
+    tk, ti, tt_batch, tt_plain = measure(tuned)
     return {"workload": "64 images, log-uniform 256x256..4096x3072, u8/u16/f32, odd k 3..31",
             "pixels": px, "graph_kernels": kernels, "work_items": items,
             "batched_ms": t_batch, "plain_ms": t_plain, "batched_mpix_s": px / t_batch / 1e3,
-            "plain_mpix_s": px / t_plain / 1e3, "speedup": t_plain / t_batch}
+            "plain_mpix_s": px / t_plain / 1e3, "speedup": t_plain / t_batch,
+            "tuned": {"tuning_s": tune_s, "graph_kernels": tk, "work_items": ti, "batched_ms": tt_batch,
+                      "plain_ms": tt_plain, "batched_mpix_s": px / tt_batch / 1e3, "speedup": tt_plain / tt_batch,
+                      "vs_untuned_batch": t_batch / tt_batch}}
 
 
 def bench_small(dev, stream, n_graph=200, reps=20):

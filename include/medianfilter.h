@@ -168,6 +168,16 @@ typedef struct mf_batch_plan mf_batch_plan;
  * buffers they point to must stay valid while the plan is run.  Must be
  * called outside any stream capture. */
 int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_plan **out);
+/* As mf_batch_plan_create; with tune != 0 every (k, dtype, image-size
+ * bucket) of the batch that the tuning table has no entry for is first
+ * autotuned (mf_autotune) on the largest image of that group -- on its own
+ * buffers, so those images' dst are written during planning -- and the
+ * images are then grouped by the kernel each one's bucket selects
+ * (variant, network configuration or data-aware root tile).  The paper picks
+ * its block shape per kernel size and data type by measurement (Sec. 4.3);
+ * here the choice is also per image size.  Synchronises the device when it
+ * tunes. */
+int mf_batch_plan_create_ex(const mf_image_desc *descs, int n, int tune, mf_batch_plan **out);
 /* Runs a plan on `stream` (one CUDA graph launch: queue reset + kernel). */
 int mf_batch_run(mf_batch_plan *plan, mf_stream_t stream);
 int mf_batch_plan_destroy(mf_batch_plan *plan);
@@ -210,9 +220,13 @@ int mf_batch_run_static(const mf_image_desc *descs, int n, mf_stream_t stream);
 /* ---- tuning and introspection ------------------------------------------ */
 
 /* Times the instantiated candidates for one (k, dtype, H, W) on the current
- * device and records the fastest in the in-memory tuning table (and in the
- * JSON file named by MF_TUNE_CACHE, if set).  Uses caller-owned scratch:
- * src and dst must be device buffers of channels * H * pitch bytes. */
+ * device -- every data-oblivious configuration (network form, tile, block
+ * shape, key width) and every data-aware root tile -- and records the
+ * fastest in the in-memory tuning table under the image's size bucket
+ * (floor(log2(H * W) / 2), clamped to 7..12), and in the JSON file named by
+ * MF_TUNE_CACHE, if set.  Calls on images of other sizes use the entry of
+ * the nearest bucket.  Uses caller-owned scratch: src and dst must be device
+ * buffers of channels * H * pitch bytes. */
 int mf_autotune(const void *src, void *dst, int H, int W, size_t pitch, int channels,
                 mf_dtype dtype, int k, mf_stream_t stream);
 

@@ -30,7 +30,7 @@ GRAD_MODES = {"atomic": MF_GRAD_ATOMIC, "deterministic": MF_GRAD_DETERMINISTIC}
 EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_tile", "mf_median_filter_config",
            "mf_median_filter_rect", "mf_d1_plan_check_rect",
            "mf_median_filter_bwd",
-           "mf_median_filter_host", "mf_batch_plan_create", "mf_batch_run",
+           "mf_median_filter_host", "mf_batch_plan_create", "mf_batch_plan_create_ex", "mf_batch_run",
            "mf_batch_plan_destroy", "mf_batch_describe", "mf_batch_run_static", "mf_autotune", "mf_describe", "mf_kernel_launch_count",
            "mf_status_string", "mf_last_error", "mf_version", "mf_shutdown", "mf_probe_minmax",
            "mf_d1_plan_check",
@@ -74,6 +74,7 @@ def load_library(path=LIB_PATH):
         lib.mf_median_filter_bwd.argtypes = [vp, vp, vp, i, i, sz, sz, i, i, i, vp]
         lib.mf_median_filter_host.argtypes = [vp, vp, i, i, sz, i, i, i, i, i, vp]
         lib.mf_batch_plan_create.argtypes = [ctypes.POINTER(ImageDesc), i, ctypes.POINTER(vp)]
+        lib.mf_batch_plan_create_ex.argtypes = [ctypes.POINTER(ImageDesc), i, i, ctypes.POINTER(vp)]
         lib.mf_batch_run.argtypes = [vp, vp]
         lib.mf_batch_plan_destroy.argtypes = [vp]
         lib.mf_batch_run_static.argtypes = [ctypes.POINTER(ImageDesc), i, vp]
@@ -152,6 +153,15 @@ def mf_batch_plan_create(descs):
     arr = (ImageDesc * len(descs))(*descs)
     out = ctypes.c_void_p()
     _check(load_library().mf_batch_plan_create(arr, len(descs), ctypes.byref(out)))
+    return out
+
+
+def mf_batch_plan_create_ex(descs, tune):
+    """As mf_batch_plan_create; tune != 0 autotunes the batch's missing
+    (k, dtype, size bucket) entries on its own images first."""
+    arr = (ImageDesc * len(descs))(*descs)
+    out = ctypes.c_void_p()
+    _check(load_library().mf_batch_plan_create_ex(arr, len(descs), int(tune), ctypes.byref(out)))
     return out
 
 

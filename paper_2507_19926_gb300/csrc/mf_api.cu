@@ -47,8 +47,8 @@ const O1Entry *find_o1_nth(int k, int dtype, bool arg, int nth) {
     return nullptr;
 }
 
-const O1Entry *find_o1(int k, int dtype, bool arg) {
-    const int tuned = tune_lookup(k, dtype, arg) == MF_OBLIVIOUS ? tune_tile(k, dtype, arg) : 0;
+const O1Entry *find_o1(int k, int dtype, bool arg, int bucket) {
+    const int tuned = tune_lookup(k, dtype, arg, bucket) == MF_OBLIVIOUS ? tune_tile(k, dtype, arg, bucket) : 0;
     const O1Entry *e = tuned ? find_o1_nth(k, dtype, arg, tuned) : nullptr;
     return e ? e : find_o1_nth(k, dtype, arg, 0);
 }
@@ -117,13 +117,13 @@ struct Plan {
     int tile;     // D1 root tile
 };
 
-static int resolve(int k, int dtype, bool arg, int variant, Plan *p) {
+static int resolve(int k, int dtype, bool arg, int variant, Plan *p, int bucket = -1) {
     p->o1 = nullptr;
     p->tile = 0;
-    const O1Entry *o1 = find_o1(k, dtype, arg);
+    const O1Entry *o1 = find_o1(k, dtype, arg, bucket);
     const bool d1 = d1_supported(k, dtype, arg) != 0;
     if (variant == MF_AUTO) {
-        int tuned = tune_lookup(k, dtype, arg);
+        int tuned = tune_lookup(k, dtype, arg, bucket);
         if (tuned == MF_OBLIVIOUS && o1) variant = MF_OBLIVIOUS;
         else if (tuned == MF_DATA_AWARE && d1) variant = MF_DATA_AWARE;
         else variant = o1 ? MF_OBLIVIOUS : MF_DATA_AWARE;
@@ -137,25 +137,26 @@ static int resolve(int k, int dtype, bool arg, int variant, Plan *p) {
     if (variant == MF_DATA_AWARE) {
         if (!d1) { set_error("no data-aware kernel for k=%d dtype=%d%s", k, dtype, arg ? " (argmedian)" : ""); return MF_ERR_UNSUPPORTED; }
         p->variant = MF_DATA_AWARE;
-        p->tile = d1_default_tile(k, dtype, arg);
+        p->tile = d1_default_tile(k, dtype, arg, 0, bucket);
         return MF_OK;
     }
     set_error("unknown variant %d", variant);
     return MF_ERR_ARG;
 }
 
-int resolve_variant(int k, int dtype, bool arg, int variant, const O1Entry **o1) {
+int resolve_variant(int k, int dtype, bool arg, int variant, const O1Entry **o1, int bucket, int *tile) {
     Plan p;
-    int rc = resolve(k, dtype, arg, variant, &p);
+    int rc = resolve(k, dtype, arg, variant, &p, bucket);
     if (rc) return rc;
     if (o1) *o1 = p.o1;
+    if (tile) *tile = p.tile;
     return p.variant;
 }
 
 // The value (or record) kernel the variant resolves to, on prepared args.
 static int launch_resolved(const ImgArgs &a, int C, int k, int dtype, int variant, cudaStream_t s) {
     Plan p;
-    int rc = resolve(k, dtype, a.idx != nullptr, variant, &p);
+    int rc = resolve(k, dtype, a.idx != nullptr, variant, &p, size_bucket((long long)a.H * a.W));
     if (rc) return rc;
     if (p.variant == MF_OBLIVIOUS) {
         rc = p.o1->launch(a, C, s);
@@ -458,13 +459,13 @@ int mf_describe(int H, int W, int channels, mf_dtype dtype, int k, mf_variant va
     if (k < 1 || k > 75 || !(k & 1) || H < 1 || W < 1 || channels < 1) { set_error("bad arguments"); return MF_ERR_ARG; }
     if (k == 1) { snprintf(buf, buflen, "identity copy"); return MF_OK; }
     Plan p;
-    int rc = resolve(k, dtype, false, variant, &p);
+    int rc = resolve(k, dtype, false, variant, &p, size_bucket((long long)H * W));
     if (rc) return rc;
     if (p.variant == MF_OBLIVIOUS)
         snprintf(buf, buflen, "oblivious k=%d tile=%dx%d block=%dx%d run=%d net_ops=%d kernel=%s", k, p.o1->tw,
                  p.o1->th, p.o1->bx, p.o1->by, p.o1->run, p.o1->net_ops, p.o1->name);
     else
-        d1_describe(k, dtype, false, p.tile, buf, buflen);
+        d1_describe(k, dtype, false, p.tile, buf, buflen);  // the tile of this image's size bucket
     return MF_OK;
 }
 

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "mf_registry.h"
+#include "mf_tune.h"
 
 struct mf_batch_plan {
     int n = 0;
@@ -41,6 +42,7 @@ struct BatchClass {
     int variant;
     const O1Entry *o1;
     int k, dtype;
+    int tile;    // data-aware root tile
     int rw, rh;  // pixels covered by one work item (block region)
     int bps;     // resident blocks per SM of its persistent kernel
     std::vector<int4> items;
@@ -61,6 +63,10 @@ static void destroy_plan(mf_batch_plan *p) {
 using namespace mf;
 
 extern "C" int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_plan **out) {
+    return mf_batch_plan_create_ex(descs, n, 0, out);
+}
+
+extern "C" int mf_batch_plan_create_ex(const mf_image_desc *descs, int n, int tune, mf_batch_plan **out) {
     if (!out) { set_error("null output"); return MF_ERR_ARG; }
     *out = nullptr;
     if (!descs || n < 1) { set_error("empty batch"); return MF_ERR_ARG; }
@@ -84,6 +90,32 @@ extern "C" int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_
         set_error("no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
         return MF_ERR_CUDA;
     }
+    // tuning: every (k, dtype, size bucket) of the batch without an entry is
+    // timed on the largest image of that group (its own buffers: the
+    // candidates write its dst, which every run overwrites)
+    if (tune) {
+        std::map<std::tuple<int, int, int>, int> rep;  // (k, dtype, bucket) -> largest image
+        for (int i = 0; i < n; i++) {
+            const mf_image_desc &d = descs[i];
+            if (d.k < 3) continue;
+            const int b = size_bucket((long long)d.H * d.W);
+            if (tune_has(d.k, d.dtype, false, b)) continue;
+            auto key = std::make_tuple(d.k, (int)d.dtype, b);
+            auto it = rep.find(key);
+            if (it == rep.end() || (long long)d.H * d.W * d.channels >
+                                       (long long)descs[it->second].H * descs[it->second].W * descs[it->second].channels)
+                rep[key] = i;
+        }
+        for (auto &kv : rep) {
+            const mf_image_desc &d = descs[kv.second];
+            const int rc = mf_autotune(d.src, d.dst, d.H, d.W, d.pitch, d.channels, d.dtype, d.k, nullptr);
+            if (rc != MF_OK) return rc;
+        }
+        if (cudaDeviceSynchronize() != cudaSuccess) {
+            set_error("batch tuning: %s", cudaGetErrorString(cudaGetLastError()));
+            return MF_ERR_CUDA;
+        }
+    }
     mf_batch_plan *p = new mf_batch_plan();
     p->n = n;
     p->descs.assign(descs, descs + n);
@@ -94,29 +126,35 @@ extern "C" int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         return (long long)descs[x].H * descs[x].W * descs[x].channels > (long long)descs[y].H * descs[y].W * descs[y].channels;
     });
-    std::map<std::tuple<int, int, int>, BatchClass> classes;
+    // one class per kernel: (variant, configuration or root tile, k, dtype);
+    // the tuning table picks them per image-size bucket
+    std::map<std::tuple<int, long long, int, int>, BatchClass> classes;
     std::vector<int> copies;
     for (int i : order) {
         const mf_image_desc &d = descs[i];
         if (d.k == 1) { copies.push_back(i); continue; }
         const O1Entry *o1 = nullptr;
-        const int var = resolve_variant(d.k, d.dtype, false, MF_AUTO, &o1);
+        int tile = 0;
+        const int var = resolve_variant(d.k, d.dtype, false, MF_AUTO, &o1, size_bucket((long long)d.H * d.W), &tile);
         if (var < 0) { destroy_plan(p); return var; }
         if (var == MF_OBLIVIOUS && !o1->persist) { set_error("no persistent form for k=%d", d.k); destroy_plan(p); return MF_ERR_UNSUPPORTED; }
-        auto key = std::make_tuple(var, d.k, (int)d.dtype);
+        const long long which = var == MF_OBLIVIOUS ? (long long)(o1 - kO1Entries) : (long long)tile;
+        auto key = std::make_tuple(var, which, d.k, (int)d.dtype);
         BatchClass &c = classes[key];
         if (c.items.empty()) {
             c.variant = var;
             c.o1 = o1;
             c.k = d.k;
             c.dtype = d.dtype;
+            c.tile = tile;
             if (var == MF_OBLIVIOUS) {
                 const int lanes = o1->lanes;
                 c.rw = lanes * o1->bx * o1->tw * o1->run;
                 c.rh = o1->by * o1->th;
             } else {
                 int T, B, nt;
-                if (d1_geometry(d.k, d.dtype, false, &T, &B, &nt)) { set_error("no data-aware plan for k=%d", d.k); destroy_plan(p); return MF_ERR_UNSUPPORTED; }
+                if (d1_geometry(d.k, d.dtype, false, tile, &T, &B, &nt)) { set_error("no data-aware plan for k=%d", d.k); destroy_plan(p); return MF_ERR_UNSUPPORTED; }
+                c.tile = T;
                 c.rw = B * T;
                 c.rh = T;
             }
@@ -179,7 +217,7 @@ extern "C" int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_
         BatchClass &c = kv.second;
         int bps = 0, rc0;
         if (c.variant == MF_OBLIVIOUS) rc0 = c.o1->persist(nullptr, nullptr, 0, nullptr, 0, sms, nullptr, &bps);
-        else rc0 = d1_persist(nullptr, nullptr, 0, nullptr, c.k, c.dtype, 0, sms, nullptr, &bps);
+        else rc0 = d1_persist(nullptr, nullptr, 0, nullptr, c.k, c.dtype, c.tile, 0, sms, nullptr, &bps);
         if (rc0 != MF_OK) {
             set_error("preparing the persistent kernel for k=%d dtype=%d: %s", c.k, c.dtype,
                       cudaGetErrorString(cudaGetLastError()));
@@ -219,8 +257,8 @@ extern "C" int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_
             if (c.variant == MF_OBLIVIOUS)
                 rc = c.o1->persist((const ImgArgs *)dm, items, (int)c.items.size(), cnt, c.bps, sms, si, &grid);
             else
-                rc = d1_persist((const ImgArgs *)dm, items, (int)c.items.size(), cnt, c.k, c.dtype, c.bps, sms, si,
-                                &grid);
+                rc = d1_persist((const ImgArgs *)dm, items, (int)c.items.size(), cnt, c.k, c.dtype, c.tile, c.bps, sms,
+                                si, &grid);
             if (rc != MF_OK)
                 set_error("persistent launch for k=%d dtype=%d: %s", c.k, c.dtype, cudaGetErrorString(cudaGetLastError()));
         }

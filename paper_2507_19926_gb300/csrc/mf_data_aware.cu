@@ -281,9 +281,10 @@ int d1_supported_tile(int k, int dtype, bool arg, int T, int kh) {
     return choose_config(k, dtype, arg, T, &B, &nt, kh) ? 1 : 0;
 }
 
-int d1_default_tile(int k, int dtype, bool arg, int kh) {
+int d1_default_tile(int k, int dtype, bool arg, int kh, int bucket) {
     const bool square = kh == 0 || kh == k;
-    const int tuned = square && tune_lookup(k, dtype, arg) == MF_DATA_AWARE ? tune_tile(k, dtype, arg) : 0;
+    const int tuned =
+        square && tune_lookup(k, dtype, arg, bucket) == MF_DATA_AWARE ? tune_tile(k, dtype, arg, bucket) : 0;
     if (tuned && d1_supported_tile(k, dtype, arg, tuned)) return tuned;
     // root-tile heuristic t(k) = 2^(floor(log2 k) - 1) (paper Sec. 4.2) on
     // the shorter window side, at least 2 (1 for a window one pixel wide or
@@ -366,7 +367,7 @@ int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s, 
             return MF_ERR_UNSUPPORTED;
         }
     }
-    if (T == 0) T = d1_default_tile(k, dtype, arg, kh);
+    if (T == 0) T = d1_default_tile(k, dtype, arg, kh, size_bucket((long long)a.H * a.W));
     int B, nt;
     if (!choose_config(k, dtype, arg, T, &B, &nt, kh, TH)) {
         set_error("no data-aware plan for a %dx%d window, tile=%d", k, kh ? kh : k, T);
@@ -430,8 +431,8 @@ static int d1_persist_t(const ImgArgs *imgs, const int4 *items, int n_items, uns
     return d1_persist_n<KT, DT, 32>(imgs, items, n_items, counter, c, nt, bps, sms, s, grid_out);
 }
 
-int d1_geometry(int k, int dtype, bool arg, int *tile, int *strip, int *threads) {
-    const int T = d1_default_tile(k, dtype, arg);
+int d1_geometry(int k, int dtype, bool arg, int tile_in, int *tile, int *strip, int *threads) {
+    const int T = tile_in > 0 ? tile_in : d1_default_tile(k, dtype, arg);
     int B, nt;
     if (!T || !choose_config(k, dtype, arg, T, &B, &nt)) return MF_ERR_UNSUPPORTED;
     *tile = T;
@@ -441,9 +442,9 @@ int d1_geometry(int k, int dtype, bool arg, int *tile, int *strip, int *threads)
 }
 
 int d1_persist(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter, int k, int dtype,
-               int blocks_per_sm, int sms, cudaStream_t s, int *grid_out) {
+               int tile, int blocks_per_sm, int sms, cudaStream_t s, int *grid_out) {
     int T, B, nt;
-    if (d1_geometry(k, dtype, false, &T, &B, &nt)) return MF_ERR_UNSUPPORTED;
+    if (d1_geometry(k, dtype, false, tile, &T, &B, &nt)) return MF_ERR_UNSUPPORTED;
     // the plan upload (synchronous copies) happens in the prepare call,
     // before any stream capture
     const D1Cached *c = get_plan(k, T, B, nt, (int)key_bytes(dtype, false));

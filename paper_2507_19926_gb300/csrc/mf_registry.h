@@ -28,25 +28,27 @@ extern const O1Entry kO1Entries[];
 extern const int kO1Count;
 
 // The configuration the tuning table selects (else the default).
-const O1Entry *find_o1(int k, int dtype, bool arg);
+// bucket: size bucket of the image (size_bucket in mf_tune.h), -1 unknown.
+const O1Entry *find_o1(int k, int dtype, bool arg, int bucket = -1);
 const O1Entry *find_o1_nth(int k, int dtype, bool arg, int nth);
 
 // Data-aware variant (mf_data_aware.cu).
 int d1_supported(int k, int dtype, bool arg);
 // kh: window height for a k-wide, kh-high window (0: k x k)
 int d1_launch(const ImgArgs &a, int channels, int k, int dtype, int tile, cudaStream_t s, int kh = 0);
-int d1_default_tile(int k, int dtype, bool arg, int kh = 0);
+int d1_default_tile(int k, int dtype, bool arg, int kh = 0, int bucket = -1);
 int d1_supported_tile(int k, int dtype, bool arg, int tile, int kh = 0);
 int d1_describe(int k, int dtype, bool arg, int tile, char *buf, size_t n);
 void d1_release_all();
 void d3_release_all();  // volumetric plans (mf_volume.cu)
 // Persistent data-aware launch over a device work list for (k, dtype); the
 // block geometry is the plan d1_geometry reports.
-int d1_geometry(int k, int dtype, bool arg, int *tile, int *strip, int *threads);
+// tile_in: the root tile (0: the default for an image of unknown size).
+int d1_geometry(int k, int dtype, bool arg, int tile_in, int *tile, int *strip, int *threads);
 // n_items == 0 prepares (plan upload, attributes) and returns the blocks
 // per SM in *grid_out; call that outside stream capture.
 int d1_persist(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *counter, int k, int dtype,
-               int blocks_per_sm, int sms, cudaStream_t s, int *grid_out);
+               int tile, int blocks_per_sm, int sms, cudaStream_t s, int *grid_out);
 
 // Argmedian from medians already in a.dst (mf_argmedian.cu).
 int launch_argmedian_from_values(const ImgArgs &a, int channels, int k, int dtype, cudaStream_t s);
@@ -64,6 +66,8 @@ void set_error(const char *fmt, ...);
 
 // Variant the plain entry point would run for (k, dtype): MF_OBLIVIOUS (and
 // its entry) or MF_DATA_AWARE; negative status if neither exists.
-int resolve_variant(int k, int dtype, bool arg, int variant, const O1Entry **o1);
+// *tile (optional) receives the data-aware root tile.
+int resolve_variant(int k, int dtype, bool arg, int variant, const O1Entry **o1, int bucket = -1,
+                    int *tile = nullptr);
 
 }  // namespace mf

@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "mf_registry.h"
+#include "mf_tune.h"
 
 namespace mf {
 
@@ -121,7 +122,8 @@ extern "C" int mf_batch_run_static(const mf_image_desc *descs, int n, mf_stream_
         if (a < b + bytes && b < a + bytes) { set_error("image %d: src and dst overlap", i); return MF_ERR_ALIAS; }
         img_cls[i] = -1;
         if (d.k == 1) continue;
-        const O1Entry *o1 = (d.k >= 3 && (d.k & 1)) ? find_o1(d.k, d.dtype, false) : nullptr;
+        const O1Entry *o1 =
+            (d.k >= 3 && (d.k & 1)) ? find_o1(d.k, d.dtype, false, size_bucket((long long)d.H * d.W)) : nullptr;
         if (!o1 || !o1->persist) {
             set_error("image %d: the static batch runs only the data-oblivious kernels, not built for k = %d "
                       "with this dtype", i, d.k);

@@ -1,9 +1,13 @@
-// Autotuner: times the instantiated candidates of one (k, dtype) on the
-// current device with CUDA events and records the fastest.  The paper picks
-// its block shape per kernel size and data type by measurement (Sec. 4.3);
-// here the choice covers the variant (Sec. 4 vs Sec. 5) and the
-// data-aware root tile.  The table can be persisted as JSON (MF_TUNE_CACHE),
-// keyed by GPU name and SM count.
+// Autotuner: times the instantiated candidates of one (k, dtype) on an
+// image of the caller's on the current device with CUDA events and records
+// the fastest for that image's size bucket.  The paper picks its block
+// shape per kernel size and data type by measurement (Sec. 4.3); here the
+// choice covers the variant (Sec. 4 vs Sec. 5), the data-oblivious
+// configuration (network form, tile, block shape, key width) and the
+// data-aware root tile, per image-size bucket (small images favour other
+// block shapes and tiles than large ones: fewer blocks than SMs, tails).
+// The table can be persisted as JSON (MF_TUNE_CACHE), keyed by GPU name and
+// SM count.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -23,9 +27,18 @@ struct TuneVal {
     float ms;
 };
 
+typedef std::tuple<int, int, int, int> TuneKey;  // k, dtype, arg, size bucket
 static std::mutex g_mu;
-static std::map<std::tuple<int, int, int>, TuneVal> *g_table = new std::map<std::tuple<int, int, int>, TuneVal>();
+static std::map<TuneKey, TuneVal> *g_table = new std::map<TuneKey, TuneVal>();
 static bool g_loaded = false;
+
+int size_bucket(long long pixels) {
+    if (pixels < 1) return -1;
+    int l = 0;
+    while ((2ll << l) <= pixels) l++;  // floor(log2(pixels))
+    int b = l / 2;
+    return b < 7 ? 7 : (b > 12 ? 12 : b);
+}
 
 static std::string device_key() {
     int dev = 0;
@@ -42,7 +55,7 @@ static std::string device_key() {
 }
 
 // Cache file format: one JSON object per line,
-// {"device": "...", "k": K, "dtype": D, "arg": A, "variant": V, "tile": T, "ms": M}
+// {"device": "...", "k": K, "dtype": D, "arg": A, "bucket": B, "variant": V, "tile": T, "ms": M}
 static void load_locked() {
     if (g_loaded) return;
     g_loaded = true;
@@ -53,40 +66,69 @@ static void load_locked() {
     const std::string dk = device_key();
     char line[1024], dev[400];
     while (fgets(line, sizeof line, f)) {
-        int k, dt, arg, var, tile;
+        int k, dt, arg, bucket, var, tile;
         float ms;
-        if (sscanf(line, " {\"device\": \"%399[^\"]\", \"k\": %d, \"dtype\": %d, \"arg\": %d, \"variant\": %d, \"tile\": %d, \"ms\": %f",
-                   dev, &k, &dt, &arg, &var, &tile, &ms) == 7 &&
+        if (sscanf(line,
+                   " {\"device\": \"%399[^\"]\", \"k\": %d, \"dtype\": %d, \"arg\": %d, \"bucket\": %d, \"variant\": %d, "
+                   "\"tile\": %d, \"ms\": %f",
+                   dev, &k, &dt, &arg, &bucket, &var, &tile, &ms) == 8 &&
             dk == dev)
-            (*g_table)[std::make_tuple(k, dt, arg)] = TuneVal{var, tile, ms};
+            (*g_table)[std::make_tuple(k, dt, arg, bucket)] = TuneVal{var, tile, ms};
     }
     fclose(f);
 }
 
-int tune_lookup(int k, int dtype, bool arg) {
-    std::lock_guard<std::mutex> lk(g_mu);
+// The entry of the bucket nearest to `bucket` (ties: the larger bucket; an
+// unknown size: the largest bucket), or nullptr.
+static const TuneVal *nearest_locked(int k, int dtype, bool arg, int bucket) {
     load_locked();
-    auto it = g_table->find(std::make_tuple(k, dtype, arg ? 1 : 0));
-    return it == g_table->end() ? MF_AUTO : it->second.variant;
+    const TuneVal *best = nullptr;
+    int best_d = 1 << 30, best_b = -1;
+    for (auto it = g_table->lower_bound(std::make_tuple(k, dtype, arg ? 1 : 0, -1000));
+         it != g_table->end() && std::get<0>(it->first) == k && std::get<1>(it->first) == dtype &&
+         std::get<2>(it->first) == (arg ? 1 : 0);
+         ++it) {
+        const int b = std::get<3>(it->first);
+        const int d = bucket < 0 ? -b : (b > bucket ? b - bucket : bucket - b);
+        if (d < best_d || (d == best_d && b > best_b)) {
+            best = &it->second;
+            best_d = d;
+            best_b = b;
+        }
+    }
+    return best;
 }
 
-int tune_tile(int k, int dtype, bool arg) {
+int tune_lookup(int k, int dtype, bool arg, int bucket) {
     std::lock_guard<std::mutex> lk(g_mu);
-    load_locked();
-    auto it = g_table->find(std::make_tuple(k, dtype, arg ? 1 : 0));
-    return it == g_table->end() ? 0 : it->second.tile;
+    const TuneVal *v = nearest_locked(k, dtype, arg, bucket);
+    return v ? v->variant : MF_AUTO;
 }
 
-void tune_record(int k, int dtype, bool arg, int variant, int tile, float ms) {
+int tune_tile(int k, int dtype, bool arg, int bucket) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const TuneVal *v = nearest_locked(k, dtype, arg, bucket);
+    return v ? v->tile : 0;
+}
+
+bool tune_has(int k, int dtype, bool arg, int bucket) {
     std::lock_guard<std::mutex> lk(g_mu);
     load_locked();
-    (*g_table)[std::make_tuple(k, dtype, arg ? 1 : 0)] = TuneVal{variant, tile, ms};
+    return g_table->count(std::make_tuple(k, dtype, arg ? 1 : 0, bucket)) != 0;
+}
+
+void tune_record(int k, int dtype, bool arg, int bucket, int variant, int tile, float ms) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_locked();
+    (*g_table)[std::make_tuple(k, dtype, arg ? 1 : 0, bucket)] = TuneVal{variant, tile, ms};
     const char *path = getenv("MF_TUNE_CACHE");
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "{\"device\": \"%s\", \"k\": %d, \"dtype\": %d, \"arg\": %d, \"variant\": %d, \"tile\": %d, \"ms\": %.6f}\n",
-            device_key().c_str(), k, dtype, arg ? 1 : 0, variant, tile, ms);
+    fprintf(f,
+            "{\"device\": \"%s\", \"k\": %d, \"dtype\": %d, \"arg\": %d, \"bucket\": %d, \"variant\": %d, "
+            "\"tile\": %d, \"ms\": %.6f}\n",
+            device_key().c_str(), k, dtype, arg ? 1 : 0, bucket, variant, tile, ms);
     fclose(f);
 }
 
@@ -170,6 +212,6 @@ extern "C" int mf_autotune(const void *src, void *dst, int H, int W, size_t pitc
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { set_error("autotune: %s", cudaGetErrorString(e)); return MF_ERR_CUDA; }
     if (best_var == 0) { set_error("no candidate for k=%d dtype=%d", k, (int)dtype); return MF_ERR_UNSUPPORTED; }
-    tune_record(k, dtype, false, best_var, best_tile, best);
+    tune_record(k, dtype, false, size_bucket((long long)H * W), best_var, best_tile, best);
     return MF_OK;
 }

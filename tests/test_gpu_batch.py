@@ -60,6 +60,29 @@ def test_batch_matches_oracle_and_replays():
         mf.mf_batch_plan_destroy(plan)
 
 
+def test_tuned_batch_plan_matches_oracle():
+    """A plan that first autotunes its (k, dtype, size bucket) groups on its
+    own images (mf_batch_plan_create_ex) still filters every image exactly:
+    the tuner only chooses among kernels that compute the same filter."""
+    import torch
+    ensure_lib()
+    imgs, descs = _make_batch(SPECS, 900)
+    plan = mf.mf_batch_plan_create_ex(descs, 1)
+    try:
+        for _, _, _, dst, _, _ in imgs:
+            dst.zero_()  # tuning ran candidates into the images' own dst
+        mf.mf_batch_run(plan, None)
+        torch.cuda.synchronize()
+        for x, xs, src, dst, k, dt in imgs:
+            W = x.shape[2]
+            got = to_host(dst, x.dtype)
+            want = oracle.median_filter(x, k)
+            assert np.array_equal(got[:, :, :W].view(np.uint8), want.view(np.uint8)), (x.shape, dt, k)
+            assert (got[:, :, W:].view(np.uint8) == 0).all()
+    finally:
+        mf.mf_batch_plan_destroy(plan)
+
+
 def test_uneven_batch_at_full_size_matches_plain_launches():
     """The 64-image batch (sizes log-uniform 256x256 .. 4096x3072, dtypes
     u8/u16/f32, odd k 3..31): each image equals its plain launch bit for bit."""

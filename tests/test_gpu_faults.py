@@ -75,5 +75,6 @@ print(mf.mf_describe(512, 512, 1, mf.MF_U8, 27))
     assert a.returncode == 0, a.stderr[-2000:]
     lines = cache.read_text().strip().splitlines()
     assert lines and json.loads(lines[-1])["k"] == 27
+    assert json.loads(lines[-1])["bucket"] == 9  # 512 x 512: floor(log2(2^18) / 2)
     b = subprocess.run([sys.executable, "-c", code, ROOT, "read"], capture_output=True, text=True, env=env, timeout=300)
     assert b.returncode == 0 and b.stdout.strip().splitlines()[-1] == a.stdout.strip().splitlines()[-1]
