@@ -104,30 +104,32 @@ __global__ void __launch_bounds__(AM_BW *AM_BH) argmedian_hash_kernel(ImgArgs a,
     const char *src = a.src + (size_t)z * a.plane;
     const int tid = threadIdx.y * AM_BW + threadIdx.x, NT = AM_BW * AM_BH;
     for (int i = tid; i < NS; i += NT) ht[i] = 0ull;
-    for (int i = tid; i < SW * SH; i += NT) {
-        const int sy = i / SW, sx = i - sy * SW;
-        const int y = clampi(y0 - r + sy, a.y_lo, a.y_hi), x = clampi(x0 - r + sx, 0, a.W - 1);
-        foot[i] = Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, x));
-    }
     __syncthreads();
+    // one warp a footprint row at a time: load, key, keep for the window
+    // pass, and enter into the table (no index division)
     const unsigned long long DUP = 0xffffffff00000000ull;
-    for (int i = tid; i < SW * SH; i += NT) {
-        const int sy = i / SW, sx = i - sy * SW;
-        const uint32_t key = foot[i];
-        const uint32_t srcpix = (uint32_t)(clampi(y0 - r + sy, a.y_lo, a.y_hi) * a.W + clampi(x0 - r + sx, 0, a.W - 1));
-        const unsigned long long mine = ((unsigned long long)(srcpix + 1) << 32) | key;
-        unsigned h = am_hash(key, bits);
-        for (int probe = 0; probe < NS; probe++) {  // the table is at most half full: ends early
-            unsigned long long cur = ht[h];
-            if (cur == 0ull) {
-                cur = atomicCAS(&ht[h], 0ull, mine);
-                if (cur == 0ull) break;  // inserted
+    for (int sy = threadIdx.y; sy < SH; sy += AM_BH) {
+        const int y = clampi(y0 - r + sy, a.y_lo, a.y_hi);
+        const E *row = reinterpret_cast<const E *>(src + (ptrdiff_t)y * (ptrdiff_t)a.pitch);
+        for (int sx = threadIdx.x; sx < SW; sx += AM_BW) {
+            const int x = clampi(x0 - r + sx, 0, a.W - 1);
+            const uint32_t key = Dt<DT>::key(__ldg(row + x));
+            foot[sy * SW + sx] = key;
+            const uint32_t srcpix = (uint32_t)(y * a.W + x);
+            const unsigned long long mine = ((unsigned long long)(srcpix + 1) << 32) | key;
+            unsigned h = am_hash(key, bits);
+            for (int probe = 0; probe < NS; probe++) {  // the table is at most half full: ends early
+                unsigned long long cur = ht[h];
+                if (cur == 0ull) {
+                    cur = atomicCAS(&ht[h], 0ull, mine);
+                    if (cur == 0ull) break;  // inserted
+                }
+                if ((uint32_t)cur == key) {  // same key: same source pixel, or a duplicate
+                    if ((cur >> 32) != (unsigned long long)(srcpix + 1) && (cur & DUP) != DUP) atomicOr(&ht[h], DUP);
+                    break;
+                }
+                h = (h + 1) & (unsigned)(NS - 1);
             }
-            if ((uint32_t)cur == key) {  // same key: same source pixel, or a duplicate
-                if ((cur >> 32) != (unsigned long long)(srcpix + 1) && (cur & DUP) != DUP) atomicOr(&ht[h], DUP);
-                break;
-            }
-            h = (h + 1) & (unsigned)(NS - 1);
         }
     }
     __syncthreads();
