@@ -187,6 +187,14 @@ def probe_ipc(sms, mhz, lanes):
     return _PROBE[lanes]
 
 
+def d1_key_bytes(dt, with_idx=False):
+    """Bytes of one data-aware shared-memory key: 8-bit values as 8-bit keys,
+    16-bit as 16, 32-bit as 32; argmedian records add 16 or 32 bits."""
+    if with_idx:
+        return 8 if dt in ("u32", "f32") else 4
+    return {"u8": 1, "u16": 2, "u32": 4, "f32": 4}[dt]
+
+
 def roofline_entry(plan, dt, k, px, ms, sms, peaks, probe_mhz=None, with_idx=False):
     """Roofline of one filter call: the floor is the slower of its HBM bytes
     (in + out) and its work at the unit that bounds the variant -- min/max
@@ -215,10 +223,13 @@ def roofline_entry(plan, dt, k, px, ms, sms, peaks, probe_mhz=None, with_idx=Fal
     elif "data-aware" in plan:
         m = re.search(r"merged/px=([\d.]+) sorted/px=([\d.]+)", plan)
         if m:
-            kb = (4 if with_idx else 2) if dt in ("u8", "u16") else (8 if with_idx else 4)
+            kb = d1_key_bytes(dt, with_idx)
             elems = float(m.group(1)) + float(m.group(2))
             t_work, bound = elems * 2 * kb * px / (sms * 128 * max_mhz * 1e6), "smem"
             out["smem_frac"] = round(t_work / (ms * 1e-3), 4)
+            # the same element accesses against one conflict-free 32-lane
+            # wavefront a clock a SM (the access rate, whatever the key width)
+            out["smem_access_frac"] = round(elems * 2 * px / (sms * 32 * max_mhz * 1e6) / (ms * 1e-3), 4)
     if t_work is None or t_hbm >= t_work:
         out["bound"], out["frac"] = "hbm", out["hbm_frac"]
     else:
@@ -706,7 +717,7 @@ def run_ours(args):
         import re
         m = re.search(r"merged/px=([\d.]+) sorted/px=([\d.]+)", plan)
         if m:
-            kb = 2 if dt in ("u8", "u16") else 4
+            kb = d1_key_bytes(dt)
             elems_px = float(m.group(1)) + float(m.group(2))
             max_mhz = peaks.get("sm_max_mhz", 2070.0)
             peak = sms * 128 * max_mhz * 1e6 / 1e9  # GB/s

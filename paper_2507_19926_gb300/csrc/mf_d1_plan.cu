@@ -44,8 +44,10 @@ static const bool D1_ODD_CHUNKS = !getenv("MF_D1_EVEN_CHUNKS");
 // lifetimes (less shared memory: more blocks a SM where the state limits
 // them) at the price of phases that mix sorts and merges.  Measured on
 // 4096^2 images it pays for 4-byte keys from k = 41 (u32 k = 75 46.9 ->
-// 35.9 ms, k = 45 13.6 -> 12.8 ms) and for 2-byte keys from k = 61 (u8 k = 75
-// 20.3 -> 19.3 ms) and costs up to 12% below; volumes gain nothing.
+// 35.9 ms, k = 45 13.6 -> 12.8 ms) and for 2-byte keys from k = 61 (u16
+// k = 61 18.6 -> 14.0 ms: two 512-thread blocks then fit an SM), and costs
+// up to 12% below; 1-byte keys (whose state already fits) and volumes gain
+// nothing (u8 k = 75 15.5 ms without, 16.2 with).
 // MF_D1_BALANCE=0/1 forces it off/on for every plan.
 static int d1_balance_env() {
     const char *e = getenv("MF_D1_BALANCE");
@@ -54,7 +56,7 @@ static int d1_balance_env() {
 static bool d1_balance(int n_win, int key_bytes, bool volume) {
     static const int forced = d1_balance_env();
     if (forced >= 0) return forced != 0;
-    if (volume) return false;
+    if (volume || key_bytes == 1) return false;
     return key_bytes >= 4 ? n_win >= 41 * 41 : n_win >= 61 * 61;
 }
 // Split cores grown from shared sorted slabs plus per-node corner blocks
@@ -621,7 +623,9 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
         // the chunks of one merge run on consecutive threads: an odd number of
         // 4-byte words between their output runs spreads a warp's stores
         // (and its roughly proportional input reads) over all 32 banks
-        if (D1_ODD_CHUNKS) chunk = key_bytes == 2 ? (chunk & ~3) + 2 : (chunk | 1);
+        // (8- and 16-bit keys: 2 mod 4 elements, measured the same for both;
+        // wider keys: odd)
+        if (D1_ODD_CHUNKS) chunk = key_bytes <= 2 ? (chunk & ~3) + 2 : (chunk | 1);
         // sorts first, grouped by size class, then merges
         std::vector<int> order = by_phase[p];
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {

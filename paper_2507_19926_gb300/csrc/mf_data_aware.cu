@@ -160,10 +160,15 @@ static std::map<PlanKey, D1Plan *> *g_plans = new std::map<PlanKey, D1Plan *>();
 static std::map<std::tuple<int, int, int, int, int, int, int, int>, D1Cached *> *g_d1 =
     new std::map<std::tuple<int, int, int, int, int, int, int, int>, D1Cached *>();
 
+// Key width in shared memory: 8-bit values merge as 8-bit keys (half the
+// state and four keys a bank word: u8 4096^2 k = 27 5.12 -> 4.37 ms, k = 45
+// 9.08 -> 8.44 ms against 16-bit keys), 16-bit values as 16-bit keys,
+// 32-bit values as 32-bit keys; argmedian records carry the footprint index
+// in 16 (8/16-bit data) or 32 more bits.
 static size_t key_bytes(int dtype, bool arg) {
     const bool wide = dtype == MF_U32 || dtype == MF_F32;
     if (arg) return wide ? 8 : 4;
-    return wide ? 4 : 2;
+    return wide ? 4 : (dtype == MF_U8 ? 1 : 2);
 }
 
 // Host plan for a window of k columns by kh rows (kh = 0: square); nullptr
@@ -197,18 +202,50 @@ static bool choose_config(int k, int dtype, bool arg, int T, int *B, int *nt, in
         (square && T < 2) || T > 32 || TH > 32 || (T & (T - 1)) || (TH & (TH - 1)) || T > k || TH > kh)
         return false;
     const int kb = (int)key_bytes(dtype, arg);
+    // MF_D1_NT=256|512|1024: one root tile a block with that many threads
+    // wherever its state fits (configuration sweeps)
+    static const int forced_nt = getenv("MF_D1_NT") ? atoi(getenv("MF_D1_NT")) : 0;
+    if (forced_nt == 256 || forced_nt == 512 || forced_nt == 1024) {
+        const D1Plan *pf = host_plan(k, T, 1, forced_nt, kb, kh, TH);
+        if (pf && (size_t)pf->smem_elems * kb <= D1_SMEM_BUDGET) {
+            *B = 1;
+            *nt = forced_nt;
+            return true;
+        }
+    }
+    // strips are as wide as 16-bit keys would allow (8-bit keys count two
+    // bytes an element here: wider strips of 8-bit keys measured slower)
+    const int kbs = kb < 2 ? 2 : kb;
     for (int b = 8; b >= 1; b /= 2) {
         const D1Plan *p = host_plan(k, T, b, 256, kb, kh, TH);
-        if (p && (size_t)p->smem_elems * kb <= D1_SMEM_SMALL) {
+        if (p && (size_t)p->smem_elems * kbs <= D1_SMEM_SMALL) {
             *B = b;
             *nt = 256;
+            return true;
+        }
+    }
+    // 8-bit keys: one tile with 256 threads while three blocks fit an SM,
+    // else 512 threads while two fit (u8 4096^2 against the 16-bit-key
+    // shapes: k = 31 5.86 -> 4.59 ms, k = 45 8.50 -> 7.64 ms, k = 61 12.94 ->
+    // 11.53 ms, k = 75 18.72 -> 15.45 ms)
+    if (kb == 1) {
+        const D1Plan *p2 = host_plan(k, T, 1, 256, kb, kh, TH);
+        if (p2 && 3 * ((size_t)p2->smem_elems + 1024) <= 227 * 1024) {
+            *B = 1;
+            *nt = 256;
+            return true;
+        }
+        const D1Plan *p4 = host_plan(k, T, 1, 512, kb, kh, TH);
+        if (p4 && 2 * ((size_t)p4->smem_elems + 1024) <= 227 * 1024) {
+            *B = 1;
+            *nt = 512;
             return true;
         }
     }
     // one tile per block: 512 threads when two blocks share an SM, else
     // 1024 threads (32 warps) in a block of its own
     const D1Plan *p5 = host_plan(k, T, 1, 512, kb, kh, TH);
-    if (p5 && 2 * ((size_t)p5->smem_elems * kb + 1024) <= 227 * 1024) {
+    if (p5 && 2 * ((size_t)p5->smem_elems * kbs + 1024) <= 227 * 1024) {
         *B = 1;
         *nt = 512;
         return true;
@@ -297,7 +334,7 @@ int d1_default_tile(int k, int dtype, bool arg, int kh, int bucket) {
     if (t > 16) t = 16;
     // 2-byte keys: the 16 x 16 tree measured faster from k = 27 on
     // (u8 4096^2: 5.02 vs 5.61 ms at k = 27, 6.25 vs 6.40 ms at k = 31)
-    if (key_bytes(dtype, arg) == 2 && kmin >= 27) t = 16;
+    if (key_bytes(dtype, arg) <= 2 && kmin >= 27) t = 16;
     for (; t >= 1; t /= 2)
         if (d1_supported_tile(k, dtype, arg, t, kh)) return t;
     return 0;
@@ -314,7 +351,7 @@ static bool rect_tiles(int kw, int kh, int dtype, bool arg, int *TW, int *TH) {
         int t = 1;
         while (t * 4 <= k) t *= 2;
         if (t > 16) t = 16;
-        if (key_bytes(dtype, arg) == 2 && k >= 27) t = 16;
+        if (key_bytes(dtype, arg) <= 2 && k >= 27) t = 16;
         return t;
     };
     int tw = t_of(kw), th = t_of(kh);
@@ -380,7 +417,7 @@ int d1_launch(const ImgArgs &a, int C, int k, int dtype, int T, cudaStream_t s, 
     }
     int rc;
     switch (dtype * 2 + (arg ? 1 : 0)) {
-        case MF_U8 * 2: rc = d1_launch_t<uint16_t, MF_U8, false>(a, C, c, nt, s); break;
+        case MF_U8 * 2: rc = d1_launch_t<uint8_t, MF_U8, false>(a, C, c, nt, s); break;
         case MF_U16 * 2: rc = d1_launch_t<uint16_t, MF_U16, false>(a, C, c, nt, s); break;
         case MF_U32 * 2: rc = d1_launch_t<uint32_t, MF_U32, false>(a, C, c, nt, s); break;
         case MF_F32 * 2: rc = d1_launch_t<uint32_t, MF_F32, false>(a, C, c, nt, s); break;
@@ -451,7 +488,7 @@ int d1_persist(const ImgArgs *imgs, const int4 *items, int n_items, unsigned *co
     if (!c) return MF_ERR_CUDA;
     const int b = blocks_per_sm;
     switch (dtype) {
-        case MF_U8: return d1_persist_t<uint16_t, MF_U8>(imgs, items, n_items, counter, c, nt, b, sms, s, grid_out);
+        case MF_U8: return d1_persist_t<uint8_t, MF_U8>(imgs, items, n_items, counter, c, nt, b, sms, s, grid_out);
         case MF_U16: return d1_persist_t<uint16_t, MF_U16>(imgs, items, n_items, counter, c, nt, b, sms, s, grid_out);
         case MF_U32: return d1_persist_t<uint32_t, MF_U32>(imgs, items, n_items, counter, c, nt, b, sms, s, grid_out);
         case MF_F32: return d1_persist_t<uint32_t, MF_F32>(imgs, items, n_items, counter, c, nt, b, sms, s, grid_out);
