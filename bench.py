@@ -601,7 +601,7 @@ def bench_volume(dev, stream, flush, reps=3, cases=(("u8", 3, "auto"), ("u8", 3,
         # merged or sorted element read once and written once at the least
         m = re.search(r"merged/vox=([\d.]+) sorted/vox=([\d.]+)", plan)
         if m:
-            kb = 2 if dt in ("u8", "u16") else 4
+            kb = d1_key_bytes(dt)
             gbs = (float(m.group(1)) + float(m.group(2))) * 2 * kb * n ** 3 / (ms * 1e-3) / 1e9
             r["smem_roofline_frac"] = round(gbs / smem_peak, 4)
         res.append(r)

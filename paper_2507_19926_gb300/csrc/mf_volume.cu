@@ -199,7 +199,9 @@ static std::mutex g_d3_mu;
 // (k, key bytes, device) -> uploaded plan (nullptr: none fits)
 static std::map<std::tuple<int, int, int>, D3Cached *> *g_d3 = new std::map<std::tuple<int, int, int>, D3Cached *>();
 
-static int d3_key_bytes(int dtype) { return dtype == MF_U32 || dtype == MF_F32 ? 4 : 2; }
+// 8-bit values merge as 8-bit keys (as in the 2D data-aware kernel: half
+// the state, four keys a bank word), wider values as 16/32-bit keys.
+static int d3_key_bytes(int dtype) { return dtype == MF_U32 || dtype == MF_F32 ? 4 : (dtype == MF_U8 ? 1 : 2); }
 
 // Root tile, strip and block size: the largest T (at most 4: the T = 8 trees
 // need more than 200 KB from k = 9 on) whose state fits shared memory; with
@@ -208,11 +210,14 @@ static int d3_key_bytes(int dtype) { return dtype == MF_U32 || dtype == MF_F32 ?
 // block has enough merges to spread over its threads), else one tile with
 // 512 threads when two blocks fit, else 1024.
 static bool d3_choose(int k, int kb, D1Plan *out, int *nt_out) {
+    // 8-bit keys take the shapes of 16-bit keys: the same threads and
+    // strips, half the shared memory
+    const size_t kbs = kb < 2 ? 2 : (size_t)kb;
     for (int T = 4; T >= 1; T /= 2) {
         if (T > k) continue;
         for (int nb = 8; nb >= 1; nb /= 2) {
             D1Plan pl;
-            if (d3_build_plan(k, T, &pl, 256, kb, nb) && (size_t)pl.smem_elems * kb <= D3_SMEM_SMALL) {
+            if (d3_build_plan(k, T, &pl, 256, kb, nb) && (size_t)pl.smem_elems * kbs <= D3_SMEM_SMALL) {
                 *out = pl;
                 *nt_out = 256;
                 return true;
@@ -221,7 +226,7 @@ static bool d3_choose(int k, int kb, D1Plan *out, int *nt_out) {
         for (int nt : {512, 1024}) {
             D1Plan pl;
             if (!d3_build_plan(k, T, &pl, nt, kb, 1)) break;
-            const size_t bytes = (size_t)pl.smem_elems * kb;
+            const size_t bytes = (size_t)pl.smem_elems * kbs;
             if (nt == 512 ? 2 * (bytes + 1024) <= 227 * 1024 : bytes <= D3_SMEM_BUDGET) {
                 *out = pl;
                 *nt_out = nt;
@@ -426,7 +431,7 @@ extern "C" int mf_median_filter_3d_ex(const void *src, void *dst, int D, int H, 
         return MF_ERR_ARG;
     }
     switch (dtype) {
-        case MF_U8: rc = d3_launch_t<uint16_t, MF_U8>(a, volumes, c, s); break;
+        case MF_U8: rc = d3_launch_t<uint8_t, MF_U8>(a, volumes, c, s); break;
         case MF_U16: rc = d3_launch_t<uint16_t, MF_U16>(a, volumes, c, s); break;
         case MF_U32: rc = d3_launch_t<uint32_t, MF_U32>(a, volumes, c, s); break;
         default: rc = d3_launch_t<uint32_t, MF_F32>(a, volumes, c, s); break;
