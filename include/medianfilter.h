@@ -170,13 +170,15 @@ typedef struct mf_batch_plan mf_batch_plan;
 int mf_batch_plan_create(const mf_image_desc *descs, int n, mf_batch_plan **out);
 /* As mf_batch_plan_create; with tune != 0 every (k, dtype, image-size
  * bucket) of the batch that the tuning table has no entry for is first
- * autotuned (mf_autotune) on the largest image of that group -- on its own
- * buffers, so those images' dst are written during planning -- and the
- * images are then grouped by the kernel each one's bucket selects
- * (variant, network configuration or data-aware root tile).  The paper picks
- * its block shape per kernel size and data type by measurement (Sec. 4.3);
- * here the choice is also per image size.  Synchronises the device when it
- * tunes. */
+ * tuned on the largest image of that group -- like mf_autotune, but each
+ * candidate is timed on enough concurrent copies of the image (outputs in
+ * scratch the call allocates and frees; the image's own dst is written too)
+ * to fill the GPU, since the batch runs its kernel classes concurrently and
+ * needs throughput, not the latency of one small launch -- and the images
+ * are then grouped by the kernel each one's bucket selects (variant,
+ * network configuration or data-aware root tile).  The paper picks its block
+ * shape per kernel size and data type by measurement (Sec. 4.3); here the
+ * choice is also per image size.  Synchronises the device when it tunes. */
 int mf_batch_plan_create_ex(const mf_image_desc *descs, int n, int tune, mf_batch_plan **out);
 /* Runs a plan on `stream` (one CUDA graph launch: queue reset + kernel). */
 int mf_batch_run(mf_batch_plan *plan, mf_stream_t stream);

@@ -91,8 +91,9 @@ extern "C" int mf_batch_plan_create_ex(const mf_image_desc *descs, int n, int tu
         return MF_ERR_CUDA;
     }
     // tuning: every (k, dtype, size bucket) of the batch without an entry is
-    // timed on the largest image of that group (its own buffers: the
-    // candidates write its dst, which every run overwrites)
+    // timed on the largest image of that group, by throughput (concurrent
+    // copies, as the batch's classes run concurrently); the candidates
+    // write that image's dst, which every run overwrites
     if (tune) {
         std::map<std::tuple<int, int, int>, int> rep;  // (k, dtype, bucket) -> largest image
         for (int i = 0; i < n; i++) {
@@ -108,7 +109,7 @@ extern "C" int mf_batch_plan_create_ex(const mf_image_desc *descs, int n, int tu
         }
         for (auto &kv : rep) {
             const mf_image_desc &d = descs[kv.second];
-            const int rc = mf_autotune(d.src, d.dst, d.H, d.W, d.pitch, d.channels, d.dtype, d.k, nullptr);
+            const int rc = tune_for_batch(d.src, d.dst, d.H, d.W, d.pitch, d.channels, d.dtype, d.k);
             if (rc != MF_OK) return rc;
         }
         if (cudaDeviceSynchronize() != cudaSuccess) {

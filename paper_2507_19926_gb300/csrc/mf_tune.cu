@@ -15,6 +15,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "mf_registry.h"
 #include "mf_tune.h"
@@ -132,37 +133,138 @@ void tune_record(int k, int dtype, bool arg, int bucket, int variant, int tile, 
     fclose(f);
 }
 
-static float time_ms(int (*fn)(void *), void *ctx, cudaStream_t s, int *rc) {
-    cudaEvent_t a, b;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    *rc = fn(ctx);  // warm-up (also sets kernel attributes)
-    float best = 1e30f;
-    for (int rep = 0; rep < 3 && *rc == MF_OK; rep++) {
-        cudaEventRecord(a, s);
-        *rc = fn(ctx);
-        cudaEventRecord(b, s);
-        cudaEventSynchronize(b);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, a, b);
-        if (ms < best) best = ms;
-    }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    return best;
-}
-
+// One candidate: the data-oblivious configuration o1, else the data-aware
+// root tile.
 struct Cand {
-    const ImgArgs *a;
-    int C, k, dtype, tile;
     const O1Entry *o1;
-    cudaStream_t s;
+    int tile;
 };
 
-static int run_cand(void *p) {
-    Cand *c = (Cand *)p;
-    if (c->o1) return c->o1->launch(*c->a, c->C, c->s);
-    return d1_launch(*c->a, c->C, c->k, c->dtype, c->tile, c->s);
+static int launch_cand(const Cand &c, const ImgArgs &a, int C, int k, int dtype, cudaStream_t s) {
+    if (c.o1) return c.o1->launch(a, C, s);
+    return d1_launch(a, C, k, dtype, c.tile, s);
+}
+
+// Best of three timings (after a warm-up) of the candidate on `copies`
+// images at once: copy r reads a's input and writes dsts[r], each on its
+// own stream, all forked from and joined back to s.  copies = 1 times one
+// launch (latency); more copies of a small image fill the GPU the way a
+// batch's concurrent classes do (throughput).  Returns ms per image.
+static float time_cand(const Cand &c, const ImgArgs &a, int C, int k, int dtype, cudaStream_t s, int copies,
+                       char *const *dsts, const cudaStream_t *streams, cudaEvent_t fork, cudaEvent_t *joins,
+                       int *rc) {
+    auto run = [&]() {
+        int r0 = MF_OK;
+        if (copies == 1) return launch_cand(c, a, C, k, dtype, s);
+        cudaEventRecord(fork, s);
+        for (int r = 0; r < copies; r++) {
+            cudaStreamWaitEvent(streams[r], fork, 0);
+            ImgArgs ar = a;
+            ar.dst = dsts[r];
+            const int rr = launch_cand(c, ar, C, k, dtype, streams[r]);
+            if (rr != MF_OK) r0 = rr;
+            cudaEventRecord(joins[r], streams[r]);
+            cudaStreamWaitEvent(s, joins[r], 0);
+        }
+        return r0;
+    };
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    *rc = run();  // warm-up (also sets kernel attributes, uploads plans)
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && *rc == MF_OK; rep++) {
+        cudaEventRecord(e0, s);
+        *rc = run();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best / (float)copies;
+}
+
+// Times every candidate of (k, dtype) on the image (src, dst), `copies` at
+// a time (see time_cand), and records the fastest for the image's bucket.
+static int tune_image(const void *src, void *dst, int H, int W, size_t pitch, int channels, int dtype, int k,
+                      cudaStream_t s, int copies) {
+    ImgArgs a;
+    a.src = (const char *)src;
+    a.dst = (char *)dst;
+    a.idx = nullptr;
+    a.H = H;
+    a.y_lo = 0;
+    a.y_hi = H - 1;
+    a.W = W;
+    a.pitch = pitch;
+    a.plane = (size_t)H * pitch;
+    a.idx_pitch = a.idx_plane = 0;
+    std::vector<char *> dsts(copies, (char *)dst);
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    void *scratch = nullptr;
+    const size_t bytes = (size_t)channels * H * pitch;
+    int rc = MF_OK;
+    if (copies > 1) {  // copy r > 0 writes scratch image r - 1
+        if (dev_alloc(&scratch, bytes * (copies - 1)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("autotune: cannot allocate %zu bytes of scratch", bytes * (copies - 1));
+            return MF_ERR_ALLOC;
+        }
+        for (int r = 1; r < copies; r++) dsts[r] = (char *)scratch + bytes * (r - 1);
+        streams.resize(copies);
+        joins.resize(copies);
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        for (int r = 0; r < copies; r++) {
+            cudaStreamCreateWithFlags(&streams[r], cudaStreamNonBlocking);
+            cudaEventCreateWithFlags(&joins[r], cudaEventDisableTiming);
+        }
+    }
+    float best = 1e30f;
+    int best_var = 0, best_tile = 0;
+    const bool verbose = getenv("MF_TUNE_VERBOSE") != nullptr;
+    for (int nth = 0;; nth++) {
+        const O1Entry *o1 = find_o1_nth(k, dtype, false, nth);
+        if (!o1) break;
+        int r;
+        const float ms = time_cand(Cand{o1, 0}, a, channels, k, dtype, s, copies, dsts.data(), streams.data(), fork,
+                                   joins.data(), &r);
+        if (verbose) fprintf(stderr, "mf_autotune k=%d dtype=%d x%d %s: %.4f ms (rc %d)\n", k, dtype, copies, o1->name, ms, r);
+        if (r == MF_OK && ms < best) { best = ms; best_var = MF_OBLIVIOUS; best_tile = nth; }
+    }
+    if (d1_supported(k, dtype, false)) {
+        for (int tile = 2; tile <= 32; tile *= 2) {
+            if (!d1_supported_tile(k, dtype, false, tile)) continue;
+            int r;
+            const float ms = time_cand(Cand{nullptr, tile}, a, channels, k, dtype, s, copies, dsts.data(),
+                                       streams.data(), fork, joins.data(), &r);
+            if (verbose) fprintf(stderr, "mf_autotune k=%d dtype=%d x%d data-aware tile %d: %.4f ms (rc %d)\n", k, dtype, copies, tile, ms, r);
+            if (r == MF_OK && ms < best) { best = ms; best_var = MF_DATA_AWARE; best_tile = tile; }
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    for (cudaStream_t st : streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : joins) cudaEventDestroy(ev);
+    if (fork) cudaEventDestroy(fork);
+    if (scratch) cudaFree(scratch);
+    if (e != cudaSuccess) { set_error("autotune: %s", cudaGetErrorString(e)); return MF_ERR_CUDA; }
+    if (best_var == 0) { set_error("no candidate for k=%d dtype=%d", k, dtype); return MF_ERR_UNSUPPORTED; }
+    tune_record(k, dtype, false, size_bucket((long long)H * W), best_var, best_tile, best);
+    return rc;
+}
+
+int tune_for_batch(const void *src, void *dst, int H, int W, size_t pitch, int channels, int dtype, int k) {
+    // enough concurrent copies for about 8 M output pixels, at most 32
+    const long long px = (long long)H * W * channels;
+    long long copies = (8ll << 20) / (px > 0 ? px : 1);
+    if (copies < 1) copies = 1;
+    if (copies > 32) copies = 32;
+    return tune_image(src, dst, H, W, pitch, channels, dtype, k, nullptr, (int)copies);
 }
 
 }  // namespace mf
@@ -175,43 +277,5 @@ extern "C" int mf_autotune(const void *src, void *dst, int H, int W, size_t pitc
         set_error("bad autotune arguments");
         return MF_ERR_ARG;
     }
-    ImgArgs a;
-    a.src = (const char *)src;
-    a.dst = (char *)dst;
-    a.idx = nullptr;
-    a.H = H;
-    a.y_lo = 0;
-    a.y_hi = H - 1;
-    a.W = W;
-    a.pitch = pitch;
-    a.plane = (size_t)H * pitch;
-    a.idx_pitch = a.idx_plane = 0;
-    cudaStream_t s = (cudaStream_t)stream;
-    float best = 1e30f;
-    int best_var = 0, best_tile = 0;
-    const bool verbose = getenv("MF_TUNE_VERBOSE") != nullptr;
-    for (int nth = 0;; nth++) {
-        const O1Entry *o1 = find_o1_nth(k, dtype, false, nth);
-        if (!o1) break;
-        Cand c{&a, channels, k, dtype, 0, o1, s};
-        int rc;
-        float ms = time_ms(run_cand, &c, s, &rc);
-        if (verbose) fprintf(stderr, "mf_autotune k=%d dtype=%d %s: %.4f ms (rc %d)\n", k, (int)dtype, o1->name, ms, rc);
-        if (rc == MF_OK && ms < best) { best = ms; best_var = MF_OBLIVIOUS; best_tile = nth; }
-    }
-    if (d1_supported(k, dtype, false)) {
-        for (int tile = 2; tile <= 32; tile *= 2) {
-            if (!d1_supported_tile(k, dtype, false, tile)) continue;
-            Cand c{&a, channels, k, dtype, tile, nullptr, s};
-            int rc;
-            float ms = time_ms(run_cand, &c, s, &rc);
-            if (verbose) fprintf(stderr, "mf_autotune k=%d dtype=%d data-aware tile %d: %.4f ms (rc %d)\n", k, (int)dtype, tile, ms, rc);
-            if (rc == MF_OK && ms < best) { best = ms; best_var = MF_DATA_AWARE; best_tile = tile; }
-        }
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) { set_error("autotune: %s", cudaGetErrorString(e)); return MF_ERR_CUDA; }
-    if (best_var == 0) { set_error("no candidate for k=%d dtype=%d", k, (int)dtype); return MF_ERR_UNSUPPORTED; }
-    tune_record(k, dtype, false, size_bucket((long long)H * W), best_var, best_tile, best);
-    return MF_OK;
+    return tune_image(src, dst, H, W, pitch, channels, (int)dtype, k, (cudaStream_t)stream, 1);
 }

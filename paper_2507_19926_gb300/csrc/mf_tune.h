@@ -20,5 +20,10 @@ int tune_tile(int k, int dtype, bool arg, int bucket = -1);
 // True when (k, dtype, arg, bucket) itself has an entry.
 bool tune_has(int k, int dtype, bool arg, int bucket);
 void tune_record(int k, int dtype, bool arg, int bucket, int variant, int tile, float ms);
+// Tunes (k, dtype) for the bucket of an H x W image by throughput: each
+// candidate runs on enough concurrent copies of the image (scratch outputs,
+// allocated here) to fill the GPU, as the classes of a batch do.  dst is
+// written.  Synchronises.
+int tune_for_batch(const void *src, void *dst, int H, int W, size_t pitch, int channels, int dtype, int k);
 
 }  // namespace mf
