@@ -1,6 +1,8 @@
 """Argmedian through the automatic path for every dtype and a range of k:
-record-carrying networks where instantiated, else the value kernel followed
-by the recovery pass (the j-th window element equal to the median in slot
+record-carrying networks where instantiated; for 8/16-bit data above them
+the data-aware merges on (key, footprint index) records; for 32-bit data the
+value kernel followed by the recovery pass (a hash lookup of the median's
+source pixel, or the j-th window element equal to the median in slot
 order, j = m - #below).  Tie-heavy inputs exercise the second pass."""
 import numpy as np
 import pytest
@@ -13,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("dt", ["u8", "u16", "u32", "f32"])
-@pytest.mark.parametrize("k", [11, 17, 25, 27, 31, 45])
+@pytest.mark.parametrize("k", [11, 17, 25, 27, 29, 31, 45, 61, 75])
 def test_auto_argmedian(dt, k):
     for j, gen in enumerate((synth.levels16, synth.uniform)):
         x = gen((2, 41, 77), dt, 5000 + 10 * k + j)
