@@ -36,7 +36,7 @@ namespace mf {
 
 // Merge chunk rule (outputs per work item; each chunk pays one binary search
 // over its two input lists): chunk = clamp(phase outputs / (div * threads),
-// min, 32).  Measured on 4096^2 images, k = 27..75: 2-byte keys do best with
+// min, max).  Measured on 4096^2 images, k = 27..75: 2-byte keys do best with
 // (min 16, div 2), wider keys with (min 12, div 1).  MF_D1_CHUNK="min:div"
 // overrides both (tuning sweeps).
 static const bool D1_ODD_CHUNKS = !getenv("MF_D1_EVEN_CHUNKS");
@@ -66,14 +66,20 @@ static bool d1_balance(int n_win, int key_bytes, bool volume) {
 // 10.4 ms), so off by default.
 static const bool D1_SLABS = getenv("MF_D1_SLABS") && atoi(getenv("MF_D1_SLABS")) != 0;
 
-static void chunk_rule(int key_bytes, int *min_chunk, int *div) {
+static void chunk_rule(int key_bytes, int *min_chunk, int *div, int *max_chunk) {
     *min_chunk = key_bytes <= 2 ? 16 : 12;
     *div = key_bytes <= 2 ? 2 : 1;
-    const char *e = getenv("MF_D1_CHUNK");
-    int a = 0, b = 0;
-    if (e && sscanf(e, "%d:%d", &a, &b) == 2 && a >= 1 && a <= 32 && b >= 1 && b <= 64) {
+    // 1-byte keys: phases with many outputs take chunks of up to 62 (fewer
+    // merge-path searches; u8 k = 61 11.55 -> 10.88 ms, k = 75 15.46 -> 15.02
+    // ms, neutral below); wider keys measured no gain from it
+    *max_chunk = key_bytes == 1 ? 62 : 32;
+    const char *e = getenv("MF_D1_CHUNK");  // "min:div" or "min:div:max" (max < 64: the packed field)
+    int a = 0, b = 0, c = 0;
+    const int n = e ? sscanf(e, "%d:%d:%d", &a, &b, &c) : 0;
+    if (n >= 2 && a >= 1 && a <= 32 && b >= 1 && b <= 64) {
         *min_chunk = a;
         *div = b;
+        if (n == 3 && c >= a && c <= 62) *max_chunk = c;
     }
 }
 
@@ -608,8 +614,8 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
     plan->merge_outputs = plan->sort_elems = 0;
     auto resolve = [&](const Ref &r) { return r.list >= 0 ? B.lists[r.list].off + r.start : (r.list == -1 ? r.start : 0); };
     std::vector<std::vector<int>> by_phase(nph);
-    int min_chunk = 16, div = 1;
-    chunk_rule(key_bytes, &min_chunk, &div);
+    int min_chunk = 16, div = 1, max_chunk = 32;
+    chunk_rule(key_bytes, &min_chunk, &div, &max_chunk);
     for (size_t ti = 0; ti < B.tasks.size(); ti++)
         if (keep[ti]) by_phase[task_phase[ti]].push_back((int)ti);
     for (int p = 0; p < nph; p++) {
@@ -619,7 +625,7 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
             if (B.tasks[ti].type == D1_MERGE) outs_p += B.tasks[ti].hi - B.tasks[ti].lo + 1;
         // about one chunk per thread: phases with few outputs (the upper tree
         // levels) get short chunks so the whole block shares them
-        int chunk = (int)std::min<long long>(32, std::max<long long>(min_chunk, outs_p / ((long long)div * nt)));
+        int chunk = (int)std::min<long long>(max_chunk, std::max<long long>(min_chunk, outs_p / ((long long)div * nt)));
         // the chunks of one merge run on consecutive threads: an odd number of
         // 4-byte words between their output runs spreads a warp's stores
         // (and its roughly proportional input reads) over all 32 banks
