@@ -3,6 +3,7 @@
 // the paper's introduction (Sec. 1); the kernels live in mf_oblivious.cuh
 // (Sec. 4) and mf_data_aware.cu (Sec. 5).
 #include <atomic>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -45,6 +46,15 @@ const O1Entry *find_o1_nth(int k, int dtype, bool arg, int nth) {
         if (kO1Entries[i].k == k && kO1Entries[i].dtype == dtype && kO1Entries[i].arg == (arg ? 1 : 0))
             if (nth-- == 0) return &kO1Entries[i];
     return nullptr;
+}
+
+const O1Entry *o1_for_image(const O1Entry *e, const ImgArgs &a) {
+    if (!e || e->run <= 1 || (((uintptr_t)a.src | (uintptr_t)a.dst | (uintptr_t)a.pitch) & 15) == 0) return e;
+    for (int nth = 0;; nth++) {
+        const O1Entry *f = find_o1_nth(e->k, e->dtype, e->arg != 0, nth);
+        if (!f) return e;  // none: the wide form's own element-by-element path
+        if (f->run <= 1) return f;
+    }
 }
 
 const O1Entry *find_o1(int k, int dtype, bool arg, int bucket) {
@@ -159,8 +169,9 @@ static int launch_resolved(const ImgArgs &a, int C, int k, int dtype, int varian
     int rc = resolve(k, dtype, a.idx != nullptr, variant, &p, size_bucket((long long)a.H * a.W));
     if (rc) return rc;
     if (p.variant == MF_OBLIVIOUS) {
-        rc = p.o1->launch(a, C, s);
-        if (rc == MF_ERR_CUDA) set_error("%s: %s", p.o1->name, cudaGetErrorString(cudaGetLastError()));
+        const O1Entry *e = o1_for_image(p.o1, a);
+        rc = e->launch(a, C, s);
+        if (rc == MF_ERR_CUDA) set_error("%s: %s", e->name, cudaGetErrorString(cudaGetLastError()));
         return rc;
     }
     return d1_launch(a, C, k, dtype, p.tile, s);

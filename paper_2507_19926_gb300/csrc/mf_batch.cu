@@ -13,6 +13,8 @@
 // the largest networks need all 255 registers of a thread, which would
 // otherwise throttle every small-k class too.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -138,6 +140,13 @@ extern "C" int mf_batch_plan_create_ex(const mf_image_desc *descs, int n, int tu
         int tile = 0;
         const int var = resolve_variant(d.k, d.dtype, false, MF_AUTO, &o1, size_bucket((long long)d.H * d.W), &tile);
         if (var < 0) { destroy_plan(p); return var; }
+        if (var == MF_OBLIVIOUS) {  // wide forms need 16-byte aligned rows
+            ImgArgs t{};
+            t.src = (const char *)d.src;
+            t.dst = (char *)d.dst;
+            t.pitch = d.pitch;
+            o1 = o1_for_image(o1, t);
+        }
         if (var == MF_OBLIVIOUS && !o1->persist) { set_error("no persistent form for k=%d", d.k); destroy_plan(p); return MF_ERR_UNSUPPORTED; }
         const long long which = var == MF_OBLIVIOUS ? (long long)(o1 - kO1Entries) : (long long)tile;
         auto key = std::make_tuple(var, which, d.k, (int)d.dtype);
@@ -166,6 +175,15 @@ extern "C" int mf_batch_plan_create_ex(const mf_image_desc *descs, int n, int tu
                 for (int bx = 0; bx < gx; bx++) c.items.push_back(make_int4(i, bx, by, z));
     }
 
+    if (getenv("MF_BATCH_VERBOSE")) {  // the plan's kernel classes, one line each
+        for (auto &kv : classes) {
+            const BatchClass &c = kv.second;
+            const long long px = (long long)c.items.size() * c.rw * c.rh;
+            fprintf(stderr, "batch class k=%d dtype=%d %s items=%zu region=%dx%d px~%lld\n", c.k, c.dtype,
+                    c.variant == MF_OBLIVIOUS ? c.o1->name : "data-aware", c.items.size(), c.rw, c.rh, px);
+            if (c.variant != MF_OBLIVIOUS) fprintf(stderr, "  data-aware tile %d\n", c.tile);
+        }
+    }
     // device memory: image arguments, one counter per class, the item lists
     const size_t nclass = classes.size();
     size_t nitems = 0;

@@ -323,6 +323,11 @@ int d1_default_tile(int k, int dtype, bool arg, int kh, int bucket) {
     const int tuned =
         square && tune_lookup(k, dtype, arg, bucket) == MF_DATA_AWARE ? tune_tile(k, dtype, arg, bucket) : 0;
     if (tuned && d1_supported_tile(k, dtype, arg, tuned)) return tuned;
+    return d1_heuristic_tile(k, dtype, arg, kh);
+}
+
+int d1_heuristic_tile(int k, int dtype, bool arg, int kh) {
+    const bool square = kh == 0 || kh == k;
     // root-tile heuristic t(k) = 2^(floor(log2 k) - 1) (paper Sec. 4.2) on
     // the shorter window side, at least 2 (1 for a window one pixel wide or
     // high) and at most 16, lowered until the tree's state fits in shared

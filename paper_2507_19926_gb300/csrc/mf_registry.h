@@ -37,6 +37,12 @@ int d1_supported(int k, int dtype, bool arg);
 // kh: window height for a k-wide, kh-high window (0: k x k)
 int d1_launch(const ImgArgs &a, int channels, int k, int dtype, int tile, cudaStream_t s, int kh = 0);
 int d1_default_tile(int k, int dtype, bool arg, int kh = 0, int bucket = -1);
+// The root tile of the paper's heuristic (no tuning table): 0 if none fits.
+int d1_heuristic_tile(int k, int dtype, bool arg, int kh = 0);
+// The configuration to run on image a: e itself, unless e is a wide form
+// (vector row loads) and a's rows are not 16-byte aligned, where the first
+// configuration of the same (k, dtype) that reads element by element runs.
+const O1Entry *o1_for_image(const O1Entry *e, const ImgArgs &a);
 int d1_supported_tile(int k, int dtype, bool arg, int tile, int kh = 0);
 int d1_describe(int k, int dtype, bool arg, int tile, char *buf, size_t n);
 void d1_release_all();

@@ -124,6 +124,13 @@ extern "C" int mf_batch_run_static(const mf_image_desc *descs, int n, mf_stream_
         if (d.k == 1) continue;
         const O1Entry *o1 =
             (d.k >= 3 && (d.k & 1)) ? find_o1(d.k, d.dtype, false, size_bucket((long long)d.H * d.W)) : nullptr;
+        if (o1) {  // wide forms need 16-byte aligned rows
+            ImgArgs t{};
+            t.src = (const char *)d.src;
+            t.dst = (char *)d.dst;
+            t.pitch = d.pitch;
+            o1 = o1_for_image(o1, t);
+        }
         if (!o1 || !o1->persist) {
             set_error("image %d: the static batch runs only the data-oblivious kernels, not built for k = %d "
                       "with this dtype", i, d.k);

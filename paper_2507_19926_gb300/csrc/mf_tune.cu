@@ -224,8 +224,15 @@ static int tune_image(const void *src, void *dst, int H, int W, size_t pitch, in
             cudaEventCreateWithFlags(&joins[r], cudaEventDisableTiming);
         }
     }
-    float best = 1e30f;
+    float best = 1e30f, def_ms = 1e30f;
     int best_var = 0, best_tile = 0;
+    // the choice without a table entry: the first network configuration
+    // (the element-by-element one for unaligned rows), else the heuristic
+    // data-aware tile; a candidate must beat it by 5% to replace it, so
+    // that timing noise does not trade good defaults for equal ones
+    const O1Entry *o1_def = o1_for_image(find_o1_nth(k, dtype, false, 0), a);
+    const int d1_def = o1_def ? 0 : d1_heuristic_tile(k, dtype, false);
+    int def_var = o1_def ? MF_OBLIVIOUS : MF_DATA_AWARE, def_tile = 0;
     const bool verbose = getenv("MF_TUNE_VERBOSE") != nullptr;
     for (int nth = 0;; nth++) {
         const O1Entry *o1 = find_o1_nth(k, dtype, false, nth);
@@ -235,6 +242,7 @@ static int tune_image(const void *src, void *dst, int H, int W, size_t pitch, in
                                    joins.data(), &r);
         if (verbose) fprintf(stderr, "mf_autotune k=%d dtype=%d x%d %s: %.4f ms (rc %d)\n", k, dtype, copies, o1->name, ms, r);
         if (r == MF_OK && ms < best) { best = ms; best_var = MF_OBLIVIOUS; best_tile = nth; }
+        if (r == MF_OK && o1 == o1_def) { def_ms = ms; def_tile = nth; }
     }
     if (d1_supported(k, dtype, false)) {
         for (int tile = 2; tile <= 32; tile *= 2) {
@@ -244,7 +252,13 @@ static int tune_image(const void *src, void *dst, int H, int W, size_t pitch, in
                                        streams.data(), fork, joins.data(), &r);
             if (verbose) fprintf(stderr, "mf_autotune k=%d dtype=%d x%d data-aware tile %d: %.4f ms (rc %d)\n", k, dtype, copies, tile, ms, r);
             if (r == MF_OK && ms < best) { best = ms; best_var = MF_DATA_AWARE; best_tile = tile; }
+            if (r == MF_OK && !o1_def && tile == d1_def) { def_ms = ms; def_tile = tile; }
         }
+    }
+    if (best_var && def_ms < 1e29f && !(best < 0.95f * def_ms)) {  // keep the default
+        best = def_ms;
+        best_var = def_var;
+        best_tile = def_tile;
     }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaGetLastError();

@@ -111,20 +111,26 @@ def test_every_configuration(dt, k):
     import paper_2507_19926_gb300 as mf
     from gpu_util import ensure_lib, to_dev, to_host
     ensure_lib()
-    x = synth.levels16((2, 45, 290), dt, 3000 + k)
-    want = oracle.median_filter(x, k)
-    xd = to_dev(x)
-    n = 0
-    for config in range(16):
-        yd = torch.empty_like(xd)
-        _, H, W, pitch = mf._planes(xd)
-        try:
-            mf.mf_median_filter_config(xd.data_ptr(), yd.data_ptr(), H, W, pitch, 2, mf.DTYPE_CODES[dt], k, config,
-                                       torch.cuda.current_stream().cuda_stream)
-        except mf.MedianFilterError as e:
-            assert e.status == mf.MF_ERR_UNSUPPORTED and config > 0, e
-            break
-        torch.cuda.synchronize()
-        assert same_bits(to_host(yd, None), want), (dt, k, config)
-        n += 1
+    # rows of 290 elements (not 16-byte aligned: the wide forms read element
+    # by element), and 500 of 512-element rows (aligned: the wide forms'
+    # vector loads, with a ragged right edge)
+    for shape, padw in (((2, 45, 290), 0), ((2, 37, 500), 12)):
+        x = synth.levels16(shape, dt, 3000 + k + padw)
+        want = oracle.median_filter(x, k)
+        big = to_dev(np.pad(x, ((0, 0), (0, 0), (0, padw))))
+        xd = big[:, :, :shape[2]]
+        n = 0
+        for config in range(16):
+            yd = torch.zeros_like(big)
+            _, H, W, pitch = mf._planes(xd)
+            try:
+                mf.mf_median_filter_config(xd.data_ptr(), yd.data_ptr(), H, W, pitch, 2, mf.DTYPE_CODES[dt], k,
+                                           config, torch.cuda.current_stream().cuda_stream)
+            except mf.MedianFilterError as e:
+                assert e.status == mf.MF_ERR_UNSUPPORTED and config > 0, e
+                break
+            torch.cuda.synchronize()
+            got = to_host(yd, None)
+            assert same_bits(np.ascontiguousarray(got[:, :, :shape[2]]), want), (dt, k, config, shape)
+            n += 1
     assert n >= 1
