@@ -152,7 +152,43 @@ def _o1_instances():
     return out
 
 
+def _gen_key():
+    """Hash of everything the generated sources depend on: the instantiation
+    tables, the generator switches and the package's Python sources."""
+    h = hashlib.sha1()
+    h.update(repr((sorted(O1_VALUE.items()), sorted(O1_ARG32.items()), sorted(O1_ARG64.items()), O1_ROLLED,
+                   O1_FUSE3, O1_MAD_SELECT, O1_SYNC_EVERY)).encode())
+    for name in sorted(os.listdir(HERE)):
+        if name.endswith(".py"):
+            with open(os.path.join(HERE, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()
+
+
 def generate():
+    """Writes the generated translation units and headers into _build/gen and
+    returns the translation units; skipped (the recorded list returned) when
+    nothing they depend on changed since the last run."""
+    import json
+    stamp = os.path.join(GEN, ".stamp.json")
+    key = _gen_key()
+    try:
+        with open(stamp) as f:
+            rec = json.load(f)
+        tus = [os.path.join(GEN, n) for n in rec["tus"]]
+        heads = [os.path.join(GEN, n) for n in ("d1_sortnets.cuh", "d3_nets.cuh")]
+        if rec["key"] == key and all(os.path.exists(t) for t in tus + heads):
+            return tus
+    except (OSError, ValueError, KeyError):
+        pass
+    tus = _generate()
+    with open(stamp, "w") as f:
+        json.dump({"key": key, "tus": [os.path.basename(t) for t in tus]}, f)
+    return tus
+
+
+def _generate():
     os.makedirs(GEN, exist_ok=True)
     for name in os.listdir(GEN):
         if name.startswith("o1_k") and name.endswith(".cu"):
@@ -281,23 +317,16 @@ def kernel_source_hash(fn_name):
 
 
 def _flags_hash(src, flags):
+    """Hash of the flags, the translation unit and every file it includes
+    (transitively): a TU is rebuilt only when something it reads changed."""
     h = hashlib.sha1()
     h.update(" ".join(flags).encode())
-    with open(src, "rb") as f:
-        h.update(f.read())
-    # headers of csrc affect every TU
-    for name in sorted(os.listdir(CSRC)):
-        if name.endswith((".cuh", ".h")):
-            with open(os.path.join(CSRC, name), "rb") as f:
-                h.update(f.read())
-    for name in sorted(os.listdir(INCLUDE)):
-        if name.endswith(".h"):
-            with open(os.path.join(INCLUDE, name), "rb") as f:
-                h.update(f.read())
-    for name in sorted(os.listdir(GEN)):
-        if name.endswith(".cuh"):
-            with open(os.path.join(GEN, name), "rb") as f:
-                h.update(f.read())
+    files = []
+    _includes(src, files)
+    for fp in files:
+        h.update(fp.encode())
+        with open(fp, "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 

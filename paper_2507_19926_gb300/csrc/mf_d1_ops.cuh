@@ -9,6 +9,11 @@
 // Sort: short lists (the sorted column/row segments and the corner runs)
 // are sorted by one thread with a sorting network held in registers, as the
 // paper recommends for many small sorts (Sec. 5.1).
+// Insert: an extra row or column extended by the 1, 2 or 4 corners of a
+// split (Sec. 3.4) is a merge with a very short second list; one thread
+// moves every list element up by the number of corners below it and drops
+// the corners into the gaps, reading the list in order (no merge-path
+// search, no data-dependent read addresses).
 #pragma once
 #include <cstdint>
 
@@ -28,9 +33,10 @@ __host__ __device__ __forceinline__ KT d1_sentinel() {
 }
 
 // 16-byte device form of a task (one 128-bit load):
-//   x = a_off | type << 17 | (a_stride == FW) << 18 | chunk << 19
+//   x = a_off | (type & 1) << 17 | (gather stride == FW) << 18 | chunk << 19 | (type == INSERT) << 25
 //   y = b_off | a_len << 17,  z = out_off | b_len << 17,  w = lo | hi << 13
-// Offsets < 2^17 list elements, lengths and ranks < 2^13, chunk < 64.
+// Offsets < 2^17 list elements, lengths and ranks < 2^13, chunk < 64.  The
+// gather stride is the SORT's a_stride or the INSERT's b_stride.
 struct D1Packed {
     uint32_t x, y, z, w;
 };
@@ -38,9 +44,10 @@ struct D1Packed {
 __host__ __device__ __forceinline__ D1Task d1_unpack(const D1Packed &p, int FW) {
     D1Task t;
     t.a_off = (int)(p.x & 0x1ffffu);
-    t.type = (int)((p.x >> 17) & 1u);
+    t.type = ((p.x >> 25) & 1u) ? D1_INSERT : (int)((p.x >> 17) & 1u);
     t.a_stride = ((p.x >> 18) & 1u) ? FW : 1;
-    t.chunk = (int)(p.x >> 19);
+    t.b_stride = t.a_stride;
+    t.chunk = (int)((p.x >> 19) & 63u);
     t.b_off = (int)(p.y & 0x1ffffu);
     t.a_len = (int)(p.y >> 17);
     t.out_off = (int)(p.z & 0x1ffffu);
@@ -52,6 +59,18 @@ __host__ __device__ __forceinline__ D1Task d1_unpack(const D1Packed &p, int FW) 
 
 // Outputs lo + chunk*t.chunk ... (up to t.chunk of them, not past hi) of
 // merge(A, B) into out[(p - lo)].
+//
+// Every list is followed in shared memory by a sentinel slot holding the
+// largest key (the plan allocates it, the list's producer writes it), so
+// the element after a merge input is either that sentinel or, where the
+// input is a leading part of a longer list, the list's next element, which
+// ranks after every output of the task (it is never taken).  The loop
+// therefore needs no bounds tests: B's sentinel is never taken (a <= it
+// always), and A's index is held at its end, so that with A exhausted and B
+// at the largest key (equal values: the same output) the merge keeps
+// emitting that key without reading past A's sentinel (B's register then
+// stays at that key, which is every remaining output).  The last chunk
+// writes the output list's own sentinel.
 template <class KT>
 __host__ __device__ __forceinline__ void d1_merge_chunk(KT *sm, const D1Task &t, int chunk) {
     const KT *A = sm + t.a_off;
@@ -69,22 +88,85 @@ __host__ __device__ __forceinline__ void d1_merge_chunk(KT *sm, const D1Task &t,
         if (A[mid] <= B[p0 - 1 - mid]) lo = mid + 1;
         else hi = mid;
     }
-    int i = lo, j = p0 - lo;
+    int i = lo;
     KT *out = sm + t.out_off + (p0 - t.lo);
-    // branch-free: the index of an exhausted list is clamped to its last
-    // element and never chosen again (ta is forced by the length tests)
-    const int ia = na - 1, jb = nb - 1;
-    KT a = A[i < ia ? i : ia];
-    KT b = B[j < jb ? j : jb];
+    KT a = A[i], b = B[p0 - i];
 #pragma unroll 4
     for (int n = 0; n < cnt; n++) {
-        const bool ta = (j > jb) || (i <= ia && a <= b);
+        const bool ta = a <= b;
         out[n] = ta ? a : b;
         i += ta;
-        j += !ta;
-        a = A[i < ia ? i : ia];
-        b = B[j < jb ? j : jb];
+        i = i < na ? i : na;
+        // only the list that advanced needs its next element: one
+        // shared-memory read a step (the kernel is bound by shared-memory
+        // wavefronts; 4096^2 u32 k = 45 12.84 -> 12.26 ms against reading both)
+        const KT v = ta ? A[i] : B[p0 + n + 1 - i];
+        a = ta ? v : a;
+        b = ta ? b : v;
     }
+    if (p0 + cnt - 1 == t.hi) out[cnt] = d1_sentinel<KT>();
+}
+
+template <class KT>
+__host__ __device__ __forceinline__ void d1_cx(KT &a, KT &b) {
+    const KT lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+
+// out[0 .. n+C) = merge(L, sorted corners), L = sm[a_off .. a_off+n) sorted,
+// corners gathered at b_off + q*b_stride.  Ties keep L first, as the merge
+// does.  L element i lands at i + #(corners below it); corner q (in sorted
+// order) at q + i*_q, i*_q = #(L elements not above it).  Work item `chunk`
+// moves the L elements i0 = chunk*t.chunk .. i1 (t.chunk = 0: all of them)
+// and places the corners whose i*_q falls in [i0, i1) (or at n, for the
+// last item): there i*_q = i1 - #(elements of the item above corner q).
+template <class KT, int C>
+__host__ __device__ __forceinline__ void d1_insert(KT *sm, const D1Task &t, int chunk) {
+    KT s[C];
+#pragma unroll
+    for (int q = 0; q < C; q++) s[q] = sm[t.b_off + q * t.b_stride];
+    if constexpr (C == 2) {
+        d1_cx(s[0], s[1]);
+    } else if constexpr (C == 4) {
+        d1_cx(s[0], s[1]);
+        d1_cx(s[2], s[3]);
+        d1_cx(s[0], s[2]);
+        d1_cx(s[1], s[3]);
+        d1_cx(s[1], s[2]);
+    }
+    const KT *L = sm + t.a_off;
+    KT *out = sm + t.out_off;
+    const int n = t.a_len;
+    const int i0 = t.chunk ? chunk * t.chunk : 0;
+    const int i1 = t.chunk && i0 + t.chunk < n ? i0 + t.chunk : n;
+    int above[C];
+#pragma unroll
+    for (int q = 0; q < C; q++) above[q] = 0;
+#pragma unroll 4
+    for (int i = i0; i < i1; i++) {
+        const KT x = L[i];
+        int d = 0;
+#pragma unroll
+        for (int q = 0; q < C; q++) {
+            const int g = s[q] < x;
+            d += g;
+            above[q] += g;
+        }
+        out[i + d] = x;
+    }
+    const KT before = i0 > 0 ? L[i0 - 1] : L[0], last = L[i1 - 1];
+#pragma unroll
+    for (int q = 0; q < C; q++)
+        if ((i0 == 0 || before <= s[q]) && (i1 == n || s[q] < last)) out[q + i1 - above[q]] = s[q];
+    if (i1 == n) out[n + C] = d1_sentinel<KT>();
+}
+
+template <class KT>
+__host__ __device__ __forceinline__ void d1_insert_any(KT *sm, const D1Task &t, int chunk) {
+    if (t.b_len == 1) d1_insert<KT, 1>(sm, t, chunk);
+    else if (t.b_len == 2) d1_insert<KT, 2>(sm, t, chunk);
+    else d1_insert<KT, 4>(sm, t, chunk);
 }
 
 }  // namespace mf

@@ -66,6 +66,23 @@ static bool d1_balance(int n_win, int key_bytes, bool volume) {
 // 10.4 ms), so off by default.
 static const bool D1_SLABS = getenv("MF_D1_SLABS") && atoi(getenv("MF_D1_SLABS")) != 0;
 
+// Longest corner run extended by an INSERT task (0: every extension is a
+// sort plus a merge); MF_D1_INSERT overrides it (sweeps).
+static int d1_insert_max() {
+    static const int v = getenv("MF_D1_INSERT") ? std::min(atoi(getenv("MF_D1_INSERT")), D1_MAX_INSERT) : D1_MAX_INSERT;
+    return v;
+}
+// An INSERT moves chunks of this many times the phase's merge chunk; 0:
+// one item per INSERT.  Swept on 4096^2 images (factors 0-3): one item for
+// 1- and 2-byte keys (u8 k = 45 6.95 -> 6.63 ms, k = 75 14.73 -> 14.23 ms,
+// u16 k = 45 8.75 -> 8.27 ms against factor 1), factor 1 for wider keys,
+// whose smaller merge chunks keep the phases short (u32 k = 31 8.78 -> 8.38
+// ms).  MF_D1_INSERT_CHUNK overrides it (sweeps).
+static int d1_insert_chunk_factor(int key_bytes) {
+    static const int v = getenv("MF_D1_INSERT_CHUNK") ? atoi(getenv("MF_D1_INSERT_CHUNK")) : -1;
+    return v >= 0 ? v : (key_bytes <= 2 ? 0 : 1);
+}
+
 static void chunk_rule(int key_bytes, int *min_chunk, int *div, int *max_chunk) {
     *min_chunk = key_bytes <= 2 ? 16 : 12;
     *div = key_bytes <= 2 ? 2 : 1;
@@ -99,6 +116,7 @@ struct PTask {
     int lo, hi;
     int out;    // output list id
     int phase;
+    int b_stride;  // INSERT: gather stride of the corners
 };
 
 struct ListInfo {
@@ -111,6 +129,8 @@ struct ListInfo {
 
 struct Builder {
     int k, T, FW;  // k: window width
+    // longest corner run an INSERT takes (0: none)
+    int insert_max = D1_MAX_INSERT;
     std::vector<ListInfo> lists;
     std::vector<PTask> tasks;
 
@@ -160,6 +180,20 @@ struct Builder {
     }
 
     Ref merge_full(const Ref &A, const Ref &B) { return merge_range(A, B, 0, A.len + B.len - 1); }
+
+    // Sorted list `row` extended by the h footprint elements at f_off +
+    // i*stride (Sec. 3.4: the corners a split adds to an extra row or
+    // column).  Up to insert_max corners: one INSERT task gathering them
+    // from the footprint; more: a sort and a merge.
+    Ref extend(const Ref &row, int f_off, int stride, int h) {
+        if (h > insert_max || row.len == 0) return merge_full(row, sort_gather(f_off, stride, h));
+        const Ref corners{-1, f_off, h};
+        const int phase = 1 + phase_of(row);
+        const int n = row.len + h;
+        const int id = new_list(n, phase);
+        tasks.push_back(PTask{D1_INSERT, row, 0, corners, 0, n - 1, id, phase, stride});
+        return Ref{id, 0, n};
+    }
 
     // Ranks lo..hi of the union of sorted lists: balanced tree of two-way
     // merges, each restricted to the ranks that can reach lo..hi (a rank-j
@@ -227,6 +261,11 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
     B.k = kw;
     B.T = TW;
     B.FW = NB * TW + kw - 1;
+    // Plans with phase balancing keep extensions as sorts plus merges: an
+    // INSERT keeps the footprint resident until its phase, and with corners
+    // from sorted lists instead the inserts measured slower than the merges
+    // (u16 k = 75 20.0 -> 20.9 ms, u32 k = 45 12.9 -> 13.3 ms at 4096^2)
+    B.insert_max = d1_balance(n_win, key_bytes, false) ? 0 : d1_insert_max();
     const int FW = B.FW, FH = TH + kh - 1;
     // sorted column segments over the root core rows, for every footprint
     // column of the strip: horizontally adjacent root tiles share them
@@ -349,10 +388,7 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
                         const Ref extra = B.multiway(nc, 0, 1 << 30);
                         ncore[j][2 * i + s] = B.merge_range(core[j][i], extra, lo, hi);
                     }
-                    for (auto &kv : rows[i]) {
-                        const Ref corners = B.sort_gather(F(kv.first, nx0), 1, h);
-                        nrows[2 * i + s][kv.first] = B.merge_full(kv.second, corners);
-                    }
+                    for (auto &kv : rows[i]) nrows[2 * i + s][kv.first] = B.extend(kv.second, F(kv.first, nx0), 1, h);
                 }
             }
             core.swap(ncore);
@@ -377,10 +413,7 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
                         const Ref extra = B.multiway(nr, 0, 1 << 30);
                         ncore[2 * j + s][i] = B.merge_range(core[j][i], extra, lo, hi);
                     }
-                    for (auto &kv : cols[j]) {
-                        const Ref corners = B.sort_gather(F(ny0, kv.first), FW, h);
-                        ncols[2 * j + s][kv.first] = B.merge_full(kv.second, corners);
-                    }
+                    for (auto &kv : cols[j]) ncols[2 * j + s][kv.first] = B.extend(kv.second, F(ny0, kv.first), FW, h);
                 }
             }
             core.swap(ncore);
@@ -418,6 +451,8 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
         if (r.list >= 0) B.lists[r.list].needed = true;
     }
     std::vector<bool> keep(B.tasks.size(), false);
+    for (const PTask &t : B.tasks)  // merges read lists only (each has its sentinel slot)
+        if (t.type == D1_MERGE && (t.a.list < 0 || t.b.list < 0)) return false;
     for (int ti = (int)B.tasks.size() - 1; ti >= 0; ti--) {
         const PTask &t = B.tasks[ti];
         if (!B.lists[t.out].needed) continue;
@@ -471,7 +506,7 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
         // cost in merged-element units: a merge costs its outputs, a sort of
         // n elements about n (log2 n)^2 / 8 (a register sorting network)
         auto cost = [&](const PTask &t) -> double {
-            if (t.type == D1_MERGE) return t.hi - t.lo + 1;
+            if (t.type != D1_SORT) return t.hi - t.lo + 1;
             const double n = t.a.len, l = std::log2(std::max(2.0, n));
             return n * std::max(1.0, l * l / 8);
         };
@@ -558,7 +593,29 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
     // ---------------------------------------------------------- allocation
     // first fit over a free list, phase by phase; the footprint sits at 0
     std::vector<std::pair<int, int>> freel;  // (off, len), sorted by off
-    int top = base;
+    // List sizes: the list, its sentinel slot (largest key) that its producer
+    // writes -- merges read one element past their inputs -- and, except
+    // for 2-byte keys at 41 <= k < 61, padding to a whole, odd number of
+    // 4-byte words (1- and 2-byte keys: lists start on a word).  Threads
+    // stepping through consecutive lists in lockstep then hit distinct
+    // banks: fewer bank-conflict replays (4096^2, u8 k = 31 4.40 -> 4.08 ms,
+    // u16 k = 31 5.91 -> 5.55 ms, u32 k = 31 8.72 -> 8.30 ms; u16 k = 45
+    // measured 8.12 -> 8.48 ms, so it keeps unpadded lists).
+    const int kwin2 = B.k * B.k;  // (width squared: the rule is stated in k)
+    const bool oddw = !(key_bytes == 2 && kwin2 >= 41 * 41 && kwin2 < 61 * 61);
+    const int al = oddw && key_bytes < 4 ? 4 / key_bytes : 1;
+    auto rnd = [&](int n) { return (n + al - 1) / al * al; };
+    auto lsz = [&](int len) {
+        int n = rnd(len + 1);
+        if (oddw && key_bytes <= 4) {
+            const int per = 4 / key_bytes;  // elements a word
+            int words = (n * key_bytes + 3) / 4;
+            if (!(words & 1)) words++;
+            n = std::max(n, words * per);
+        }
+        return n;
+    };
+    int top = rnd(base);
     std::vector<std::vector<int>> prod(nph + 1), dies(nph + 2);
     for (size_t li = 0; li < B.lists.size(); li++) {
         if (lphase[li] < 0) continue;
@@ -596,12 +653,54 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
         top += len;
         return off;
     };
-    for (int p = 0; p <= nph; p++) {
-        // the footprint is free once its last reader has run
-        if (balance && p == foot_last + 1 && base > 0) release(0, base);
-        for (int li : dies[p]) release(B.lists[li].off, B.lists[li].len);
-        if (p < nph)
-            for (int li : prod[p]) B.lists[li].off = alloc(B.lists[li].len);
+    if (balance) {
+        // Balanced plans free lists in every phase: pack the lists as
+        // rectangles (phases x elements), largest first, each at the lowest
+        // offset clear of every list live in an overlapping phase.  First
+        // fit phase by phase fragmented these plans by up to a third (u32
+        // k = 75, 8 x 8 tile: 115.5 -> 89.5 KB, two blocks a SM again: 50.5
+        // -> 33.6 ms at 4096^2).
+        struct Box {
+            int off, end, t0, t1;
+        };
+        std::vector<Box> placed;
+        placed.push_back(Box{0, rnd(base), 0, std::max(foot_last, 0)});
+        std::vector<int> order;
+        for (size_t li = 0; li < B.lists.size(); li++)
+            if (lphase[li] >= 0) order.push_back((int)li);
+        auto t1_of = [&](int li) { return std::max(last[li], lphase[li]); };
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            const int sx = lsz(B.lists[x].len), sy = lsz(B.lists[y].len);
+            if (sx != sy) return sx > sy;
+            return t1_of(x) - lphase[x] > t1_of(y) - lphase[y];
+        });
+        top = rnd(base);
+        std::vector<std::pair<int, int>> busy;
+        for (int li : order) {
+            const int t0 = lphase[li], t1 = t1_of(li), sz = lsz(B.lists[li].len);
+            busy.clear();
+            for (const Box &b : placed)
+                if (b.t0 <= t1 && t0 <= b.t1) busy.push_back({b.off, b.end});
+            std::sort(busy.begin(), busy.end());
+            int off = 0;
+            for (auto &b : busy) {
+                if (off + sz <= b.first) break;
+                off = std::max(off, b.second);
+            }
+            B.lists[li].off = off;
+            placed.push_back(Box{off, off + sz, t0, t1});
+            top = std::max(top, off + sz);
+        }
+    } else {
+        for (int p = 0; p <= nph; p++) {
+            // the footprint is free once its last reader has run
+            if (balance && p == foot_last + 1 && base > 0) release(0, rnd(base));
+            // every list is followed by a sentinel slot (largest key) that its
+            // producer writes: merges read one element past their inputs
+            for (int li : dies[p]) release(B.lists[li].off, lsz(B.lists[li].len));
+            if (p < nph)
+                for (int li : prod[p]) B.lists[li].off = alloc(lsz(B.lists[li].len));
+        }
     }
 
     // ---------------------------------------------------------- emit
@@ -622,16 +721,16 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
         plan->phase_begin.push_back((int)plan->work.size());
         long long outs_p = 0;
         for (int ti : by_phase[p])
-            if (B.tasks[ti].type == D1_MERGE) outs_p += B.tasks[ti].hi - B.tasks[ti].lo + 1;
+            if (B.tasks[ti].type != D1_SORT) outs_p += B.tasks[ti].hi - B.tasks[ti].lo + 1;
         // about one chunk per thread: phases with few outputs (the upper tree
         // levels) get short chunks so the whole block shares them
         int chunk = (int)std::min<long long>(max_chunk, std::max<long long>(min_chunk, outs_p / ((long long)div * nt)));
         // the chunks of one merge run on consecutive threads: an odd number of
         // 4-byte words between their output runs spreads a warp's stores
         // (and its roughly proportional input reads) over all 32 banks
-        // (8- and 16-bit keys: 2 mod 4 elements, measured the same for both;
-        // wider keys: odd)
-        if (D1_ODD_CHUNKS) chunk = key_bytes <= 2 ? (chunk & ~3) + 2 : (chunk | 1);
+        // (8-bit keys: 4 mod 8 elements, 16-bit keys: 2 mod 4, wider keys:
+        // odd)
+        if (D1_ODD_CHUNKS) chunk = key_bytes == 1 ? (chunk & ~7) + 4 : key_bytes == 2 ? (chunk & ~3) + 2 : (chunk | 1);
         // sorts first, grouped by size class, then merges
         std::vector<int> order = by_phase[p];
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -649,6 +748,7 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
             o.a_stride = t.a_stride;
             o.b_off = resolve(t.b);
             o.b_len = t.b.len;
+            o.b_stride = t.type == D1_INSERT ? t.b_stride : 1;
             o.lo = t.lo;
             o.hi = t.hi;
             o.out_off = B.lists[t.out].off;
@@ -658,6 +758,13 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
                 plan->work.push_back((uint32_t)tid << 12);
                 plan->max_sort = std::max(plan->max_sort, t.a.len);
                 plan->sort_elems += t.a.len;
+            } else if (t.type == D1_INSERT) {
+                // chunks over the list elements, as long as the phase's merge chunks
+                const int n = t.a.len, f = d1_insert_chunk_factor(key_bytes);
+                o.chunk = f > 0 ? std::min(std::min(f * chunk, 62), n) : 0;
+                const int nchunks = o.chunk ? (n + o.chunk - 1) / o.chunk : 1;
+                for (int cidx = 0; cidx < nchunks; cidx++) plan->work.push_back(((uint32_t)tid << 12) | (uint32_t)cidx);
+                plan->merge_outputs += t.hi - t.lo + 1;
             } else {
                 const int n = t.hi - t.lo + 1;
                 o.chunk = std::min(chunk, n);
@@ -675,7 +782,8 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
     for (const D1Task &t : plan->tasks)
         if (t.a_off >= (1 << 17) || t.b_off >= (1 << 17) || t.out_off >= (1 << 17) || t.a_len >= (1 << 13) ||
             t.b_len >= (1 << 13) || t.lo >= (1 << 13) || t.hi >= (1 << 13) || t.chunk >= 64 ||
-            (t.type == D1_SORT && t.a_stride != 1 && t.a_stride != plan->FW))
+            (t.type == D1_SORT && t.a_stride != 1 && t.a_stride != plan->FW) ||
+            (t.type == D1_INSERT && (t.b_len > D1_MAX_INSERT || (t.b_stride != 1 && t.b_stride != plan->FW))))
             return false;
     return plan->tasks.size() < (1u << 20);
 }
@@ -874,8 +982,9 @@ void d1_pack_tasks(const D1Plan &plan, std::vector<D1Packed> *out) {
     for (size_t i = 0; i < plan.tasks.size(); i++) {
         const D1Task &t = plan.tasks[i];
         D1Packed &p = (*out)[i];
-        p.x = (uint32_t)t.a_off | (uint32_t)t.type << 17 | (uint32_t)(t.type == D1_SORT && t.a_stride == plan.FW) << 18 |
-              (uint32_t)t.chunk << 19;
+        const bool fw = (t.type == D1_SORT && t.a_stride == plan.FW) || (t.type == D1_INSERT && t.b_stride == plan.FW);
+        p.x = (uint32_t)t.a_off | (uint32_t)(t.type == D1_MERGE) << 17 | (uint32_t)fw << 18 | (uint32_t)t.chunk << 19 |
+              (uint32_t)(t.type == D1_INSERT) << 25;
         p.y = (uint32_t)t.b_off | (uint32_t)t.a_len << 17;
         p.z = (uint32_t)t.out_off | (uint32_t)t.b_len << 17;
         p.w = (uint32_t)t.lo | (uint32_t)t.hi << 13;
@@ -897,6 +1006,9 @@ void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *m
                 for (int i = 0; i < t.a_len; i++) v[i] = sm[t.a_off + (size_t)i * t.a_stride];
                 std::sort(v.begin(), v.end());
                 std::copy(v.begin(), v.end(), sm.begin() + t.out_off);
+                sm[t.out_off + t.a_len] = d1_sentinel<uint64_t>();
+            } else if (t.type == D1_INSERT) {
+                d1_insert_any<uint64_t>(sm.data(), t, chunk);
             } else {
                 d1_merge_chunk<uint64_t>(sm.data(), t, chunk);
             }

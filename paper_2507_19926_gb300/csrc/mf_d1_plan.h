@@ -13,7 +13,15 @@
 
 namespace mf {
 
-enum { D1_SORT = 0, D1_MERGE = 1 };
+// SORT: register network over a gathered run.  MERGE: output ranks of a
+// two-list merge, cut into chunks.  INSERT: a sorted list extended by up to
+// D1_MAX_INSERT gathered elements (the corners a split adds to an extra row
+// or column, Sec. 3.4), one thread, no merge-path search.
+enum { D1_SORT = 0, D1_MERGE = 1, D1_INSERT = 2 };
+
+// Largest corner run an INSERT task takes (each list element is compared
+// with every corner, so longer runs stay merges).
+constexpr int D1_MAX_INSERT = 4;
 
 // Longest list one thread sorts with a register network (longer runs are
 // sorted in pieces and merged): keeps the kernel within 64 registers so a
@@ -24,7 +32,8 @@ constexpr int D1_MAX_SORT = 32;
 struct D1Task {
     int32_t type;
     int32_t a_off, a_len, a_stride;  // SORT: gathers a_len elements at a_off + i*a_stride
-    int32_t b_off, b_len;            // MERGE: second input (a_stride unused)
+    int32_t b_off, b_len;            // MERGE: second input (a_stride unused); INSERT: the corners
+    int32_t b_stride;                // INSERT: corners gathered at b_off + i*b_stride (a list: 1)
     int32_t lo, hi;                  // MERGE: output ranks lo..hi (inclusive) of merge(A, B)
     int32_t out_off;                 // first output element
     int32_t chunk;                   // MERGE: outputs per work item

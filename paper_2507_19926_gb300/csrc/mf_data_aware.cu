@@ -8,7 +8,9 @@
 // statically planned phases (mf_d1_plan.cu) replace the kernel boundaries
 // with block barriers, so nothing but the image and the medians touches
 // HBM.  Within a phase, small sorts run as register networks (one thread
-// per list) and merges as merge-path chunks (one thread per chunk).
+// per list), merges as merge-path chunks (one thread per chunk) and the
+// corner extensions of extra rows and columns as inserts (one thread per
+// list).
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -46,6 +48,7 @@ __device__ __forceinline__ void d1_sort_task(KT *sm, const D1Task &t) {
 #pragma unroll
     for (int i = 0; i < N; i++)
         if (i < t.a_len) sm[t.out_off + i] = v[i];
+    sm[t.out_off + t.a_len] = S;  // the list's sentinel slot (see d1_merge_chunk)
 }
 
 // NMAX: the longest sort of the plan, rounded up to a power of two; the
@@ -84,12 +87,18 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
     const int x0 = bxi * SW, y0 = byi * TH;
     const char *src = a.src + (size_t)z * a.plane;
 
-    // footprint of the strip, clamped to the image
-    for (int i = tid; i < FW * FH; i += NT) {
-        const int fy = i / FW, fx = i - fy * FW;
-        const int y = clampi(y0 - RY + fy, a.y_lo, a.y_hi);
-        const int x = clampi(x0 - RX + fx, 0, a.W - 1);
-        sm[i] = D1Key<DT, KT, ARG>::make(Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, x)), i);
+    // footprint of the strip, clamped to the image: a warp a row (coalesced
+    // loads, no index division)
+    {
+        const int lane = tid & 31, nw = NT >> 5;
+        for (int fy = tid >> 5; fy < FH; fy += nw) {
+            const int y = clampi(y0 - RY + fy, a.y_lo, a.y_hi);
+            for (int fx = lane; fx < FW; fx += 32) {
+                const int x = clampi(x0 - RX + fx, 0, a.W - 1);
+                const int i = fy * FW + fx;
+                sm[i] = D1Key<DT, KT, ARG>::make(Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, x)), i);
+            }
+        }
     }
     __syncthreads();
 
@@ -99,6 +108,7 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
             const uint32_t item = p.work[w];
             const D1Task t = d1_unpack(p.tasks[item >> 12], FW);
             if (t.type == D1_SORT) d1_sort_any<KT, NMAX>(sm, t);
+            else if (t.type == D1_INSERT) d1_insert_any<KT>(sm, t, (int)(item & 4095u));
             else d1_merge_chunk<KT>(sm, t, (int)(item & 4095u));
         }
         __syncthreads();

@@ -61,6 +61,7 @@ __device__ __forceinline__ void d3_sort_task(KT *sm, const D1Task &t) {
 #pragma unroll
     for (int i = 0; i < N; i++)
         if (i < t.a_len) sm[t.out_off + i] = v[i];
+    sm[t.out_off + t.a_len] = S;  // the list's sentinel slot (see d1_merge_chunk)
 }
 
 template <class KT, int NMAX>

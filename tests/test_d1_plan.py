@@ -64,6 +64,26 @@ def test_plan_argmedian_records():
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("k,T", [(5, 4), (9, 4), (17, 8), (31, 16), (45, 16)])
+def test_plan_ties_at_the_largest_key(k, T):
+    """Keys equal to the largest key (the value of the sentinel slot that
+    follows every list) dominate the footprint, so merges run out of one
+    input while the other sits at that key; the medians must still be the
+    brute-force order statistic of each window (numpy sort of the k x k
+    window, rank (k*k - 1) / 2)."""
+    FW = T + k - 1
+    top = np.uint64(0xFFFFFFFFFFFFFFFF)
+    rng = np.random.default_rng(1000 + k)
+    vals = np.array([0, 1, 2, 3, top], dtype=np.uint64)
+    for p_top in (0.45, 0.5, 0.55, 0.9):
+        img = vals[np.where(rng.random((FW, FW)) < p_top, 4, rng.integers(0, 4, (FW, FW)))]
+        _, med = mf.mf_d1_plan_check(k, T, img.ravel())
+        m = (k * k - 1) // 2
+        want = np.array([np.sort(img[y:y + k, x:x + k].ravel())[m] for y in range(T) for x in range(T)],
+                        dtype=np.uint64)
+        assert np.array_equal(med, want), (k, T, p_top)
+
+
 def test_plan_rejects_bad_tiles():
     with pytest.raises(mf.MedianFilterError):
         mf.mf_d1_plan_check(5, 8)
