@@ -83,6 +83,21 @@ static int d1_insert_chunk_factor(int key_bytes) {
     return v >= 0 ? v : (key_bytes <= 2 ? 0 : 1);
 }
 
+// Longest sort of one thread in the 2D plans.  A 32-element register
+// network spills at the kernel's 64 registers for 1- and 2-byte keys and
+// records; 16-element pieces plus a merge measured faster (4096^2: u32
+// k = 61 24.9 -> 20.5 ms, u16 k = 75 18.3 -> 17.2 ms, u8 k = 45 6.69 -> 6.55
+// ms) except for 2-byte keys below k = 61 (u16 k = 45 8.04 -> 8.19 ms) and
+// 4-byte keys below k = 41 (u32 k = 31 8.17 -> 8.42 ms).  MF_D1_MAX_SORT
+// overrides it (sweeps).
+static int d1_max_sort(int n_win, int key_bytes) {
+    static const int forced = getenv("MF_D1_MAX_SORT") ? atoi(getenv("MF_D1_MAX_SORT")) : 0;
+    if (forced > 0) return std::min(forced, D1_MAX_SORT);
+    if (key_bytes == 2 && n_win < 61 * 61) return 32;
+    if (key_bytes >= 4 && n_win < 41 * 41) return 32;
+    return 16;
+}
+
 static void chunk_rule(int key_bytes, int *min_chunk, int *div, int *max_chunk) {
     *min_chunk = key_bytes <= 2 ? 16 : 12;
     *div = key_bytes <= 2 ? 2 : 1;
@@ -131,6 +146,8 @@ struct Builder {
     int k, T, FW;  // k: window width
     // longest corner run an INSERT takes (0: none)
     int insert_max = D1_MAX_INSERT;
+    // longest run one SORT task sorts (longer runs: even pieces, merged)
+    int max_sort = D1_MAX_SORT;
     std::vector<ListInfo> lists;
     std::vector<PTask> tasks;
 
@@ -144,10 +161,11 @@ struct Builder {
     // Sorts n footprint elements at f_off + i*stride.  Runs longer than the
     // largest register sorting network are sorted in pieces and merged.
     Ref sort_gather(int f_off, int stride, int n) {
-        if (n > D1_MAX_SORT) {
+        if (n > max_sort) {
             std::vector<Ref> parts;
-            for (int s = 0; s < n; s += D1_MAX_SORT)
-                parts.push_back(sort_gather(f_off + s * stride, stride, std::min(D1_MAX_SORT, n - s)));
+            const int np = (n + max_sort - 1) / max_sort, per = (n + np - 1) / np;
+            for (int s = 0; s < n; s += per)
+                parts.push_back(sort_gather(f_off + s * stride, stride, std::min(per, n - s)));
             return multiway(parts, 0, n - 1);
         }
         const int id = new_list(n, 0);
@@ -266,6 +284,7 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
     // from sorted lists instead the inserts measured slower than the merges
     // (u16 k = 75 20.0 -> 20.9 ms, u32 k = 45 12.9 -> 13.3 ms at 4096^2)
     B.insert_max = d1_balance(n_win, key_bytes, false) ? 0 : d1_insert_max();
+    B.max_sort = d1_max_sort(n_win, key_bytes);
     const int FW = B.FW, FH = TH + kh - 1;
     // sorted column segments over the root core rows, for every footprint
     // column of the strip: horizontally adjacent root tiles share them

@@ -24,8 +24,9 @@ enum { D1_SORT = 0, D1_MERGE = 1, D1_INSERT = 2 };
 constexpr int D1_MAX_INSERT = 4;
 
 // Longest list one thread sorts with a register network (longer runs are
-// sorted in pieces and merged): keeps the kernel within 64 registers so a
-// block can run 1024 threads.
+// sorted in even pieces and merged): keeps the kernel within 64 registers
+// so a block can run 1024 threads.  The 2D plans use 16 except for 2-byte
+// keys below k = 61 (mf_d1_plan.cu, d1_max_sort).
 constexpr int D1_MAX_SORT = 32;
 
 // One task.  Offsets and lengths are in list elements of shared memory.
