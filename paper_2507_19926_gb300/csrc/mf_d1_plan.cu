@@ -35,10 +35,12 @@
 namespace mf {
 
 // Merge chunk rule (outputs per work item; each chunk pays one binary search
-// over its two input lists): chunk = clamp(phase outputs / (div * threads),
-// min, max).  Measured on 4096^2 images, k = 27..75: 2-byte keys do best with
-// (min 16, div 2), wider keys with (min 12, div 1).  MF_D1_CHUNK="min:div"
-// overrides both (tuning sweeps).
+// over its two input lists): the chunk between min and max that finishes
+// the phase's items in the fewest rounds over the block (finish_plan).
+// Measured on 4096^2 images, k = 27..75: 2-byte keys do best with min 16,
+// wider keys with min 12; div only enters the clamp rule
+// clamp(phase outputs / (div * threads), min, max) that MF_D1_CHUNK_FIT=0
+// restores.  MF_D1_CHUNK="min:div[:max]" overrides them (tuning sweeps).
 static const bool D1_ODD_CHUNKS = !getenv("MF_D1_EVEN_CHUNKS");
 // Phase balancing of the tasks off the critical chain.  It shortens list
 // lifetimes (less shared memory: more blocks a SM where the state limits
@@ -264,7 +266,7 @@ static void keep_range(int n, int c, int d, int n_held, int *lo, int *hi) {
 }  // namespace
 
 static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int nt, int key_bytes, D1Plan *plan,
-                        bool balance);
+                        bool balance, bool volume = false);
 
 bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, int kh, int TH) {
     // k: window width (columns), kh: window height (rows); root tile T
@@ -463,7 +465,7 @@ bool d1_build_plan(int k, int T, D1Plan *plan, int NB, int nt, int key_bytes, in
 // the footprint occupies the first `base` elements).  The geometry fields of
 // `plan` are set by the caller.
 static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int nt, int key_bytes, D1Plan *plan,
-                        bool balance) {
+                        bool balance, bool volume) {
     // ---------------------------------------------------------- liveness
     for (const Ref &r : outs) {
         if (r.len != 1) return false;
@@ -614,14 +616,14 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
     std::vector<std::pair<int, int>> freel;  // (off, len), sorted by off
     // List sizes: the list, its sentinel slot (largest key) that its producer
     // writes -- merges read one element past their inputs -- and, except
-    // for 2-byte keys at 41 <= k < 61, padding to a whole, odd number of
+    // for 2-byte keys at 41 <= k < 61 and 3D plans, padding to a whole, odd number of
     // 4-byte words (1- and 2-byte keys: lists start on a word).  Threads
     // stepping through consecutive lists in lockstep then hit distinct
     // banks: fewer bank-conflict replays (4096^2, u8 k = 31 4.40 -> 4.08 ms,
     // u16 k = 31 5.91 -> 5.55 ms, u32 k = 31 8.72 -> 8.30 ms; u16 k = 45
     // measured 8.12 -> 8.48 ms, so it keeps unpadded lists).
     const int kwin2 = B.k * B.k;  // (width squared: the rule is stated in k)
-    const bool oddw = !(key_bytes == 2 && kwin2 >= 41 * 41 && kwin2 < 61 * 61);
+    const bool oddw = !volume && !(key_bytes == 2 && kwin2 >= 41 * 41 && kwin2 < 61 * 61);
     const int al = oddw && key_bytes < 4 ? 4 / key_bytes : 1;
     auto rnd = [&](int n) { return (n + al - 1) / al * al; };
     auto lsz = [&](int len) {
@@ -672,18 +674,18 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
         top += len;
         return off;
     };
-    if (balance) {
-        // Balanced plans free lists in every phase: pack the lists as
-        // rectangles (phases x elements), largest first, each at the lowest
-        // offset clear of every list live in an overlapping phase.  First
-        // fit phase by phase fragmented these plans by up to a third (u32
-        // k = 75, 8 x 8 tile: 115.5 -> 89.5 KB, two blocks a SM again: 50.5
-        // -> 33.6 ms at 4096^2).
+    // Packing of the lists as rectangles (phases x elements), largest first,
+    // each at the lowest offset clear of every list live in an overlapping
+    // phase.  Balanced plans free lists in every phase and first fit phase
+    // by phase fragments them by up to a third (u32 k = 75, 8 x 8 tile:
+    // 115.5 -> 89.5 KB, two blocks a SM again: 50.5 -> 33.6 ms at 4096^2);
+    // other plans take it where it needs less shared memory (3D plans).
+    auto pack = [&](std::vector<int> &offs) {
         struct Box {
             int off, end, t0, t1;
         };
         std::vector<Box> placed;
-        placed.push_back(Box{0, rnd(base), 0, std::max(foot_last, 0)});
+        placed.push_back(Box{0, rnd(base), 0, balance ? std::max(foot_last, 0) : nph});
         std::vector<int> order;
         for (size_t li = 0; li < B.lists.size(); li++)
             if (lphase[li] >= 0) order.push_back((int)li);
@@ -693,7 +695,7 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
             if (sx != sy) return sx > sy;
             return t1_of(x) - lphase[x] > t1_of(y) - lphase[y];
         });
-        top = rnd(base);
+        int ptop = rnd(base);
         std::vector<std::pair<int, int>> busy;
         for (int li : order) {
             const int t0 = lphase[li], t1 = t1_of(li), sz = lsz(B.lists[li].len);
@@ -706,19 +708,26 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
                 if (off + sz <= b.first) break;
                 off = std::max(off, b.second);
             }
-            B.lists[li].off = off;
+            offs[li] = off;
             placed.push_back(Box{off, off + sz, t0, t1});
-            top = std::max(top, off + sz);
+            ptop = std::max(ptop, off + sz);
         }
-    } else {
-        for (int p = 0; p <= nph; p++) {
-            // the footprint is free once its last reader has run
-            if (balance && p == foot_last + 1 && base > 0) release(0, rnd(base));
-            // every list is followed by a sentinel slot (largest key) that its
-            // producer writes: merges read one element past their inputs
-            for (int li : dies[p]) release(B.lists[li].off, lsz(B.lists[li].len));
-            if (p < nph)
-                for (int li : prod[p]) B.lists[li].off = alloc(lsz(B.lists[li].len));
+        return ptop;
+    };
+    for (int p = 0; p <= nph; p++) {
+        // the footprint is free once its last reader has run
+        if (balance && p == foot_last + 1 && base > 0) release(0, rnd(base));
+        for (int li : dies[p]) release(B.lists[li].off, lsz(B.lists[li].len));
+        if (p < nph)
+            for (int li : prod[p]) B.lists[li].off = alloc(lsz(B.lists[li].len));
+    }
+    {
+        std::vector<int> offs(B.lists.size(), -1);
+        const int ptop = pack(offs);
+        if (balance || (volume && ptop < top)) {
+            for (size_t li = 0; li < B.lists.size(); li++)
+                if (lphase[li] >= 0) B.lists[li].off = offs[li];
+            top = ptop;
         }
     }
 
@@ -749,7 +758,42 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
         // (and its roughly proportional input reads) over all 32 banks
         // (8-bit keys: 4 mod 8 elements, 16-bit keys: 2 mod 4, wider keys:
         // odd)
-        if (D1_ODD_CHUNKS) chunk = key_bytes == 1 ? (chunk & ~7) + 4 : key_bytes == 2 ? (chunk & ~3) + 2 : (chunk | 1);
+        auto round_chunk = [&](int c) {
+            if (!D1_ODD_CHUNKS) return c;
+            return key_bytes == 1 ? (c & ~7) + 4 : key_bytes == 2 ? (c & ~3) + 2 : (c | 1);
+        };
+        chunk = round_chunk(chunk);
+        // Of the rounded chunks from min to max, the one whose rounds of
+        // work items over the block's threads finish first: rounds(c) x
+        // (c + 14, an item's fixed cost in merged elements), the larger
+        // chunk on ties.  A phase of 288-384 items on 256 threads otherwise
+        // runs a second round for a few threads while the rest wait at the
+        // barrier (4096^2: u8 k = 31 4.03 -> 3.73 ms, k = 61 10.43 -> 9.65
+        // ms, u32 k = 75 33.2 -> 32.1 ms; MF_D1_CHUNK_FIT=0 keeps the clamp
+        // rule above).
+        static const int fit_env = getenv("MF_D1_CHUNK_FIT") ? atoi(getenv("MF_D1_CHUNK_FIT")) : 14;
+        if (fit_env) {
+            long best = -1;
+            const int fct = d1_insert_chunk_factor(key_bytes);
+            for (int c = min_chunk; c <= max_chunk; c++) {
+                const int rc = round_chunk(c);
+                if (rc > 62) break;
+                long items = 0;
+                for (int ti : by_phase[p]) {
+                    const PTask &t = B.tasks[ti];
+                    const int n = t.hi - t.lo + 1;
+                    if (t.type == D1_SORT) items++;
+                    else if (t.type == D1_INSERT) items += fct > 0 ? (t.a.len + std::min(fct * rc, 62) - 1) / std::min(fct * rc, 62) : 1;
+                    else items += (n + rc - 1) / rc;
+                }
+                const long rounds = (items + nt - 1) / nt;
+                const long cost = rounds * (fit_env + rc);
+                if (best < 0 || cost <= best) {
+                    best = cost;
+                    chunk = rc;
+                }
+            }
+        }
         // sorts first, grouped by size class, then merges
         std::vector<int> order = by_phase[p];
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -993,7 +1037,7 @@ bool d3_build_plan(int k, int T, D1Plan *plan, int nt, int key_bytes, int NB) {
     plan->FW = F;   // x lines are F elements apart
     plan->FH = F;
     plan->FD = FX;  // FW * FH * FD: the footprint's element count
-    return finish_plan(B, outs, F * F * FX, nt, key_bytes, plan, d1_balance((int)n_win, key_bytes, true));
+    return finish_plan(B, outs, F * F * FX, nt, key_bytes, plan, d1_balance((int)n_win, key_bytes, true), true);
 }
 
 void d1_pack_tasks(const D1Plan &plan, std::vector<D1Packed> *out) {
