@@ -32,33 +32,45 @@ __host__ __device__ __forceinline__ KT d1_sentinel() {
     return (KT)~(KT)0;
 }
 
-// 16-byte device form of a task (one 128-bit load):
-//   x = a_off | (type & 1) << 17 | (gather stride == FW) << 18 | chunk << 19 | (type == INSERT) << 25
-//   y = b_off | a_len << 17,  z = out_off | b_len << 17,  w = lo | hi << 13
-// Offsets < 2^17 list elements, lengths and ranks < 2^13, chunk < 64.  The
+// 16-byte device form of one work item (one 128-bit load; the item carries
+// everything its thread needs, so no second, dependent fetch of its task):
+//   x = a_off | type << 17 | (gather stride == FW) << 19 | last << 20 | cnt << 21
+//   y = b_off | a_len << 17,  z = out_off | b_len << 17,  w = start
+// Offsets < 2^17 list elements, lengths and ranks < 2^13, cnt < 256.  The
 // gather stride is the SORT's a_stride or the INSERT's b_stride.
-struct D1Packed {
+struct alignas(16) D1Packed {
     uint32_t x, y, z, w;
 };
 
-__host__ __device__ __forceinline__ D1Task d1_unpack(const D1Packed &p, int FW) {
-    D1Task t;
+// One work item, decoded.
+struct D1Item {
+    int type;
+    int a_off, a_len, a_stride;  // SORT: gather a_len elements at a_off + i*a_stride; else list A (INSERT: L)
+    int b_off, b_len, b_stride;  // MERGE: list B; INSERT: b_len corners at b_off + q*b_stride
+    int out_off;                 // SORT, INSERT: the output list; MERGE: this item's first output
+    int start, cnt;              // MERGE: output ranks start .. start+cnt-1 of merge(A, B);
+                                 // INSERT: L elements start .. start+cnt-1
+    int last;                    // the item that writes the output list's sentinel slot
+};
+
+__host__ __device__ __forceinline__ D1Item d1_unpack(const D1Packed &p, int FW) {
+    D1Item t;
     t.a_off = (int)(p.x & 0x1ffffu);
-    t.type = ((p.x >> 25) & 1u) ? D1_INSERT : (int)((p.x >> 17) & 1u);
-    t.a_stride = ((p.x >> 18) & 1u) ? FW : 1;
+    t.type = (int)((p.x >> 17) & 3u);
+    t.a_stride = ((p.x >> 19) & 1u) ? FW : 1;
     t.b_stride = t.a_stride;
-    t.chunk = (int)((p.x >> 19) & 63u);
+    t.last = (int)((p.x >> 20) & 1u);
+    t.cnt = (int)(p.x >> 21);
     t.b_off = (int)(p.y & 0x1ffffu);
     t.a_len = (int)(p.y >> 17);
     t.out_off = (int)(p.z & 0x1ffffu);
     t.b_len = (int)(p.z >> 17);
-    t.lo = (int)(p.w & 0x1fffu);
-    t.hi = (int)(p.w >> 13);
+    t.start = (int)p.w;
     return t;
 }
 
-// Outputs lo + chunk*t.chunk ... (up to t.chunk of them, not past hi) of
-// merge(A, B) into out[(p - lo)].
+// Output ranks t.start .. t.start+t.cnt-1 of merge(A, B) into
+// sm[t.out_off ..].
 //
 // Every list is followed in shared memory by a sentinel slot holding the
 // largest key (the plan allocates it, the list's producer writes it), so
@@ -72,13 +84,11 @@ __host__ __device__ __forceinline__ D1Task d1_unpack(const D1Packed &p, int FW) 
 // stays at that key, which is every remaining output).  The last chunk
 // writes the output list's own sentinel.
 template <class KT>
-__host__ __device__ __forceinline__ void d1_merge_chunk(KT *sm, const D1Task &t, int chunk) {
+__host__ __device__ __forceinline__ void d1_merge_item(KT *sm, const D1Item &t) {
     const KT *A = sm + t.a_off;
     const KT *B = sm + t.b_off;
     const int na = t.a_len, nb = t.b_len;
-    const int p0 = t.lo + chunk * t.chunk;
-    int cnt = t.hi - p0 + 1;
-    if (cnt > t.chunk) cnt = t.chunk;
+    const int p0 = t.start, cnt = t.cnt;
     // i = number of A elements among the first p0 outputs
     int lo = p0 - nb > 0 ? p0 - nb : 0;
     int hi = p0 < na ? p0 : na;
@@ -89,7 +99,7 @@ __host__ __device__ __forceinline__ void d1_merge_chunk(KT *sm, const D1Task &t,
         else hi = mid;
     }
     int i = lo;
-    KT *out = sm + t.out_off + (p0 - t.lo);
+    KT *out = sm + t.out_off;
     KT a = A[i], b = B[p0 - i];
 #pragma unroll 4
     for (int n = 0; n < cnt; n++) {
@@ -104,7 +114,7 @@ __host__ __device__ __forceinline__ void d1_merge_chunk(KT *sm, const D1Task &t,
         a = ta ? v : a;
         b = ta ? b : v;
     }
-    if (p0 + cnt - 1 == t.hi) out[cnt] = d1_sentinel<KT>();
+    if (t.last) out[cnt] = d1_sentinel<KT>();
 }
 
 template <class KT>
@@ -117,12 +127,12 @@ __host__ __device__ __forceinline__ void d1_cx(KT &a, KT &b) {
 // out[0 .. n+C) = merge(L, sorted corners), L = sm[a_off .. a_off+n) sorted,
 // corners gathered at b_off + q*b_stride.  Ties keep L first, as the merge
 // does.  L element i lands at i + #(corners below it); corner q (in sorted
-// order) at q + i*_q, i*_q = #(L elements not above it).  Work item `chunk`
-// moves the L elements i0 = chunk*t.chunk .. i1 (t.chunk = 0: all of them)
-// and places the corners whose i*_q falls in [i0, i1) (or at n, for the
-// last item): there i*_q = i1 - #(elements of the item above corner q).
+// order) at q + i*_q, i*_q = #(L elements not above it).  The item moves the
+// L elements i0 = t.start .. i1 = i0 + t.cnt and places the corners whose
+// i*_q falls in [i0, i1) (or at n, for the last item): there i*_q = i1 -
+// #(elements of the item above corner q).
 template <class KT, int C>
-__host__ __device__ __forceinline__ void d1_insert(KT *sm, const D1Task &t, int chunk) {
+__host__ __device__ __forceinline__ void d1_insert(KT *sm, const D1Item &t) {
     KT s[C];
 #pragma unroll
     for (int q = 0; q < C; q++) s[q] = sm[t.b_off + q * t.b_stride];
@@ -138,8 +148,7 @@ __host__ __device__ __forceinline__ void d1_insert(KT *sm, const D1Task &t, int 
     const KT *L = sm + t.a_off;
     KT *out = sm + t.out_off;
     const int n = t.a_len;
-    const int i0 = t.chunk ? chunk * t.chunk : 0;
-    const int i1 = t.chunk && i0 + t.chunk < n ? i0 + t.chunk : n;
+    const int i0 = t.start, i1 = t.start + t.cnt;
     int above[C];
 #pragma unroll
     for (int q = 0; q < C; q++) above[q] = 0;
@@ -163,10 +172,10 @@ __host__ __device__ __forceinline__ void d1_insert(KT *sm, const D1Task &t, int 
 }
 
 template <class KT>
-__host__ __device__ __forceinline__ void d1_insert_any(KT *sm, const D1Task &t, int chunk) {
-    if (t.b_len == 1) d1_insert<KT, 1>(sm, t, chunk);
-    else if (t.b_len == 2) d1_insert<KT, 2>(sm, t, chunk);
-    else d1_insert<KT, 4>(sm, t, chunk);
+__host__ __device__ __forceinline__ void d1_insert_any(KT *sm, const D1Item &t) {
+    if (t.b_len == 1) d1_insert<KT, 1>(sm, t);
+    else if (t.b_len == 2) d1_insert<KT, 2>(sm, t);
+    else d1_insert<KT, 4>(sm, t);
 }
 
 }  // namespace mf

@@ -846,7 +846,7 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
         if (t.a_off >= (1 << 17) || t.b_off >= (1 << 17) || t.out_off >= (1 << 17) || t.a_len >= (1 << 13) ||
             t.b_len >= (1 << 13) || t.lo >= (1 << 13) || t.hi >= (1 << 13) || t.chunk >= 64 ||
             (t.type == D1_SORT && t.a_stride != 1 && t.a_stride != plan->FW) ||
-            (t.type == D1_INSERT && (t.b_len > D1_MAX_INSERT || (t.b_stride != 1 && t.b_stride != plan->FW))))
+            (t.type == D1_INSERT && (t.b_len > D1_MAX_INSERT || t.a_len > 255 || (t.b_stride != 1 && t.b_stride != plan->FW))))
             return false;
     return plan->tasks.size() < (1u << 20);
 }
@@ -1040,17 +1040,32 @@ bool d3_build_plan(int k, int T, D1Plan *plan, int nt, int key_bytes, int NB) {
     return finish_plan(B, outs, F * F * FX, nt, key_bytes, plan, d1_balance((int)n_win, key_bytes, true), true);
 }
 
-void d1_pack_tasks(const D1Plan &plan, std::vector<D1Packed> *out) {
-    out->resize(plan.tasks.size());
-    for (size_t i = 0; i < plan.tasks.size(); i++) {
-        const D1Task &t = plan.tasks[i];
-        D1Packed &p = (*out)[i];
+void d1_pack_items(const D1Plan &plan, std::vector<D1Packed> *out) {
+    out->resize(plan.work.size());
+    for (size_t w = 0; w < plan.work.size(); w++) {
+        const D1Task &t = plan.tasks[plan.work[w] >> 12];
+        const int c = (int)(plan.work[w] & 4095u);
+        int out_off = t.out_off, start = 0, cnt = 0, last = 1;
+        if (t.type == D1_MERGE) {
+            const int p0 = t.lo + c * t.chunk;
+            cnt = std::min(t.hi - p0 + 1, t.chunk);
+            start = p0;
+            out_off = t.out_off + (p0 - t.lo);
+            last = p0 + cnt - 1 == t.hi;
+        } else if (t.type == D1_INSERT) {
+            const int n = t.a_len;
+            start = t.chunk ? c * t.chunk : 0;
+            const int i1 = t.chunk ? std::min(n, start + t.chunk) : n;
+            cnt = i1 - start;
+            last = i1 == n;
+        }
         const bool fw = (t.type == D1_SORT && t.a_stride == plan.FW) || (t.type == D1_INSERT && t.b_stride == plan.FW);
-        p.x = (uint32_t)t.a_off | (uint32_t)(t.type == D1_MERGE) << 17 | (uint32_t)fw << 18 | (uint32_t)t.chunk << 19 |
-              (uint32_t)(t.type == D1_INSERT) << 25;
+        D1Packed &p = (*out)[w];
+        p.x = (uint32_t)t.a_off | (uint32_t)t.type << 17 | (uint32_t)fw << 19 | (uint32_t)last << 20 |
+              (uint32_t)cnt << 21;
         p.y = (uint32_t)t.b_off | (uint32_t)t.a_len << 17;
-        p.z = (uint32_t)t.out_off | (uint32_t)t.b_len << 17;
-        p.w = (uint32_t)t.lo | (uint32_t)t.hi << 13;
+        p.z = (uint32_t)out_off | (uint32_t)t.b_len << 17;
+        p.w = (uint32_t)start;
     }
 }
 
@@ -1058,12 +1073,11 @@ void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *m
     std::vector<uint64_t> sm(plan.smem_elems, 0xdeadbeefdeadbeefull);
     std::copy(footprint, footprint + (size_t)plan.FW * plan.FH * plan.FD, sm.begin());
     const int nph = (int)plan.phase_begin.size() - 1;
-    std::vector<D1Packed> packed;
-    d1_pack_tasks(plan, &packed);
+    std::vector<D1Packed> items;
+    d1_pack_items(plan, &items);
     for (int p = 0; p < nph; p++) {
         for (int w = plan.phase_begin[p]; w < plan.phase_begin[p + 1]; w++) {
-            const D1Task t = d1_unpack(packed[plan.work[w] >> 12], plan.FW);
-            const int chunk = plan.work[w] & 4095;
+            const D1Item t = d1_unpack(items[w], plan.FW);
             if (t.type == D1_SORT) {
                 std::vector<uint64_t> v(t.a_len);
                 for (int i = 0; i < t.a_len; i++) v[i] = sm[t.a_off + (size_t)i * t.a_stride];
@@ -1071,9 +1085,9 @@ void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *m
                 std::copy(v.begin(), v.end(), sm.begin() + t.out_off);
                 sm[t.out_off + t.a_len] = d1_sentinel<uint64_t>();
             } else if (t.type == D1_INSERT) {
-                d1_insert_any<uint64_t>(sm.data(), t, chunk);
+                d1_insert_any<uint64_t>(sm.data(), t);
             } else {
-                d1_merge_chunk<uint64_t>(sm.data(), t, chunk);
+                d1_merge_item<uint64_t>(sm.data(), t);
             }
         }
     }

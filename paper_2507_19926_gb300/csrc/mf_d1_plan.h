@@ -52,7 +52,7 @@ struct D1Plan {
     int nt = 256;                    // threads per block the chunking targets
     int smem_elems = 0;              // shared-memory list elements needed (footprint included)
     std::vector<D1Task> tasks;       // host form; the device gets them packed (D1Packed)
-    std::vector<uint32_t> work;      // task << 12 | chunk, grouped by phase
+    std::vector<uint32_t> work;      // task << 12 | chunk, grouped by phase (the device gets d1_pack_items)
     std::vector<int32_t> phase_begin;  // phases + 1 entries into work
     std::vector<int32_t> out_off;    // TH * B*T: offset of each pixel's median (row-major in the strip)
     int max_sort = 0;                // longest SORT task
@@ -85,8 +85,9 @@ constexpr int D3_MAX_K = 19;
 bool d3_build_plan(int k, int T, D1Plan *plan, int nt = 256, int key_bytes = 4, int NB = 1);
 
 struct D1Packed;
-// The 16-byte device form of every task (layout in mf_d1_ops.cuh).
-void d1_pack_tasks(const D1Plan &plan, std::vector<D1Packed> *out);
+// The 16-byte device form of every work item, in work order (layout in
+// mf_d1_ops.cuh); phase_begin indexes it.
+void d1_pack_items(const D1Plan &plan, std::vector<D1Packed> *out);
 
 // Runs a plan on the host for one footprint of keys (FH*FW, row-major),
 // writing the T * B*T medians (row-major).  Used by tests to check the

@@ -30,8 +30,7 @@ constexpr size_t D1_SMEM_BUDGET = 200 * 1024;
 constexpr size_t D1_SMEM_SMALL = 56 * 1024;
 
 struct D1Dev {
-    const D1Packed *tasks;
-    const uint32_t *work;
+    const D1Packed *items;  // one 16-byte record per work item, in work order
     const int32_t *phase_begin;
     const int32_t *out_off;
     int nphases;
@@ -39,7 +38,7 @@ struct D1Dev {
 };
 
 template <class KT, int N>
-__device__ __forceinline__ void d1_sort_task(KT *sm, const D1Task &t) {
+__device__ __forceinline__ void d1_sort_task(KT *sm, const D1Item &t) {
     KT v[N];
     const KT S = d1_sentinel<KT>();
 #pragma unroll
@@ -48,14 +47,14 @@ __device__ __forceinline__ void d1_sort_task(KT *sm, const D1Task &t) {
 #pragma unroll
     for (int i = 0; i < N; i++)
         if (i < t.a_len) sm[t.out_off + i] = v[i];
-    sm[t.out_off + t.a_len] = S;  // the list's sentinel slot (see d1_merge_chunk)
+    sm[t.out_off + t.a_len] = S;  // the list's sentinel slot (see d1_merge_item)
 }
 
 // NMAX: the longest sort of the plan, rounded up to a power of two; the
 // kernel is instantiated per NMAX so that short plans do not pay for the
 // registers of a 64-element network.
 template <class KT, int NMAX>
-__device__ __forceinline__ void d1_sort_any(KT *sm, const D1Task &t) {
+__device__ __forceinline__ void d1_sort_any(KT *sm, const D1Item &t) {
     const int n = t.a_len;
     if (n <= 2) d1_sort_task<KT, 2>(sm, t);
     else if (n <= 4) d1_sort_task<KT, 4>(sm, t);
@@ -105,11 +104,10 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
     for (int ph = 0; ph < p.nphases; ph++) {
         const int wb = p.phase_begin[ph], we = p.phase_begin[ph + 1];
         for (int w = wb + tid; w < we; w += NT) {
-            const uint32_t item = p.work[w];
-            const D1Task t = d1_unpack(p.tasks[item >> 12], FW);
+            const D1Item t = d1_unpack(p.items[w], FW);
             if (t.type == D1_SORT) d1_sort_any<KT, NMAX>(sm, t);
-            else if (t.type == D1_INSERT) d1_insert_any<KT>(sm, t, (int)(item & 4095u));
-            else d1_merge_chunk<KT>(sm, t, (int)(item & 4095u));
+            else if (t.type == D1_INSERT) d1_insert_any<KT>(sm, t);
+            else d1_merge_item<KT>(sm, t);
         }
         __syncthreads();
     }
@@ -288,10 +286,10 @@ static D1Cached *get_plan(int k, int T, int B, int nt, int kb, int kh = 0, int T
     c->plan = *hp;
     const D1Plan &pl = c->plan;
     std::vector<D1Packed> packed;
-    d1_pack_tasks(pl, &packed);
-    const size_t bt = packed.size() * sizeof(D1Packed), bw = pl.work.size() * 4,
+    d1_pack_items(pl, &packed);
+    const size_t bt = packed.size() * sizeof(D1Packed),
                  bp = pl.phase_begin.size() * 4, bo = pl.out_off.size() * 4;
-    const size_t total = bt + bw + bp + bo + 64;
+    const size_t total = bt + bp + bo + 64;
     if (dev_alloc(&c->mem, total) != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -299,18 +297,16 @@ static D1Cached *get_plan(int k, int T, int B, int nt, int kb, int kh = 0, int T
     }
     char *m = (char *)c->mem;
     if (cudaMemcpy(m, packed.data(), bt, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(m + bt, pl.work.data(), bw, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(m + bt + bw, pl.phase_begin.data(), bp, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(m + bt + bw + bp, pl.out_off.data(), bo, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(m + bt, pl.phase_begin.data(), bp, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m + bt + bp, pl.out_off.data(), bo, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(c->mem);
         delete c;
         return nullptr;
     }
-    c->dev.tasks = (const D1Packed *)m;
-    c->dev.work = (const uint32_t *)(m + bt);
-    c->dev.phase_begin = (const int32_t *)(m + bt + bw);
-    c->dev.out_off = (const int32_t *)(m + bt + bw + bp);
+    c->dev.items = (const D1Packed *)m;
+    c->dev.phase_begin = (const int32_t *)(m + bt);
+    c->dev.out_off = (const int32_t *)(m + bt + bp);
     c->dev.nphases = (int)pl.phase_begin.size() - 1;
     c->dev.k = k;
     c->dev.kh = hp->kh;
