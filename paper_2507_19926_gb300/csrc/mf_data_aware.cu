@@ -86,9 +86,11 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
     const int x0 = bxi * SW, y0 = byi * TH;
     const char *src = a.src + (size_t)z * a.plane;
 
-    // footprint of the strip, clamped to the image: a warp a row (coalesced
-    // loads, no index division)
-    {
+    // footprint of the strip, clamped to the image: a warp a row where rows
+    // are at least a warp wide and every warp gets one (coalesced loads, no
+    // index division), else the block over the flattened footprint (thin
+    // windows: a few narrow or short rows would leave most lanes idle)
+    if (FW >= 32 && FH >= (NT >> 5)) {
         const int lane = tid & 31, nw = NT >> 5;
         for (int fy = tid >> 5; fy < FH; fy += nw) {
             const int y = clampi(y0 - RY + fy, a.y_lo, a.y_hi);
@@ -97,6 +99,13 @@ __device__ __forceinline__ void d1_block(const ImgArgs &a, const D1Dev &p, int b
                 const int i = fy * FW + fx;
                 sm[i] = D1Key<DT, KT, ARG>::make(Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, x)), i);
             }
+        }
+    } else {
+        for (int i = tid; i < FW * FH; i += NT) {
+            const int fy = i / FW, fx = i - fy * FW;
+            const int y = clampi(y0 - RY + fy, a.y_lo, a.y_hi);
+            const int x = clampi(x0 - RX + fx, 0, a.W - 1);
+            sm[i] = D1Key<DT, KT, ARG>::make(Dt<DT>::key(ldg_elem<E>(src, a.pitch, y, x)), i);
         }
     }
     __syncthreads();
