@@ -270,6 +270,17 @@ int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint
 int mf_d1_plan_check_rect(int kw, int kh, int tile_w, int tile_h, int strip, const uint64_t *footprint,
                           uint64_t *medians, int *stats);
 
+/* As mf_d1_plan_check_rect for the plan the kernels build for keys of
+ * key_bytes bytes (1, 2, 4 or 8: 8-bit values, 16-bit values or 8/16-bit
+ * records, 32-bit values, 32-bit records) run by blocks of `threads` threads
+ * (256, 512 or 1024): the key width and the block size select the merge
+ * chunks, the list padding, phase balancing and the longest sort
+ * (mf_d1_plan_check_rect plans for 4-byte keys and 256 threads).  The
+ * footprint still holds 64-bit keys.  MF_ERR_ARG for other key widths or
+ * block sizes. */
+int mf_d1_plan_check_ex(int kw, int kh, int tile_w, int tile_h, int strip, int key_bytes, int threads,
+                        const uint64_t *footprint, uint64_t *medians, int *stats);
+
 /* Number of CUDA kernels this library launched since load (all threads). */
 uint64_t mf_kernel_launch_count(void);
 

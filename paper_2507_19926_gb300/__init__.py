@@ -28,7 +28,7 @@ GRAD_MODES = {"atomic": MF_GRAD_ATOMIC, "deterministic": MF_GRAD_DETERMINISTIC}
 
 # C symbols declared in include/medianfilter.h and include/medianfilter_volume.h
 EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_tile", "mf_median_filter_config",
-           "mf_median_filter_rect", "mf_d1_plan_check_rect",
+           "mf_median_filter_rect", "mf_d1_plan_check_rect", "mf_d1_plan_check_ex",
            "mf_median_filter_bwd",
            "mf_median_filter_host", "mf_batch_plan_create", "mf_batch_plan_create_ex", "mf_batch_run",
            "mf_batch_plan_destroy", "mf_batch_describe", "mf_batch_run_static", "mf_autotune", "mf_describe", "mf_kernel_launch_count",
@@ -71,6 +71,7 @@ def load_library(path=LIB_PATH):
         lib.mf_median_filter_config.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp]
         lib.mf_median_filter_rect.argtypes = [vp, vp, i, i, sz, i, i, i, i, vp, sz, vp]
         lib.mf_d1_plan_check_rect.argtypes = [i, i, i, i, i, vp, vp, vp]
+        lib.mf_d1_plan_check_ex.argtypes = [i, i, i, i, i, i, i, vp, vp, vp]
         lib.mf_median_filter_bwd.argtypes = [vp, vp, vp, i, i, sz, sz, i, i, i, vp]
         lib.mf_median_filter_host.argtypes = [vp, vp, i, i, sz, i, i, i, i, i, vp]
         lib.mf_batch_plan_create.argtypes = [ctypes.POINTER(ImageDesc), i, ctypes.POINTER(vp)]
@@ -208,12 +209,13 @@ def mf_probe_minmax(kind, iters=4096):
     return rate.value, ms.value
 
 
-def mf_d1_plan_check(k, tile, footprint=None, strip=1, kh=None, tile_h=None):
+def mf_d1_plan_check(k, tile, footprint=None, strip=1, kh=None, tile_h=None, key_bytes=None, threads=256):
     """Builds the data-aware schedule for (k, tile, strip) -- a window of k
     columns by kh rows and root tiles of tile columns by tile_h rows when
-    given; with a uint64 footprint of keys ((tile_h+kh-1) x
-    (strip*tile+k-1)) also runs it on the CPU.  Returns (stats dict,
-    tile_h x strip*tile medians or None)."""
+    given, for keys of key_bytes bytes and blocks of `threads` threads when
+    key_bytes is given (else 4-byte keys, 256 threads); with a uint64
+    footprint of keys ((tile_h+kh-1) x (strip*tile+k-1)) also runs it on the
+    CPU.  Returns (stats dict, tile_h x strip*tile medians or None)."""
     import numpy as np
     st = np.zeros(7, np.int32)
     med = None
@@ -222,9 +224,13 @@ def mf_d1_plan_check(k, tile, footprint=None, strip=1, kh=None, tile_h=None):
     if footprint is not None:
         fp = np.ascontiguousarray(footprint, dtype=np.uint64)
         med = np.zeros(tile * th * strip, np.uint64)
-    _check(load_library().mf_d1_plan_check_rect(k, k if kh is None else kh, tile, th, strip,
-                                                fp.ctypes.data if fp is not None else None,
-                                                med.ctypes.data if med is not None else None, st.ctypes.data))
+    args = (fp.ctypes.data if fp is not None else None, med.ctypes.data if med is not None else None,
+            st.ctypes.data)
+    kh_ = k if kh is None else kh
+    if key_bytes is None:
+        _check(load_library().mf_d1_plan_check_rect(k, kh_, tile, th, strip, *args))
+    else:
+        _check(load_library().mf_d1_plan_check_ex(k, kh_, tile, th, strip, key_bytes, threads, *args))
     names = ["smem_elems", "phases", "tasks", "work_items", "merged", "sorted", "max_sort"]
     return dict(zip(names, [int(v) for v in st])), med
 

@@ -1097,10 +1097,13 @@ void d1_run_plan_host(const D1Plan &plan, const uint64_t *footprint, uint64_t *m
 }  // namespace mf
 
 // Host check of the data-aware schedule (declared in medianfilter.h).
-extern "C" int mf_d1_plan_check_rect(int kw, int kh, int tile_w, int tile_h, int strip,
-                                     const uint64_t *footprint, uint64_t *medians, int *stats) {
+extern "C" int mf_d1_plan_check_ex(int kw, int kh, int tile_w, int tile_h, int strip, int key_bytes, int threads,
+                                   const uint64_t *footprint, uint64_t *medians, int *stats) {
+    if ((key_bytes != 1 && key_bytes != 2 && key_bytes != 4 && key_bytes != 8) ||
+        (threads != 256 && threads != 512 && threads != 1024))
+        return MF_ERR_ARG;
     mf::D1Plan plan;
-    if (!mf::d1_build_plan(kw, tile_w, &plan, strip, 256, 4, kh, tile_h)) return MF_ERR_UNSUPPORTED;
+    if (!mf::d1_build_plan(kw, tile_w, &plan, strip, threads, key_bytes, kh, tile_h)) return MF_ERR_UNSUPPORTED;
     if (stats) {
         stats[0] = plan.smem_elems;
         stats[1] = (int)plan.phase_begin.size() - 1;
@@ -1112,6 +1115,11 @@ extern "C" int mf_d1_plan_check_rect(int kw, int kh, int tile_w, int tile_h, int
     }
     if (footprint && medians) mf::d1_run_plan_host(plan, footprint, medians);
     return MF_OK;
+}
+
+extern "C" int mf_d1_plan_check_rect(int kw, int kh, int tile_w, int tile_h, int strip,
+                                     const uint64_t *footprint, uint64_t *medians, int *stats) {
+    return mf_d1_plan_check_ex(kw, kh, tile_w, tile_h, strip, 4, 256, footprint, medians, stats);
 }
 
 extern "C" int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,

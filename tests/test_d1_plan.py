@@ -84,6 +84,46 @@ def test_plan_ties_at_the_largest_key(k, T):
         assert np.array_equal(med, want), (k, T, p_top)
 
 
+# (k, root tile, key bytes, threads): the plans the kernels run by default
+# for 8-bit values (1-byte keys), 16-bit values and 8/16-bit records (2 or 4
+# bytes), 32-bit values (4) and 32-bit records (8), at the block sizes the
+# kernel picks for them -- their chunking, list padding, phase balancing and
+# sort lengths differ from the 4-byte, 256-thread plans above.
+KB_CASES = [(27, 16, 1, 256), (31, 16, 1, 256), (45, 16, 1, 256), (61, 16, 1, 256), (75, 16, 1, 512),
+            (31, 16, 2, 512), (45, 16, 2, 512), (61, 16, 2, 512), (75, 16, 2, 1024), (33, 8, 4, 256),
+            (45, 16, 4, 1024), (61, 8, 4, 512), (75, 8, 4, 512), (29, 8, 8, 256), (45, 8, 8, 512)]
+
+
+@pytest.mark.parametrize("k,T,kb,nt", KB_CASES)
+def test_plan_by_key_width_matches_oracle(k, T, kb, nt):
+    FW = T + k - 1
+    r = k // 2
+    m = (k * k - 1) // 2
+    top = np.uint64(0xFFFFFFFFFFFFFFFF)
+    for s in range(3):
+        if s < 2:
+            gen = synth.levels16 if s else synth.uniform
+            img = gen((FW, FW), "u16", 31 * k + T + kb + s)
+            _, med = mf.mf_d1_plan_check(k, T, img.astype(np.uint64).ravel(), key_bytes=kb, threads=nt)
+            want = oracle.median_filter(img, k)[r:r + T, r:r + T].ravel()
+            assert np.array_equal(med.astype(np.uint16), want), (k, T, kb, nt, s)
+        else:  # most keys equal to the sentinel value
+            rng = np.random.default_rng(k + kb)
+            vals = np.array([0, 1, 2, top], dtype=np.uint64)
+            img = vals[np.where(rng.random((FW, FW)) < 0.55, 3, rng.integers(0, 3, (FW, FW)))]
+            _, med = mf.mf_d1_plan_check(k, T, img.ravel(), key_bytes=kb, threads=nt)
+            want = np.array([np.sort(img[y:y + k, x:x + k].ravel())[m] for y in range(T) for x in range(T)],
+                            dtype=np.uint64)
+            assert np.array_equal(med, want), (k, T, kb, nt)
+
+
+def test_plan_check_ex_rejects_bad_key_width():
+    with pytest.raises(mf.MedianFilterError):
+        mf.mf_d1_plan_check(9, 4, key_bytes=3)
+    with pytest.raises(mf.MedianFilterError):
+        mf.mf_d1_plan_check(9, 4, key_bytes=4, threads=128)
+
+
 def test_plan_rejects_bad_tiles():
     with pytest.raises(mf.MedianFilterError):
         mf.mf_d1_plan_check(5, 8)
