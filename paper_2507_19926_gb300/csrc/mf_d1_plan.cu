@@ -841,7 +841,9 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
     plan->phase_begin.push_back((int)plan->work.size());
     plan->out_off.resize(outs.size());
     for (size_t i = 0; i < outs.size(); i++) plan->out_off[i] = resolve(outs[i]);
-    // limits of the packed device form
+    // limits of the packed device form (every element position, a merge
+    // item's output position inside its list included, below 2^17)
+    if (plan->smem_elems > (1 << 17)) return false;
     for (const D1Task &t : plan->tasks)
         if (t.a_off >= (1 << 17) || t.b_off >= (1 << 17) || t.out_off >= (1 << 17) || t.a_len >= (1 << 13) ||
             t.b_len >= (1 << 13) || t.lo >= (1 << 13) || t.hi >= (1 << 13) || t.chunk >= 64 ||
