@@ -57,10 +57,35 @@ const O1Entry *o1_for_image(const O1Entry *e, const ImgArgs &a) {
     }
 }
 
-const O1Entry *find_o1(int k, int dtype, bool arg, int bucket) {
-    const int tuned = tune_lookup(k, dtype, arg, bucket) == MF_OBLIVIOUS ? tune_tile(k, dtype, arg, bucket) : 0;
-    const O1Entry *e = tuned ? find_o1_nth(k, dtype, arg, tuned) : nullptr;
-    return e ? e : find_o1_nth(k, dtype, arg, 0);
+// Untuned default for an image filtered on its own (`alone`) in an
+// image-size bucket.  The wide forms (a run of 4 or 2 root tiles a lane)
+// are the defaults at k = 3, 5 because they win on large images; a small
+// image alone then has too few blocks to fill the GPU (in a batch its
+// blocks run beside other images', and the default stays).
+// With 16-bit keys (8/16-bit data) buckets below 10 (under 2^20 pixels)
+// take the first configuration without a run and bucket 10 (up to 2^22
+// pixels) the first with a run of 2, where there is one (measured from a
+// CUDA graph of 200 launches: 640 x 480 u8 k = 5 3.64 -> 2.74 us, k = 3
+// 2.72 -> 1.90 us; 1920 x 1080 u8 k = 5 8.08 -> 7.16 us, k = 3 4.40 ->
+// 3.83 us; 32-bit keys showed no such gain).
+static const O1Entry *o1_default(int k, int dtype, bool arg, int bucket, bool alone) {
+    const O1Entry *d = find_o1_nth(k, dtype, arg, 0);
+    if (!alone || !d || d->run <= 1 || d->lanes != 2 || bucket < 0 || bucket > 10) return d;
+    const int want = bucket <= 9 ? 1 : 2;
+    for (int nth = 1;; nth++) {
+        const O1Entry *f = find_o1_nth(k, dtype, arg, nth);
+        if (!f) return d;
+        if (f->run == want && f->lanes == 2) return f;
+    }
+}
+
+const O1Entry *find_o1(int k, int dtype, bool arg, int bucket, bool alone) {
+    // a tuning entry (nearest size bucket) names its configuration, the
+    // default one included
+    const O1Entry *e = tune_lookup(k, dtype, arg, bucket) == MF_OBLIVIOUS
+                           ? find_o1_nth(k, dtype, arg, tune_tile(k, dtype, arg, bucket))
+                           : nullptr;
+    return e ? e : o1_default(k, dtype, arg, bucket, alone);
 }
 
 static int esize(int dtype) {
@@ -127,10 +152,10 @@ struct Plan {
     int tile;     // D1 root tile
 };
 
-static int resolve(int k, int dtype, bool arg, int variant, Plan *p, int bucket = -1) {
+static int resolve(int k, int dtype, bool arg, int variant, Plan *p, int bucket = -1, bool alone = false) {
     p->o1 = nullptr;
     p->tile = 0;
-    const O1Entry *o1 = find_o1(k, dtype, arg, bucket);
+    const O1Entry *o1 = find_o1(k, dtype, arg, bucket, alone);
     const bool d1 = d1_supported(k, dtype, arg) != 0;
     if (variant == MF_AUTO) {
         int tuned = tune_lookup(k, dtype, arg, bucket);
@@ -166,7 +191,7 @@ int resolve_variant(int k, int dtype, bool arg, int variant, const O1Entry **o1,
 // The value (or record) kernel the variant resolves to, on prepared args.
 static int launch_resolved(const ImgArgs &a, int C, int k, int dtype, int variant, cudaStream_t s) {
     Plan p;
-    int rc = resolve(k, dtype, a.idx != nullptr, variant, &p, size_bucket((long long)a.H * a.W));
+    int rc = resolve(k, dtype, a.idx != nullptr, variant, &p, size_bucket((long long)a.H * a.W), true);
     if (rc) return rc;
     if (p.variant == MF_OBLIVIOUS) {
         const O1Entry *e = o1_for_image(p.o1, a);
@@ -475,7 +500,7 @@ int mf_describe(int H, int W, int channels, mf_dtype dtype, int k, mf_variant va
     if (k < 1 || k > 75 || !(k & 1) || H < 1 || W < 1 || channels < 1) { set_error("bad arguments"); return MF_ERR_ARG; }
     if (k == 1) { snprintf(buf, buflen, "identity copy"); return MF_OK; }
     Plan p;
-    int rc = resolve(k, dtype, false, variant, &p, size_bucket((long long)H * W));
+    int rc = resolve(k, dtype, false, variant, &p, size_bucket((long long)H * W), true);
     if (rc) return rc;
     if (p.variant == MF_OBLIVIOUS)
         snprintf(buf, buflen, "oblivious k=%d tile=%dx%d block=%dx%d run=%d net_ops=%d kernel=%s", k, p.o1->tw,

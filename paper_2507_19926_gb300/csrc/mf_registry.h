@@ -27,9 +27,11 @@ struct O1Entry {
 extern const O1Entry kO1Entries[];
 extern const int kO1Count;
 
-// The configuration the tuning table selects (else the default).
-// bucket: size bucket of the image (size_bucket in mf_tune.h), -1 unknown.
-const O1Entry *find_o1(int k, int dtype, bool arg, int bucket = -1);
+// The configuration a call runs for (k, dtype, argmedian): the one the
+// tuning table selects, else the default (for an image filtered on its
+// own, `alone`, a size-aware default at k = 3, 5).  bucket: size bucket of
+// the image (size_bucket in mf_tune.h), -1 unknown.
+const O1Entry *find_o1(int k, int dtype, bool arg, int bucket = -1, bool alone = false);
 const O1Entry *find_o1_nth(int k, int dtype, bool arg, int nth);
 
 // Data-aware variant (mf_data_aware.cu).
