@@ -721,10 +721,10 @@ static bool finish_plan(Builder &B, const std::vector<Ref> &outs, int base, int 
         if (p < nph)
             for (int li : prod[p]) B.lists[li].off = alloc(lsz(B.lists[li].len));
     }
-    {
+    if (balance || volume) {
         std::vector<int> offs(B.lists.size(), -1);
         const int ptop = pack(offs);
-        if (balance || (volume && ptop < top)) {
+        if (balance || ptop < top) {
             for (size_t li = 0; li < B.lists.size(); li++)
                 if (lphase[li] >= 0) B.lists[li].off = offs[li];
             top = ptop;
