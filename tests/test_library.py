@@ -74,6 +74,24 @@ def test_describe_dispatch(lib):
     assert mf.mf_describe(10, 10, 1, mf.MF_F32, 1) == "identity copy"
 
 
+def test_size_aware_default_for_lone_small_images(lib):
+    """Untuned, a lone 8/16-bit image at k = 3, 5 runs the configuration
+    without a wide run below 2^20 pixels, the 2-tile run up to 2^22 pixels
+    and the 4-tile run above (host dispatch only; no GPU)."""
+    import os
+    if os.environ.get("MF_TUNE_CACHE"):
+        pytest.skip("a tuning cache decides the configuration")
+    for k in (3, 5):
+        for dt in (mf.MF_U8, mf.MF_U16):
+            runs = [mf.mf_describe(H, W, 1, dt, k, mf.MF_AUTO).split("run=")[1].split()[0]
+                    for H, W in ((480, 640), (1080, 1920), (4096, 4096))]
+            assert runs == ["1", "2", "4"], (k, dt, runs)
+    # 32-bit keys keep their default at every size
+    small = mf.mf_describe(480, 640, 1, mf.MF_F32, 5, mf.MF_AUTO)
+    big = mf.mf_describe(4096, 4096, 1, mf.MF_F32, 5, mf.MF_AUTO)
+    assert small.split("kernel=")[1] == big.split("kernel=")[1]
+
+
 def test_batch_rejects_bad_descriptors(lib):
     d = mf.ImageDesc(0x1000, 0x900000, 8, 8, 8, 1, mf.MF_U8, 33)  # k > 31
     with pytest.raises(mf.MedianFilterError):
