@@ -65,6 +65,15 @@ int mf_median_filter_3d_describe(int k, mf_dtype dtype, char *buf, size_t n);
  * no plan exists. */
 int mf_d3_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians, int *stats);
 
+/* As mf_d3_plan_check for the plan the kernel builds for keys of key_bytes
+ * bytes (1: 8-bit data, 2: 16-bit data, 4: 32-bit data) run by blocks of
+ * `threads` threads (256, 512 or 1024), which select its merge chunks
+ * (mf_d3_plan_check plans for 4-byte keys and 256 threads).  The footprint
+ * still holds 64-bit keys.  MF_ERR_ARG for other key widths or block
+ * sizes. */
+int mf_d3_plan_check_ex(int k, int tile, int strip, int key_bytes, int threads, const uint64_t *footprint,
+                        uint64_t *medians, int *stats);
+
 #ifdef __cplusplus
 }
 #endif

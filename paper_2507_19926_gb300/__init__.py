@@ -35,7 +35,8 @@ EXPORTS = ["mf_median_filter", "mf_median_filter_ex", "mf_median_filter_tile", "
            "mf_status_string", "mf_last_error", "mf_version", "mf_shutdown", "mf_probe_minmax",
            "mf_d1_plan_check",
            # include/medianfilter_volume.h
-           "mf_median_filter_3d", "mf_median_filter_3d_ex", "mf_median_filter_3d_describe", "mf_d3_plan_check"]
+           "mf_median_filter_3d", "mf_median_filter_3d_ex", "mf_median_filter_3d_describe", "mf_d3_plan_check",
+           "mf_d3_plan_check_ex"]
 
 
 class MedianFilterError(RuntimeError):
@@ -89,6 +90,7 @@ def load_library(path=LIB_PATH):
         lib.mf_median_filter_3d_ex.argtypes = [vp, vp, i, i, i, sz, i, i, i, i, vp]
         lib.mf_median_filter_3d_describe.argtypes = [i, i, ctypes.c_char_p, sz]
         lib.mf_d3_plan_check.argtypes = [i, i, i, vp, vp, vp]
+        lib.mf_d3_plan_check_ex.argtypes = [i, i, i, i, i, vp, vp, vp]
         lib.mf_status_string.argtypes = [i]
         lib.mf_status_string.restype = ctypes.c_char_p
         lib.mf_last_error.restype = ctypes.c_char_p
@@ -250,20 +252,25 @@ def mf_median_filter_3d_describe(k, dtype):
     return buf.value.decode()
 
 
-def mf_d3_plan_check(k, tile, footprint=None, strip=1):
-    """Builds the volumetric schedule for (k, tile, strip); with a uint64
-    footprint of keys (F = tile + k - 1 in y and z, FX = strip*tile + k - 1
-    in x, element (fx, fy, fz) at (fy*FX + fx)*F + fz) also runs it on the
-    CPU.  Returns (stats dict, strip*tile^3 medians in (z, y, x) order or
-    None)."""
+def mf_d3_plan_check(k, tile, footprint=None, strip=1, key_bytes=None, threads=256):
+    """Builds the volumetric schedule for (k, tile, strip) -- for keys of
+    key_bytes bytes and blocks of `threads` threads when key_bytes is given
+    (else 4-byte keys, 256 threads); with a uint64 footprint of keys
+    (F = tile + k - 1 in y and z, FX = strip*tile + k - 1 in x, element
+    (fx, fy, fz) at (fy*FX + fx)*F + fz) also runs it on the CPU.  Returns
+    (stats dict, strip*tile^3 medians in (z, y, x) order or None)."""
     import numpy as np
     st = np.zeros(7, np.int32)
     med = fp = None
     if footprint is not None:
         fp = np.ascontiguousarray(footprint, dtype=np.uint64)
         med = np.zeros(strip * tile ** 3, np.uint64)
-    _check(load_library().mf_d3_plan_check(k, tile, strip, fp.ctypes.data if fp is not None else None,
-                                           med.ctypes.data if med is not None else None, st.ctypes.data))
+    args = (fp.ctypes.data if fp is not None else None, med.ctypes.data if med is not None else None,
+            st.ctypes.data)
+    if key_bytes is None:
+        _check(load_library().mf_d3_plan_check(k, tile, strip, *args))
+    else:
+        _check(load_library().mf_d3_plan_check_ex(k, tile, strip, key_bytes, threads, *args))
     names = ["smem_elems", "phases", "tasks", "work_items", "merged", "sorted", "max_sort"]
     return dict(zip(names, [int(v) for v in st])), med
 

@@ -29,6 +29,7 @@
 #include <tuple>
 
 #include "../../include/medianfilter.h"
+#include "../../include/medianfilter_volume.h"
 #include "mf_d1_ops.cuh"
 #include "mf_d1_plan.h"
 
@@ -1129,11 +1130,13 @@ extern "C" int mf_d1_plan_check(int k, int tile, int strip, const uint64_t *foot
     return mf_d1_plan_check_rect(k, k, tile, tile, strip, footprint, medians, stats);
 }
 
-// Host check of the volumetric schedule (declared in medianfilter.h).
-extern "C" int mf_d3_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,
-                                int *stats) {
+// Host check of the volumetric schedule (declared in medianfilter_volume.h).
+extern "C" int mf_d3_plan_check_ex(int k, int tile, int strip, int key_bytes, int threads, const uint64_t *footprint,
+                                   uint64_t *medians, int *stats) {
+    if ((key_bytes != 1 && key_bytes != 2 && key_bytes != 4) || (threads != 256 && threads != 512 && threads != 1024))
+        return MF_ERR_ARG;
     mf::D1Plan plan;
-    if (!mf::d3_build_plan(k, tile, &plan, 256, 4, strip)) return MF_ERR_UNSUPPORTED;
+    if (!mf::d3_build_plan(k, tile, &plan, threads, key_bytes, strip)) return MF_ERR_UNSUPPORTED;
     if (stats) {
         stats[0] = plan.smem_elems;
         stats[1] = (int)plan.phase_begin.size() - 1;
@@ -1145,4 +1148,9 @@ extern "C" int mf_d3_plan_check(int k, int tile, int strip, const uint64_t *foot
     }
     if (footprint && medians) mf::d1_run_plan_host(plan, footprint, medians);
     return MF_OK;
+}
+
+extern "C" int mf_d3_plan_check(int k, int tile, int strip, const uint64_t *footprint, uint64_t *medians,
+                                int *stats) {
+    return mf_d3_plan_check_ex(k, tile, strip, 4, 256, footprint, medians, stats);
 }

@@ -47,6 +47,33 @@ def test_strip_plan_matches_oracle(k, T, B):
     assert st["sorted"] < B * one["sorted"]  # shared line sorts
 
 
+# (k, root tile, strip, key bytes, threads): the plans the volumetric kernel
+# runs by default for 8-bit (1-byte keys), 16-bit (2) and 32-bit (4) data
+VOL_CASES = [(7, 4, 2, 1, 256), (9, 4, 1, 1, 256), (15, 4, 1, 1, 512), (19, 4, 1, 1, 1024), (7, 4, 2, 2, 256),
+             (7, 4, 1, 4, 256), (19, 2, 1, 4, 512)]
+
+
+@pytest.mark.parametrize("k,T,B,kb,nt", VOL_CASES)
+def test_plan_by_key_width_matches_oracle(k, T, B, kb, nt):
+    F, FX = T + k - 1, B * T + k - 1
+    r = k // 2
+    for s, gen in enumerate((synth.uniform, synth.levels16)):
+        vol = gen((F, F, FX), "u16", 53 * k + T + kb + s)
+        _, med = mf.mf_d3_plan_check(k, T, _footprint(vol), strip=B, key_bytes=kb, threads=nt)
+        want = oracle.median_filter_3d(vol, k)[r:r + T, r:r + T, r:r + B * T].ravel()
+        assert np.array_equal(med.astype(np.uint16), want), (k, T, B, kb, nt, s)
+    # most keys equal to the sentinel value (the largest key)
+    top = np.uint64(0xFFFFFFFFFFFFFFFF)
+    rng = np.random.default_rng(k + kb)
+    vals = np.array([0, 1, 2, top], dtype=np.uint64)
+    vol = vals[np.where(rng.random((F, F, FX)) < 0.55, 3, rng.integers(0, 3, (F, F, FX)))]
+    _, med = mf.mf_d3_plan_check(k, T, _footprint(vol), strip=B, key_bytes=kb, threads=nt)
+    m = (k ** 3 - 1) // 2
+    want = np.array([np.sort(vol[z:z + k, y:y + k, x:x + k].ravel())[m]
+                     for z in range(T) for y in range(T) for x in range(B * T)], dtype=np.uint64)
+    assert np.array_equal(med, want), (k, T, B, kb, nt)
+
+
 def test_plan_work_grows_slower_than_the_window():
     """Sharing the sorted core among the T^3 voxels of a root tile: merged
     elements per voxel stay below the k^3 elements of one window, and their
